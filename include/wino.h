@@ -1,0 +1,179 @@
+/*
+ * wino.h -- C ABI of the GB300 Winograd point-selection library.
+ *
+ * The library computes Toom-Cook / Winograd convolution F(m, r) and
+ * F(m x m, r x r) with transform matrices built from a caller-chosen point
+ * set (Alam, Anderson, Barabasz, Gregg, "Winograd Convolution for Deep Neural
+ * Networks: Efficient Point Selection"), and the batched FP32-versus-FP64
+ * error sweep over the point parameter c that the paper uses to pick points
+ * (Sec. 6).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a wino_status; nothing is thrown across the ABI.
+ *    wino_last_error() returns a thread-local text for the last failure.
+ *  - Device pointers are plain CUDA device addresses (for example a torch
+ *    tensor's data_ptr()), contiguous, row-major, owned by the caller.
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work of a call is enqueued on that stream and the
+ *    call returns without synchronising, unless stated otherwise.
+ *  - The library keeps internal scratch (allocated on first use and grown
+ *    when needed, or caller-provided through wino_set_workspace) and releases
+ *    it in wino_shutdown().  It never frees caller memory.
+ *  - There is no CPU fallback: when no sm_103 device is present the GPU
+ *    entry points return WINO_EUNSUPPORTED.
+ *  - Point sets: alpha = m + r - 1 doubles holding alpha-1 distinct finite
+ *    points and exactly one +INFINITY, in any order.  The library sorts the
+ *    finite points ascending and puts infinity last (the modified Toom-Cook
+ *    construction of Sec. 4.2 treats infinity as the extra point).
+ */
+#ifndef WINO_H
+#define WINO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WINO_OK = 0,
+  WINO_EINVAL = -1,        /* bad argument: size, null pointer, dtype      */
+  WINO_ESINGULAR = -2,     /* two finite points equal (Vandermonde singular) */
+  WINO_ENOMEM = -3,        /* scratch could not be allocated / is too small */
+  WINO_ECUDA = -4,         /* a CUDA runtime call failed                    */
+  WINO_ETIMEOUT = -5,      /* a bounded device wait gave up                 */
+  WINO_EUNSUPPORTED = -6   /* no sm_103 device, or unsupported combination  */
+} wino_status;
+
+/* Arithmetic of the Winograd-domain contraction (the alpha^2 GEMMs).
+ * Transforms are FP32 in every form; only the contraction changes.        */
+typedef enum {
+  WINO_F32 = 0,            /* FP32 SIMT fused multiply-add                  */
+  WINO_BF16_TC = 1,        /* BF16 operands on tcgen05, FP32 accumulate     */
+  WINO_FP16_TC = 2,        /* FP16 operands on tcgen05, FP32 accumulate     */
+  WINO_SPLIT_BF16X3 = 3    /* hi/lo BF16 split, 3 tcgen05 products, FP32 acc */
+} wino_dtype;
+
+/* Largest alpha = m + r - 1 the library accepts. */
+#define WINO_MAX_ALPHA 12
+
+/* ---------------------------------------------------------------------- */
+/* Transform matrices (host, FP64).                                        */
+/* ---------------------------------------------------------------------- */
+
+/* Builds the modified Toom-Cook matrices for F(m, r) from `points`
+ * (Sec. 4.1 Eqs. (10)-(11) with N_i folded into G; Sec. 4.2 Eq. (19) for the
+ * point at infinity):
+ *   G [alpha][r]    : G[i][k]  = a_i^k / N_i,  N_i = prod_{j != i}(a_i - a_j);
+ *                     last row e_{r-1}
+ *   AT[m][alpha]    : AT[j][i] = a_i^j; last column e_{m-1}
+ *   BT[alpha][alpha]: row i < alpha-1 = ascending coefficients of
+ *                     prod_{j != i}(x - a_j); last row = coefficients of
+ *                     M'(x) = prod_j (x - a_j)
+ * so that Y = AT [(G g) .* (BT d)] (Eq. (8)) is the correlation
+ * Y_j = sum_k g_k d_{j+k}.  Rows/columns follow the canonical point order
+ * (finite ascending, infinity last).  Outputs are caller-owned host arrays,
+ * row-major FP64.  Returns WINO_ESINGULAR on equal finite points, WINO_EINVAL
+ * on non-finite points other than one +INFINITY, on m < 1, r < 1 or
+ * alpha > WINO_MAX_ALPHA.  Pure host code; needs no GPU.                   */
+int wino_make_matrices(const double* points, int m, int r,
+                       double* AT, double* G, double* BT);
+
+/* ---------------------------------------------------------------------- */
+/* Winograd convolution layer (device).                                     */
+/* ---------------------------------------------------------------------- */
+
+/* 1D layer, Eq. (8) applied per tile of m outputs (tiles overlap by r-1,
+ * stride m, zero padding `pad`, ragged last tile zero-filled):
+ *   x[N][C][L], w[K][C][r], y[N][K][Lo], Lo = L + 2*pad - r + 1,
+ *   y[n][k][o] = sum_c sum_u x[n][c][o+u-pad] * w[k][c][u]   (stride 1).
+ * x, w, y are FP32 device arrays; `dtype` selects the contraction.        */
+int wino_conv1d(const void* x, const void* w, void* y,
+                int N, int C, int K, int L, int pad,
+                const double* points, int m, int r, int dtype,
+                void* cuda_stream);
+
+/* 2D layer, Eq. (9) per m x m output tile; the per-tile Hadamard products
+ * summed over C_in form alpha^2 independent GEMMs (Sec. 4.1):
+ *   x[N][C][H][W], w[K][C][r][r], y[N][K][Ho][Wo], Ho = H+2pad-r+1,
+ *   Wo = W+2pad-r+1, y[n][k][p][q] = sum_{c,u,v} x[n][c][p+u-pad][q+v-pad]
+ *   * w[k][c][u][v]   (Eq. (1), stride 1).  FP32 device arrays.            */
+int wino_conv2d(const void* x, const void* w, void* y,
+                int N, int C, int K, int H, int W, int pad,
+                const double* points, int m, int r, int dtype,
+                void* cuda_stream);
+
+/* Scratch the layer needs for this shape (bytes); 0 on invalid input.     */
+size_t wino_workspace_bytes(int N, int C, int K, int H, int W,
+                            int m, int r, int dtype);
+
+/* Hands the library caller-owned device scratch of `bytes` bytes, used by
+ * later layer calls instead of an internal allocation (NULL, 0 = go back to
+ * internal scratch).  A call whose need exceeds it returns WINO_ENOMEM.
+ * The caller keeps ownership and must keep it alive while calls using it
+ * are in flight.                                                           */
+int wino_set_workspace(void* dev_ptr, size_t bytes);
+
+/* FP64 direct correlation, Eq. (1), the reference the paper measures FP32
+ * Winograd against (Sec. 6: "normal convolution using double precision").
+ * x[N][C][H][W] and w[K][C][r][r] are FP32 device arrays (widened exactly),
+ * y64[N][K][Ho][Wo] is an FP64 device array.  dim = 1 treats H as 1 and
+ * w as [K][C][r].                                                          */
+int wino_direct_conv_f64(const void* x, const void* w, void* y64,
+                         int dim, int N, int C, int K, int H, int W,
+                         int pad, int r, void* cuda_stream);
+
+/* Error statistics of an FP32 result against its FP64 reference, reduced on
+ * the device in FP64 (warp shuffles): out4 (host, FP64) receives
+ *   { sum |yhat - y|, sum |y|, max |yhat - y|, max |y| }.
+ * Synchronises `cuda_stream` because the result is a host array.          */
+int wino_error_stats(const void* yhat_f32, const void* y_f64, int64_t n,
+                     double* out4, void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* Batched point sweep (device), Sec. 6.1-6.3.                              */
+/* ---------------------------------------------------------------------- */
+
+/* One problem size of the sweep: 1D F(m, r) (dim = 1) or 2D F(m x m, r x r)
+ * (dim = 2); `d` is the fixed second group parameter of Eq. (22).          */
+typedef struct {
+  int dim, m, r;
+  double d;
+} wino_size;
+
+/* Subset masks: bit b selects slot b of
+ *   [-1/c, -c, c, 1/c, -1/d, -d, d, 1/d]
+ * (Eqs. (21)-(25)); the point set is {0, inf} plus the selected slots.  A
+ * mask is valid for a size when popcount(mask) = alpha - 2, and, when
+ * |d| == 1 (the d-group collapses to {-1, 1}), bits 4 and 7 are clear (bits
+ * 5 and 6 stand for -1 and 1).  Invalid (size, mask) pairs are skipped and
+ * get NaN.  A c for which two points coincide exactly gets +INFINITY.
+ *
+ * For every valid (size, mask, c): `trials` single-tile problems with g, d
+ * uniform in [-1, 1) drawn from the counter-based SplitMix64 stream of
+ * `seed` (the same trials for every mask and c of a size), evaluated with
+ * FP32 Winograd (transforms and Hadamard product in FP32, matrices built in
+ * FP64 and rounded once) and scored against the FP64 direct correlation:
+ *   err = sum_t ||yhat_t - y_t||_1 / sum_t ||y_t||_1.
+ * err_out is a caller-owned HOST array [n_sizes][n_subsets][n_c] (FP64).
+ * c_grid, sizes, subsets are host arrays.  Synchronises `cuda_stream`.     */
+int wino_error_sweep(const double* c_grid, int n_c,
+                     const wino_size* sizes, int n_sizes,
+                     const unsigned char* subsets, int n_subsets,
+                     int trials, unsigned long long seed,
+                     double* err_out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* Library state.                                                           */
+/* ---------------------------------------------------------------------- */
+
+const char* wino_last_error(void);  /* thread-local message, never NULL  */
+int wino_device_ok(void);           /* 1 when an sm_103 device is usable  */
+void wino_shutdown(void);           /* frees internal scratch and graphs  */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WINO_H */

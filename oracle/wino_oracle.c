@@ -1,0 +1,679 @@
+/*
+ * wino_oracle.c -- plain CPU oracle for Winograd point selection.
+ *
+ * TEST INFRASTRUCTURE ONLY: the slow, obviously correct statement of what
+ * the GPU library computes.  Only tests/, __graft_entry__.smoke() and
+ * bench.py's CPU-baseline leg may load it; the library never does.  It
+ * shares no code with paper_2201_10369_gb300/.
+ *
+ * Build: cc -O2 -ffp-contract=off -fPIC -shared wino_oracle.c -lm -lpthread
+ * (-ffp-contract=off so that every a*b+c written below rounds twice unless
+ * it is spelled fmaf).
+ *
+ * FP32 operation order (the paper does not state one; this is the reading
+ * the GPU path also follows): every matrix-vector product is computed output
+ * by output as acc = 0; for each inner index in ascending order
+ * acc = fmaf(matrix entry, vector entry, acc).  The Hadamard product is a
+ * single rounded multiply; in a layer the per-frequency products are summed
+ * over input channels c in ascending order with fmaf.
+ */
+#include "wino_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Point sets and the modified Toom-Cook matrices (Sec. 4.1, 4.2).           */
+/* ------------------------------------------------------------------------ */
+
+int orc_canonical_points(const double* points, int alpha, double* out) {
+  int n_inf = 0, nf = 0;
+  double fin[ORC_MAX_ALPHA];
+  if (alpha < 2 || alpha > ORC_MAX_ALPHA) return -1;
+  for (int i = 0; i < alpha; ++i) {
+    double p = points[i];
+    if (isnan(p)) return -1;
+    if (isinf(p)) {
+      if (p < 0) return -1;
+      ++n_inf;
+    } else {
+      fin[nf++] = p;
+    }
+  }
+  if (n_inf != 1) return -1;
+  /* insertion sort, ascending */
+  for (int i = 1; i < nf; ++i) {
+    double v = fin[i];
+    int j = i - 1;
+    while (j >= 0 && fin[j] > v) {
+      fin[j + 1] = fin[j];
+      --j;
+    }
+    fin[j + 1] = v;
+  }
+  for (int i = 0; i < nf; ++i) out[i] = fin[i];
+  out[nf] = INFINITY;
+  return alpha;
+}
+
+/* Multiplies the ascending coefficient vector p (degree deg) by (x - a):
+ * q_l = p_{l-1} - a * p_l, one rounded multiply then one rounded subtract. */
+static void poly_mul_linear(double* p, int deg, double a) {
+  p[deg + 1] = p[deg];
+  for (int l = deg; l >= 1; --l) p[l] = p[l - 1] - a * p[l];
+  p[0] = 0.0 - a * p[0];
+}
+
+int orc_make_matrices(const double* points, int m, int r,
+                      double* AT, double* G, double* BT) {
+  if (m < 1 || r < 1) return -1;
+  const int alpha = m + r - 1;
+  if (alpha < 2 || alpha > ORC_MAX_ALPHA) return -1;
+  double a[ORC_MAX_ALPHA];
+  if (orc_canonical_points(points, alpha, a) < 0) return -1;
+  const int nf = alpha - 1; /* finite points a_0 .. a_{alpha-2} */
+  for (int i = 0; i + 1 < nf; ++i)
+    if (a[i] == a[i + 1]) return -2;
+
+  /* N_i = prod_{j != i} (a_i - a_j), factors in ascending j (Sec. 4.1). */
+  double N[ORC_MAX_ALPHA];
+  for (int i = 0; i < nf; ++i) {
+    double prod = 1.0;
+    for (int j = 0; j < nf; ++j)
+      if (j != i) prod = prod * (a[i] - a[j]);
+    N[i] = prod;
+  }
+
+  /* G: Vandermonde rows a_i^k scaled by 1/N_i (Eq. (10), N_i folded into G),
+   * powers by repeated multiplication, then one division; last row e_{r-1}
+   * for the point at infinity (Eq. (19)). */
+  for (int i = 0; i < nf; ++i) {
+    double pw = 1.0;
+    for (int k = 0; k < r; ++k) {
+      G[i * r + k] = pw / N[i];
+      pw = pw * a[i];
+    }
+  }
+  for (int k = 0; k < r; ++k) G[nf * r + k] = (k == r - 1) ? 1.0 : 0.0;
+
+  /* AT: AT[j][i] = a_i^j (Eq. (10)); last column e_{m-1} (Eq. (19)). */
+  for (int i = 0; i < nf; ++i) {
+    double pw = 1.0;
+    for (int j = 0; j < m; ++j) {
+      AT[j * alpha + i] = pw;
+      pw = pw * a[i];
+    }
+  }
+  for (int j = 0; j < m; ++j) AT[j * alpha + nf] = (j == m - 1) ? 1.0 : 0.0;
+
+  /* BT: row i < nf = coefficients of prod_{j != i}(x - a_j) (Eq. (11),
+   * M_i = M/m_i); last row = coefficients of M'(x) = prod_j (x - a_j)
+   * (Eq. (19)).  Factors multiplied in ascending j. */
+  double poly[ORC_MAX_ALPHA + 1];
+  for (int i = 0; i < nf; ++i) {
+    int deg = 0;
+    for (int l = 0; l <= alpha; ++l) poly[l] = 0.0;
+    poly[0] = 1.0;
+    for (int j = 0; j < nf; ++j) {
+      if (j == i) continue;
+      poly_mul_linear(poly, deg, a[j]);
+      ++deg;
+    }
+    for (int l = 0; l < alpha; ++l) BT[i * alpha + l] = (l <= deg) ? poly[l] : 0.0;
+  }
+  {
+    int deg = 0;
+    for (int l = 0; l <= alpha; ++l) poly[l] = 0.0;
+    poly[0] = 1.0;
+    for (int j = 0; j < nf; ++j) {
+      poly_mul_linear(poly, deg, a[j]);
+      ++deg;
+    }
+    for (int l = 0; l < alpha; ++l) BT[nf * alpha + l] = poly[l];
+  }
+  return alpha;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct correlation (Eq. (1)).                                             */
+/* ------------------------------------------------------------------------ */
+
+void orc_direct_f64(const float* x, const float* w, double* y, int dim,
+                    int N, int C, int K, int H, int W, int pad, int r) {
+  const int Hin = (dim == 1) ? 1 : H;
+  const int rh = (dim == 1) ? 1 : r;
+  const int Ho = (dim == 1) ? 1 : H + 2 * pad - r + 1;
+  const int Wo = W + 2 * pad - r + 1;
+  const int padh = (dim == 1) ? 0 : pad;
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k)
+      for (int p = 0; p < Ho; ++p)
+        for (int q = 0; q < Wo; ++q) {
+          double acc = 0.0;
+          for (int c = 0; c < C; ++c)
+            for (int u = 0; u < rh; ++u)
+              for (int v = 0; v < r; ++v) {
+                int hh = p + u - padh, ww = q + v - pad;
+                if (hh < 0 || hh >= Hin || ww < 0 || ww >= W) continue;
+                double xv = (double)x[(((size_t)n * C + c) * Hin + hh) * W + ww];
+                double wv = (double)w[(((size_t)k * C + c) * rh + u) * r + v];
+                acc += xv * wv;
+              }
+          y[(((size_t)n * K + k) * Ho + p) * Wo + q] = acc;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 Winograd, one tile (Eqs. (8), (9)).                                  */
+/* ------------------------------------------------------------------------ */
+
+void orc_tile1d_f32(const float* AT, const float* G, const float* BT,
+                    int m, int r, const float* g, const float* d, float* y) {
+  const int alpha = m + r - 1;
+  float u[ORC_MAX_ALPHA], v[ORC_MAX_ALPHA], p[ORC_MAX_ALPHA];
+  for (int i = 0; i < alpha; ++i) { /* u = G g */
+    float acc = 0.0f;
+    for (int k = 0; k < r; ++k) acc = fmaf(G[i * r + k], g[k], acc);
+    u[i] = acc;
+  }
+  for (int i = 0; i < alpha; ++i) { /* v = BT d */
+    float acc = 0.0f;
+    for (int l = 0; l < alpha; ++l) acc = fmaf(BT[i * alpha + l], d[l], acc);
+    v[i] = acc;
+  }
+  for (int i = 0; i < alpha; ++i) p[i] = u[i] * v[i]; /* Hadamard */
+  for (int j = 0; j < m; ++j) { /* y = AT p */
+    float acc = 0.0f;
+    for (int i = 0; i < alpha; ++i) acc = fmaf(AT[j * alpha + i], p[i], acc);
+    y[j] = acc;
+  }
+}
+
+/* 2D nesting of the 1D algorithm, Eq. (9): U = G g G^T, V = B^T d B,
+ * Y = A^T (U .* V) A, each as two matrix products (left factor first). */
+void orc_tile2d_f32(const float* AT, const float* G, const float* BT,
+                    int m, int r, const float* g, const float* d, float* y) {
+  const int A = m + r - 1;
+  float Wk[ORC_MAX_ALPHA * ORC_MAX_ALPHA], U[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float T[ORC_MAX_ALPHA * ORC_MAX_ALPHA], V[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float Z[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int i = 0; i < A; ++i) /* Wk = G g  (A x r) */
+    for (int k = 0; k < r; ++k) {
+      float acc = 0.0f;
+      for (int l = 0; l < r; ++l) acc = fmaf(G[i * r + l], g[l * r + k], acc);
+      Wk[i * r + k] = acc;
+    }
+  for (int i = 0; i < A; ++i) /* U = Wk G^T  (A x A) */
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+      for (int k = 0; k < r; ++k) acc = fmaf(Wk[i * r + k], G[j * r + k], acc);
+      U[i * A + j] = acc;
+    }
+  for (int i = 0; i < A; ++i) /* T = B^T d */
+    for (int l = 0; l < A; ++l) {
+      float acc = 0.0f;
+      for (int k = 0; k < A; ++k) acc = fmaf(BT[i * A + k], d[k * A + l], acc);
+      T[i * A + l] = acc;
+    }
+  for (int i = 0; i < A; ++i) /* V = T B,  B[l][j] = BT[j][l] */
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+      for (int l = 0; l < A; ++l) acc = fmaf(T[i * A + l], BT[j * A + l], acc);
+      V[i * A + j] = acc;
+    }
+  for (int i = 0; i < A * A; ++i) V[i] = U[i] * V[i]; /* Hadamard */
+  for (int a = 0; a < m; ++a) /* Z = A^T P */
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+      for (int i = 0; i < A; ++i) acc = fmaf(AT[a * A + i], V[i * A + j], acc);
+      Z[a * A + j] = acc;
+    }
+  for (int a = 0; a < m; ++a) /* Y = Z A,  A[j][b] = AT[b][j] */
+    for (int b = 0; b < m; ++b) {
+      float acc = 0.0f;
+      for (int j = 0; j < A; ++j) acc = fmaf(Z[a * A + j], AT[b * A + j], acc);
+      y[a * m + b] = acc;
+    }
+}
+
+void orc_tile_direct_f32(int dim, int m, int r, const float* g,
+                         const float* d, float* y) {
+  const int A = m + r - 1;
+  if (dim == 1) {
+    for (int j = 0; j < m; ++j) {
+      float acc = 0.0f;
+      for (int k = 0; k < r; ++k) acc = fmaf(g[k], d[j + k], acc);
+      y[j] = acc;
+    }
+    return;
+  }
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      float acc = 0.0f;
+      for (int u = 0; u < r; ++u)
+        for (int v = 0; v < r; ++v) acc = fmaf(g[u * r + v], d[(a + u) * A + b + v], acc);
+      y[a * m + b] = acc;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reduced-precision operand rounding (precision form of the contraction).  */
+/* ------------------------------------------------------------------------ */
+
+static uint32_t f2u(float v) { uint32_t u; memcpy(&u, &v, 4); return u; }
+static float u2f(uint32_t u) { float v; memcpy(&v, &u, 4); return v; }
+
+/* BF16 = the top 16 bits of an FP32 value, round to nearest even. */
+float orc_round_bf16(float v) {
+  if (isnan(v)) return v;
+  uint32_t u = f2u(v);
+  uint32_t lsb = (u >> 16) & 1u;
+  u = u + 0x7FFFu + lsb;
+  return u2f(u & 0xFFFF0000u);
+}
+
+/* FP16 (1 sign, 5 exponent, 10 fraction bits) round to nearest even,
+ * written out in terms of the representable grid: the spacing of FP16 at
+ * |v| is 2^(e-10) for normal e >= -14, 2^-24 for subnormals; values at or
+ * above 65520 overflow to infinity. */
+float orc_round_fp16(float v) {
+  if (isnan(v) || isinf(v)) return v;
+  double a = fabs((double)v);
+  if (a >= 65520.0) return v < 0 ? -INFINITY : INFINITY;
+  int e;
+  double spacing;
+  if (a < 0x1p-14) {
+    spacing = 0x1p-24;
+  } else {
+    frexp(a, &e); /* a = f * 2^e, f in [0.5, 1) -> unbiased exponent e-1 */
+    spacing = ldexp(1.0, (e - 1) - 10);
+  }
+  double q = a / spacing;       /* exact: spacing is a power of two */
+  double fl = floor(q);
+  double rem = q - fl;
+  double n = fl;
+  if (rem > 0.5 || (rem == 0.5 && fmod(fl, 2.0) != 0.0)) n = fl + 1.0;
+  double res = n * spacing;
+  return (float)(v < 0 ? -res : res);
+}
+
+static float round_mode(float v, int lowp) {
+  if (lowp == 2) return orc_round_fp16(v);
+  return orc_round_bf16(v);
+}
+
+/* power of two 2^-E with max * 2^-E in [1, 2); 1 when max is 0. */
+static float pow2_normaliser(double mx) {
+  if (!(mx > 0.0) || isinf(mx)) return 1.0f;
+  int e;
+  frexp(mx, &e);
+  return (float)ldexp(1.0, -(e - 1));
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 Winograd layer.                                                      */
+/* ------------------------------------------------------------------------ */
+
+int orc_wino_layer(const float* x, const float* w, float* y, int dim,
+                   int N, int C, int K, int H, int W, int pad,
+                   const double* points, int m, int r, int lowp) {
+  const int A = m + r - 1;
+  double ATd[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Gd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  double BTd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  int st = orc_make_matrices(points, m, r, ATd, Gd, BTd);
+  if (st < 0) return st;
+  float AT[ORC_MAX_ALPHA * ORC_MAX_ALPHA], G[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float BT[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int i = 0; i < m * A; ++i) AT[i] = (float)ATd[i];
+  for (int i = 0; i < A * r; ++i) G[i] = (float)Gd[i];
+  for (int i = 0; i < A * A; ++i) BT[i] = (float)BTd[i];
+
+  const int Hin = (dim == 1) ? 1 : H;
+  const int Ho = (dim == 1) ? 1 : H + 2 * pad - r + 1;
+  const int Wo = W + 2 * pad - r + 1;
+  const int padh = (dim == 1) ? 0 : pad;
+  const int th = (dim == 1) ? 1 : (Ho + m - 1) / m;
+  const int tw = (Wo + m - 1) / m;
+  const int F = (dim == 1) ? A : A * A;       /* frequencies per tile */
+  const int ro = (dim == 1) ? 1 : m;          /* output tile rows     */
+  const int rw = (dim == 1) ? r : r * r;      /* filter taps          */
+  const size_t T = (size_t)N * th * tw;
+
+  float* V = (float*)malloc(sizeof(float) * (size_t)F * C * K);
+  float* U = (float*)malloc(sizeof(float) * (size_t)F * T * C);
+  if (!V || !U) { free(V); free(U); return -1; }
+
+  /* filter transform: V[f][c][k] = (G g G^T)[f]  (1D: G g) */
+  float tmpd[ORC_MAX_ALPHA * ORC_MAX_ALPHA], outt[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int k = 0; k < K; ++k)
+    for (int c = 0; c < C; ++c) {
+      const float* g = w + ((size_t)k * C + c) * rw;
+      if (dim == 1) {
+        for (int i = 0; i < A; ++i) {
+          float acc = 0.0f;
+          for (int q = 0; q < r; ++q) acc = fmaf(G[i * r + q], g[q], acc);
+          outt[i] = acc;
+        }
+      } else {
+        float Wk[ORC_MAX_ALPHA * 5];
+        for (int i = 0; i < A; ++i)
+          for (int q = 0; q < r; ++q) {
+            float acc = 0.0f;
+            for (int l = 0; l < r; ++l) acc = fmaf(G[i * r + l], g[l * r + q], acc);
+            Wk[i * r + q] = acc;
+          }
+        for (int i = 0; i < A; ++i)
+          for (int j = 0; j < A; ++j) {
+            float acc = 0.0f;
+            for (int q = 0; q < r; ++q) acc = fmaf(Wk[i * r + q], G[j * r + q], acc);
+            outt[i * A + j] = acc;
+          }
+      }
+      for (int f = 0; f < F; ++f) V[((size_t)f * C + c) * K + k] = outt[f];
+    }
+
+  /* input transform: U[f][t][c] = (B^T d B)[f] of the zero-padded patch */
+  for (int n = 0; n < N; ++n)
+    for (int ti = 0; ti < th; ++ti)
+      for (int tj = 0; tj < tw; ++tj) {
+        size_t t = ((size_t)n * th + ti) * tw + tj;
+        for (int c = 0; c < C; ++c) {
+          const int pr = (dim == 1) ? 1 : A;
+          for (int i = 0; i < pr; ++i)
+            for (int j = 0; j < A; ++j) {
+              int hh = ti * m - padh + i, ww = tj * m - pad + j;
+              float v = 0.0f;
+              if (hh >= 0 && hh < Hin && ww >= 0 && ww < W)
+                v = x[(((size_t)n * C + c) * Hin + hh) * W + ww];
+              tmpd[i * A + j] = v;
+            }
+          if (dim == 1) {
+            for (int i = 0; i < A; ++i) {
+              float acc = 0.0f;
+              for (int l = 0; l < A; ++l) acc = fmaf(BT[i * A + l], tmpd[l], acc);
+              outt[i] = acc;
+            }
+          } else {
+            float Tm[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+            for (int i = 0; i < A; ++i)
+              for (int l = 0; l < A; ++l) {
+                float acc = 0.0f;
+                for (int q = 0; q < A; ++q) acc = fmaf(BT[i * A + q], tmpd[q * A + l], acc);
+                Tm[i * A + l] = acc;
+              }
+            for (int i = 0; i < A; ++i)
+              for (int j = 0; j < A; ++j) {
+                float acc = 0.0f;
+                for (int l = 0; l < A; ++l) acc = fmaf(Tm[i * A + l], BT[j * A + l], acc);
+                outt[i * A + j] = acc;
+              }
+          }
+          for (int f = 0; f < F; ++f) U[((size_t)f * T + t) * C + c] = outt[f];
+        }
+      }
+
+  /* precision form: per-frequency power-of-two scales, operand rounding */
+  float sU[ORC_MAX_ALPHA * ORC_MAX_ALPHA], sV[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int f = 0; f < F; ++f) { sU[f] = 1.0f; sV[f] = 1.0f; }
+  if (lowp != 0) {
+    double rown[ORC_MAX_ALPHA];
+    for (int i = 0; i < A; ++i) {
+      double s = 0.0;
+      for (int l = 0; l < A; ++l) s += fabs((double)BT[i * A + l]);
+      rown[i] = s;
+    }
+    for (int f = 0; f < F; ++f) {
+      double gain = (dim == 1) ? rown[f] : rown[f / A] * rown[f % A];
+      sU[f] = pow2_normaliser(gain);
+      double mx = 0.0;
+      for (size_t q = 0; q < (size_t)C * K; ++q) {
+        double a = fabs((double)V[(size_t)f * C * K + q]);
+        if (a > mx) mx = a;
+      }
+      sV[f] = pow2_normaliser(mx);
+    }
+  }
+
+  /* contraction over c and output transform, per (tile, k) */
+  float Mf[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (size_t t = 0; t < T; ++t) {
+    const int n = (int)(t / ((size_t)th * tw));
+    const int ti = (int)((t / tw) % th), tj = (int)(t % tw);
+    for (int k = 0; k < K; ++k) {
+      for (int f = 0; f < F; ++f) {
+        float acc = 0.0f;
+        for (int c = 0; c < C; ++c) {
+          float u = U[((size_t)f * T + t) * C + c];
+          float v = V[((size_t)f * C + c) * K + k];
+          if (lowp == 0) {
+            acc = fmaf(u, v, acc);
+          } else if (lowp == 1 || lowp == 2) {
+            float uq = round_mode(u * sU[f], lowp), vq = round_mode(v * sV[f], lowp);
+            acc = fmaf(uq, vq, acc);
+          } else {
+            float us = u * sU[f], vs = v * sV[f];
+            float uh = orc_round_bf16(us), vh = orc_round_bf16(vs);
+            float ul = orc_round_bf16(us - uh), vl = orc_round_bf16(vs - vh);
+            acc = fmaf(uh, vh, acc);
+            acc = fmaf(uh, vl, acc);
+            acc = fmaf(ul, vh, acc);
+          }
+        }
+        if (lowp != 0) acc = acc / (sU[f] * sV[f]); /* exact: powers of two */
+        Mf[f] = acc;
+      }
+      if (dim == 1) {
+        for (int j = 0; j < m; ++j) {
+          float acc = 0.0f;
+          for (int i = 0; i < A; ++i) acc = fmaf(AT[j * A + i], Mf[i], acc);
+          int q = tj * m + j;
+          if (q < Wo) y[((size_t)n * K + k) * Wo + q] = acc;
+        }
+      } else {
+        float Z[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+        for (int a = 0; a < m; ++a)
+          for (int j = 0; j < A; ++j) {
+            float acc = 0.0f;
+            for (int i = 0; i < A; ++i) acc = fmaf(AT[a * A + i], Mf[i * A + j], acc);
+            Z[a * A + j] = acc;
+          }
+        for (int a = 0; a < ro; ++a)
+          for (int b = 0; b < m; ++b) {
+            float acc = 0.0f;
+            for (int j = 0; j < A; ++j) acc = fmaf(Z[a * A + j], AT[b * A + j], acc);
+            int p = ti * m + a, q = tj * m + b;
+            if (p < Ho && q < Wo) y[(((size_t)n * K + k) * Ho + p) * Wo + q] = acc;
+          }
+      }
+    }
+  }
+  free(U);
+  free(V);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based trial inputs: SplitMix64.                                   */
+/* ------------------------------------------------------------------------ */
+
+uint64_t orc_splitmix64(uint64_t seed, uint64_t n) {
+  /* state after n steps is seed + n * golden gamma; output = finaliser */
+  uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* Counter: 1 + idx + 2^12 (trial + 2^20 (r + 2^4 (m + 2^4 dim))).
+ * Value: top 24 bits k of the output, x = k 2^-23 - 1 (exact in FP32). */
+float orc_trial_value(uint64_t seed, int dim, int m, int r, int trial, int idx) {
+  uint64_t ctr = (uint64_t)dim;
+  ctr = ctr * 16u + (uint64_t)m;
+  ctr = ctr * 16u + (uint64_t)r;
+  ctr = ctr * (1ull << 20) + (uint64_t)trial;
+  ctr = ctr * (1ull << 12) + (uint64_t)idx;
+  uint64_t z = orc_splitmix64(seed, ctr + 1u);
+  double k = (double)(z >> 40);
+  return (float)(k * 0x1p-23 - 1.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Subset masks over the proposed point families (Eqs. (20)-(25)).           */
+/* ------------------------------------------------------------------------ */
+
+int orc_mask_points(int dim, int m, int r, double d, unsigned mask,
+                    double c, double* points) {
+  (void)dim;
+  const int alpha = m + r - 1;
+  int cnt = 0;
+  for (int b = 0; b < 8; ++b) cnt += (mask >> b) & 1u;
+  if (mask > 255u || cnt != alpha - 2) return -1;
+  if (fabs(d) == 1.0 && (mask & 0x90u)) return -1; /* -1/d, 1/d duplicate -d, d */
+  const double slot[8] = {-1.0 / c, -c, c, 1.0 / c, -1.0 / d, -d, d, 1.0 / d};
+  int n = 0;
+  points[n++] = 0.0;
+  for (int b = 0; b < 8; ++b)
+    if ((mask >> b) & 1u) points[n++] = slot[b];
+  points[n++] = INFINITY;
+  return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The error sweep.                                                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int alpha, nin_g, nin_d, nout;
+  float* g;     /* [trials][nin_g] */
+  float* d;     /* [trials][nin_d] */
+  double* y;    /* [trials][nout]  FP64 reference */
+  double ysum;  /* sum_t ||y_t||_1 */
+} size_data;
+
+static int build_size_data(const orc_size* s, int trials, uint64_t seed, size_data* sd) {
+  const int A = s->m + s->r - 1;
+  sd->alpha = A;
+  sd->nin_g = (s->dim == 1) ? s->r : s->r * s->r;
+  sd->nin_d = (s->dim == 1) ? A : A * A;
+  sd->nout = (s->dim == 1) ? s->m : s->m * s->m;
+  sd->g = (float*)malloc(sizeof(float) * (size_t)trials * sd->nin_g);
+  sd->d = (float*)malloc(sizeof(float) * (size_t)trials * sd->nin_d);
+  sd->y = (double*)malloc(sizeof(double) * (size_t)trials * sd->nout);
+  if (!sd->g || !sd->d || !sd->y) return -1;
+  sd->ysum = 0.0;
+  for (int t = 0; t < trials; ++t) {
+    float* g = sd->g + (size_t)t * sd->nin_g;
+    float* d = sd->d + (size_t)t * sd->nin_d;
+    double* y = sd->y + (size_t)t * sd->nout;
+    for (int i = 0; i < sd->nin_g; ++i) g[i] = orc_trial_value(seed, s->dim, s->m, s->r, t, i);
+    for (int i = 0; i < sd->nin_d; ++i) d[i] = orc_trial_value(seed, s->dim, s->m, s->r, t, 256 + i);
+    /* FP64 direct correlation of one tile */
+    if (s->dim == 1)
+      orc_direct_f64(d, g, y, 1, 1, 1, 1, 1, A, 0, s->r);
+    else
+      orc_direct_f64(d, g, y, 2, 1, 1, 1, A, A, 0, s->r);
+    for (int j = 0; j < sd->nout; ++j) sd->ysum += fabs(y[j]);
+  }
+  return 0;
+}
+
+static double eval_instance(const orc_size* s, const size_data* sd, const double* pts,
+                            int trials) {
+  const int A = sd->alpha, m = s->m, r = s->r;
+  double ATd[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Gd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  double BTd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  int st = orc_make_matrices(pts, m, r, ATd, Gd, BTd);
+  if (st == -2) return INFINITY;
+  if (st < 0) return NAN;
+  float AT[ORC_MAX_ALPHA * ORC_MAX_ALPHA], G[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float BT[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int i = 0; i < m * A; ++i) AT[i] = (float)ATd[i];
+  for (int i = 0; i < A * r; ++i) G[i] = (float)Gd[i];
+  for (int i = 0; i < A * A; ++i) BT[i] = (float)BTd[i];
+  double num = 0.0;
+  float yh[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int t = 0; t < trials; ++t) {
+    const float* g = sd->g + (size_t)t * sd->nin_g;
+    const float* d = sd->d + (size_t)t * sd->nin_d;
+    const double* y = sd->y + (size_t)t * sd->nout;
+    if (s->dim == 1)
+      orc_tile1d_f32(AT, G, BT, m, r, g, d, yh);
+    else
+      orc_tile2d_f32(AT, G, BT, m, r, g, d, yh);
+    for (int j = 0; j < sd->nout; ++j) num += fabs((double)yh[j] - y[j]);
+  }
+  return num / sd->ysum;
+}
+
+typedef struct {
+  const double* c_grid;
+  int n_c, n_sizes, n_masks, trials, c_stride, tid, nth;
+  const orc_size* sizes;
+  const unsigned char* masks;
+  const size_data* sd;
+  double* err;
+} sweep_job;
+
+static void* sweep_worker(void* arg) {
+  sweep_job* jb = (sweep_job*)arg;
+  size_t idx = 0;
+  for (int s = 0; s < jb->n_sizes; ++s)
+    for (int q = 0; q < jb->n_masks; ++q)
+      for (int k = 0; k < jb->n_c; k += jb->c_stride, ++idx) {
+        if ((int)(idx % (size_t)jb->nth) != jb->tid) continue;
+        const orc_size* sz = &jb->sizes[s];
+        double pts[ORC_MAX_ALPHA + 2];
+        double* out = &jb->err[((size_t)s * jb->n_masks + q) * jb->n_c + k];
+        int a = orc_mask_points(sz->dim, sz->m, sz->r, sz->d, jb->masks[q], jb->c_grid[k], pts);
+        if (a < 0) { *out = NAN; continue; }
+        *out = eval_instance(sz, &jb->sd[s], pts, jb->trials);
+      }
+  return NULL;
+}
+
+int orc_error_sweep(const double* c_grid, int n_c, const orc_size* sizes,
+                    int n_sizes, const unsigned char* masks, int n_masks,
+                    int trials, uint64_t seed, double* err_out,
+                    int c_stride, int n_threads) {
+  if (c_stride < 1) c_stride = 1;
+  if (n_threads < 1) n_threads = 1;
+  size_data* sd = (size_data*)calloc((size_t)n_sizes, sizeof(size_data));
+  if (!sd) return -1;
+  int rc = 0;
+  for (int s = 0; s < n_sizes && rc == 0; ++s) rc = build_size_data(&sizes[s], trials, seed, &sd[s]);
+  if (rc == 0) {
+    sweep_job* jobs = (sweep_job*)calloc((size_t)n_threads, sizeof(sweep_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int i = 0; i < n_threads; ++i) {
+      sweep_job j = {c_grid, n_c, n_sizes, n_masks, trials, c_stride, i, n_threads,
+                     sizes, masks, sd, err_out};
+      jobs[i] = j;
+    }
+    for (int i = 1; i < n_threads; ++i) pthread_create(&th[i], NULL, sweep_worker, &jobs[i]);
+    sweep_worker(&jobs[0]);
+    for (int i = 1; i < n_threads; ++i) pthread_join(th[i], NULL);
+    free(jobs);
+    free(th);
+  }
+  for (int s = 0; s < n_sizes; ++s) { free(sd[s].g); free(sd[s].d); free(sd[s].y); }
+  free(sd);
+  return rc;
+}
+
+double orc_direct_error(int dim, int m, int r, int trials, uint64_t seed) {
+  orc_size s = {dim, m, r, 1.0};
+  size_data sd;
+  memset(&sd, 0, sizeof(sd));
+  if (build_size_data(&s, trials, seed, &sd) != 0) return NAN;
+  double num = 0.0;
+  float yh[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int t = 0; t < trials; ++t) {
+    orc_tile_direct_f32(dim, m, r, sd.g + (size_t)t * sd.nin_g, sd.d + (size_t)t * sd.nin_d, yh);
+    for (int j = 0; j < sd.nout; ++j) num += fabs((double)yh[j] - sd.y[(size_t)t * sd.nout + j]);
+  }
+  double e = num / sd.ysum;
+  free(sd.g); free(sd.d); free(sd.y);
+  return e;
+}

@@ -1,0 +1,166 @@
+"""Pins of the oracle's sweep: the counter-based generator, the subset masks
+of Eqs. (20)-(25), the error metric against the paper's printed errors
+(Tables 2-4, 7-8) and the shape of the F(4,3) error curve (Sec. 6.1)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_errors.txt")
+
+
+def test_splitmix64_published_outputs(orc):
+    """First outputs of SplitMix64 seeded with 0, as published with the
+    generator (Steele, Lea, Flood 2014; Vigna's reference code)."""
+    assert orc.splitmix64(0, 1) == 0xE220A8397B1DCDAF
+    assert orc.splitmix64(0, 2) == 0x6E789E6AA1B965F4
+    assert orc.splitmix64(0, 3) == 0x06C45D188009454F
+
+
+def test_trial_values_grid_and_distribution(orc):
+    vals = np.array([orc.trial_value(0, 2, 4, 3, t, i) for t in range(200) for i in range(45)])
+    assert np.all(vals >= -1.0) and np.all(vals < 1.0)
+    k = (vals + 1.0) * 2 ** 23
+    assert np.array_equal(k, np.round(k))
+    assert abs(vals.mean()) < 0.03 and abs(vals.var() - 1 / 3) < 0.02
+    assert orc.trial_value(0, 2, 4, 3, 5, 7) != orc.trial_value(0, 2, 4, 3, 5, 263)
+
+
+SWEEP_SIZES = [(1, m, 3, 1.0) for m in range(2, 7)] + [(1, 7, 3, 2.478), (1, 8, 3, 1.229)] + \
+    [(2, m, 3, 1.0) for m in range(2, 7)]
+
+
+def test_mask_enumeration_counts(orc):
+    """Valid masks per size: C(6, alpha-2) with d = 1 (m <= 6), 8 for F(7,3)
+    and 1 for F(8,3): 123 (size, mask) pairs, x 4096 c = 503 808 instances."""
+    counts = []
+    for dim, m, r, d in SWEEP_SIZES:
+        counts.append(sum(orc.mask_points(dim, m, r, d, mk, 1.7) is not None for mk in range(256)))
+    assert counts == [15, 20, 15, 6, 1, 8, 1, 15, 20, 15, 6, 1]
+    assert sum(counts) * 4096 == 503808
+
+
+def test_mask_points_families(orc):
+    c = 1.5
+    assert sorted(orc.mask_points(1, 2, 3, 1.0, 0b0110, c)[:-1]) == [-c, 0.0, c]
+    full = orc.mask_points(1, 4, 3, 1.0, 0x0F, c)
+    assert sorted(full[:-1]) == sorted([0.0, -1 / c, -c, c, 1 / c]) and math.isinf(full[-1])
+    # c = 2, d = 1 at n = 8 reproduces P8 = {0, +-1/2, +-1, +-2, inf} (Table 7)
+    p8 = orc.mask_points(1, 6, 3, 1.0, 0x6F, 2.0)
+    assert sorted(p8[:-1]) == [-2.0, -1.0, -0.5, 0.0, 0.5, 1.0, 2.0]
+    # d = 1: slots -1/d and 1/d duplicate -d and d and are invalid
+    assert orc.mask_points(1, 2, 3, 1.0, 0x90, c) is None
+    assert orc.mask_points(1, 2, 3, 1.0, 0x07, c) is None  # wrong popcount
+
+
+def test_sweep_matches_tilewise_bruteforce(orc):
+    """The sweep's metric equals the definition evaluated trial by trial with
+    the tile functions and the FP64 direct correlation."""
+    trials, seed = 40, 11
+    for dim, m, mask, c in [(1, 4, 0x0F, 1.7), (2, 3, 0x62, 2.0), (2, 2, 0x09, 0.9)]:
+        err = orc.error_sweep([c], [(dim, m, 3, 1.0)], [mask], trials, seed)[0, 0, 0]
+        pts = orc.mask_points(dim, m, 3, 1.0, mask, c)
+        ATd, Gd, BTd = orc.make_matrices(pts, m, 3)
+        AT, G, BT = (a.astype(np.float32) for a in (ATd, Gd, BTd))
+        a = m + 2
+        num = den = 0.0
+        for t in range(trials):
+            g = np.array([orc.trial_value(seed, dim, m, 3, t, i) for i in range(3 ** dim)], np.float32)
+            d = np.array([orc.trial_value(seed, dim, m, 3, t, 256 + i) for i in range(a ** dim)],
+                         np.float32)
+            if dim == 1:
+                y = orc.direct_f64(d.reshape(1, 1, a), g.reshape(1, 1, 3), 1, 0, 3).ravel()
+                yh = orc.tile_f32(1, AT, G, BT, m, 3, g, d)
+            else:
+                y = orc.direct_f64(d.reshape(1, 1, a, a), g.reshape(1, 1, 3, 3), 2, 0, 3).ravel()
+                yh = orc.tile_f32(2, AT, G, BT, m, 3, g.reshape(3, 3), d.reshape(a, a)).ravel()
+            num += np.abs(yh.astype(np.float64) - y).sum()
+            den += np.abs(y).sum()
+        assert err == pytest.approx(num / den, rel=1e-12)
+
+
+def test_sweep_invalid_and_singular(orc):
+    e = orc.error_sweep([1.0, 1.5], [(1, 4, 3, 1.0)], [0x0F, 0x07], 10, 0)
+    assert math.isinf(e[0, 0, 0])        # c = 1: -c = -1/c coincide
+    assert np.isfinite(e[0, 0, 1])
+    assert np.all(np.isnan(e[0, 1]))     # popcount 3 for alpha - 2 = 4
+
+
+def test_sweep_threads_deterministic(orc):
+    cg = np.geomspace(0.05, 20, 64)
+    e1 = orc.error_sweep(cg, SWEEP_SIZES[:3], [0x06, 0x0F, 0x61], 30, 0, n_threads=1)
+    e4 = orc.error_sweep(cg, SWEEP_SIZES[:3], [0x06, 0x0F, 0x61], 30, 0, n_threads=4)
+    assert np.array_equal(e1, e4, equal_nan=True)
+
+
+def _golden_rows():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = [s.strip() for s in line.split("|")]
+            rows.append(dict(label=p[0], dim=int(p[1]), m=int(p[2]), d=float(p[3]),
+                             mask=None if p[4] == "-" else int(p[4], 16),
+                             c=None if p[5] == "-" else float(p[5]), paper=float(p[6]),
+                             pin=p[7], cite=p[8]))
+    return rows
+
+
+def _mean_abs_y(orc, dim, m, trials, seed):
+    a = m + 2
+    tot = n = 0
+    for t in range(trials):
+        g = np.array([orc.trial_value(seed, dim, m, 3, t, i) for i in range(3 ** dim)], np.float32)
+        d = np.array([orc.trial_value(seed, dim, m, 3, t, 256 + i) for i in range(a ** dim)],
+                     np.float32)
+        if dim == 1:
+            y = orc.direct_f64(d.reshape(1, 1, a), g.reshape(1, 1, 3), 1, 0, 3)
+        else:
+            y = orc.direct_f64(d.reshape(1, 1, a, a), g.reshape(1, 1, 3, 3), 2, 0, 3)
+        tot += np.abs(y).sum()
+        n += y.size
+    return tot / n
+
+
+@pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r["label"])
+def test_paper_printed_errors(orc, row):
+    """Our FP32-vs-FP64 error, in the per-element absolute reading, against
+    the paper's printed value (Huffman order there, plain order here)."""
+    trials, seed = 5000, 0
+    dim, m = row["dim"], row["m"]
+    if row["mask"] is None:
+        rel = orc.direct_error(dim, m, 3, trials, seed)
+    else:
+        rel = orc.error_sweep([row["c"]], [(dim, m, 3, row["d"])], [row["mask"]], trials, seed)[0, 0, 0]
+    ours = rel * _mean_abs_y(orc, dim, m, trials, seed)
+    ratio = ours / row["paper"]
+    if row["pin"] == "tight":
+        assert 0.75 <= ratio <= 1.05, (row["cite"], ours, row["paper"])
+    else:
+        assert 0.5 <= ratio <= 4.0, (row["cite"], ours, row["paper"])
+
+
+@pytest.mark.slow
+def test_f43_error_curve_minimum(orc):
+    """Sec. 6.1: for {-1/c, -c, 0, c, 1/c} with c in [1.1, 2.5] (step 1e-3) the
+    error curve's low region lies around c = 1.6-1.8, rising on both sides.
+    Pinned loosely (plain summation order, not the paper's Huffman order):
+    the smoothed minimum lies in [1.45, 1.9] and both ends are higher."""
+    c = np.round(np.arange(1.1, 2.5 + 1e-9, 1e-3), 6)
+    e = orc.error_sweep(c, [(1, 4, 3, 1.0), (2, 4, 3, 1.0)], [0x0F], 2000, 0, n_threads=8)
+    w = 101
+    for s in range(2):
+        sm = np.convolve(e[s, 0], np.ones(w) / w, mode="valid")
+        cmin = c[w // 2 + int(np.argmin(sm))]
+        assert 1.45 <= cmin <= 1.9, cmin
+        assert sm[0] > sm.min() * 1.05 and sm[-1] > sm.min() * 1.05
+
+
+def test_direct_below_winograd(orc):
+    """Tables 7-8 ordering: direct FP32 < F(2,3) with P4 < F(4,3) < F(6,3)."""
+    e0 = orc.direct_error(1, 2, 3, 2000, 0)
+    e = orc.error_sweep([1.0, 1.829, 2.0], [(1, 2, 3, 1.0), (1, 4, 3, 1.0), (1, 6, 3, 1.0)],
+                        [0x60, 0x0F, 0x6F], 2000, 0)
+    assert e0 < e[0, 0, 0] < e[1, 1, 1] < e[2, 2, 2]
