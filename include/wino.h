@@ -164,9 +164,34 @@ int wino_error_sweep(const double* c_grid, int n_c,
                      int trials, unsigned long long seed,
                      double* err_out, void* cuda_stream);
 
+/* The FP64 transform matrices the sweep builds on the device for the
+ * instances (size, mask, c_k), k < n_c -- the same construction as
+ * wino_make_matrices (Sec. 4.1-4.2), run by the sweep's own device code.
+ * AT[n_c][m][alpha], G[n_c][alpha][r], BT[n_c][alpha][alpha] are caller-owned
+ * HOST arrays; `singular` (host, n_c bytes, may be NULL) receives 1 where two
+ * points coincide.  Returns WINO_EINVAL when the mask is invalid for the size.
+ * Synchronises `cuda_stream`.                                               */
+int wino_instance_matrices(const double* c_grid, int n_c, wino_size size,
+                           unsigned mask, double* AT, double* G, double* BT,
+                           unsigned char* singular, void* cuda_stream);
+
 /* ---------------------------------------------------------------------- */
 /* Library state.                                                           */
 /* ---------------------------------------------------------------------- */
+
+/* Optional CUDA-event timing of the library's kernels: while enabled, every
+ * launch records a start/stop event pair on its own stream (skipped during
+ * graph capture).  wino_profile_read sums, then forgets, the recorded
+ * launches of one kernel ("filter_transform", "input_transform",
+ * "wino_gemm", "output_transform", "fused_layer", "tc_gemm", "tc_transform",
+ * "sweep_eval", "sweep_prepare", "direct_f64", "error_stats", "mlp"); it
+ * waits for the recorded events.                                           */
+int wino_profile_enable(int on);
+int wino_profile_read(const char* kernel, double* total_ms, int* launches);
+
+/* Number of kernels this library has launched in this process (all
+ * devices); a diagnostic for counting launches inside a timed region.      */
+unsigned long long wino_kernel_launches(void);
 
 const char* wino_last_error(void);  /* thread-local message, never NULL  */
 int wino_device_ok(void);           /* 1 when an sm_103 device is usable  */

@@ -1,0 +1,98 @@
+// common.cuh -- internal declarations shared by the library's translation
+// units (not part of the public ABI; see include/wino.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "construct.cuh"
+
+namespace wino {
+
+// FP32 transform matrices of one point set, passed to layer kernels by
+// value (they live in the kernel-parameter constant bank, so unrolled
+// transforms read them as instruction operands).
+constexpr int kMaxR = 7;
+struct LayerMats {
+  float AT[kMaxAlpha * kMaxAlpha];  // [m][alpha]
+  float G[kMaxAlpha * kMaxR];       // [alpha][r]
+  float BT[kMaxAlpha * kMaxAlpha];  // [alpha][alpha]
+  int m, r, alpha;
+};
+
+// Layer geometry (stride 1, zero padding).  dim 1: H = Ho = th = 1.
+struct LayerGeom {
+  int dim, N, C, K, H, W, pad, Ho, Wo, th, tw;
+  int64_t T;  // tiles = N * th * tw
+  int F;      // frequencies = alpha^dim
+};
+
+// Internal return code: "no specialised kernel for this shape, use the
+// general path" (never returned through the ABI).
+constexpr int kFallback = 1;
+
+// Error reporting (thread-local text, see wino_last_error).
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// Counts kernel launches (reported by wino_kernel_launches).
+void note_launches(int n);
+
+// Optional event timing of one kernel launch (profile.cu): construct right
+// before the launch, destroy right after it.
+enum KernelId {
+  kKFilter = 0, kKInput, kKGemm, kKOutput, kKFused, kKTcGemm, kKTcTransform, kKSweepEval,
+  kKSweepPrep, kKDirect, kKStats, kKMlp, kNumKernelIds
+};
+class ProfScope {
+ public:
+  ProfScope(int id, cudaStream_t st);
+  ~ProfScope();
+
+ private:
+  int id_;
+  cudaStream_t st_;
+  void* a_;
+};
+
+// Scratch owned by the library (grow-only, per purpose and device).
+enum ScratchSlot { kScratchLayer = 0, kScratchSweep = 1, kScratchStats = 2, kScratchTC = 3,
+                   kScratchMLP = 4, kNumScratch = 5 };
+int scratch_get(int slot, size_t bytes, void** ptr);
+
+// ---- layer path (layer.cu) ----------------------------------------------
+size_t layer_workspace_bytes(const LayerGeom& g, int dtype);
+int layer_forward_f32(const float* x, const float* w, float* y, const LayerGeom& g,
+                      const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// ---- precision form (tc_gemm.cu) ----------------------------------------
+int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& g,
+                     const LayerMats& M, int dtype, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// ---- references and reductions (reference.cu) ---------------------------
+int direct_conv_f64(const float* x, const float* w, double* y, int dim, int N, int C, int K,
+                    int H, int W, int pad, int r, cudaStream_t st);
+int error_stats(const float* yhat, const double* y, int64_t n, double* out4_host,
+                cudaStream_t st);
+
+// ---- sweep (sweep.cu) -----------------------------------------------------
+struct SweepSize {
+  int dim, m, r;
+  double d;
+};
+int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_sizes,
+                const unsigned char* subsets, int n_subsets, int trials, unsigned long long seed,
+                double* err_out, cudaStream_t st);
+int instance_matrices(const double* c_grid, int n_c, const SweepSize& s, unsigned mask,
+                      double* AT, double* G, double* BT, unsigned char* singular,
+                      cudaStream_t st);
+
+}  // namespace wino
+
+#define WINO_CUDA_TRY(expr)                               \
+  do {                                                    \
+    cudaError_t e__ = (expr);                             \
+    if (e__ != cudaSuccess) return ::wino::cuda_fail(e__, #expr); \
+  } while (0)

@@ -1,0 +1,152 @@
+// reference.cu -- the FP64 steps of the method: direct correlation (Eq. (1))
+// as the reference FP32 Winograd is measured against (Sec. 6), and the
+// error reduction (sum and max of |yhat - y| and |y|) with FP64 warp-shuffle
+// accumulators.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/wino.h"
+#include "common.cuh"
+
+namespace wino {
+
+// K5: one thread per output (n, k, p, q), q fastest: neighbouring threads
+// read neighbouring input columns, the filter tap is warp-uniform.
+__global__ void k_direct_f64(const float* __restrict__ x, const float* __restrict__ w,
+                             double* __restrict__ y, int N, int C, int K, int H, int W, int pad,
+                             int rh, int r, int padh, int Ho, int Wo) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)N * K * Ho * Wo;
+  if (idx >= total) return;
+  const int q = (int)(idx % Wo);
+  const int p = (int)((idx / Wo) % Ho);
+  const int k = (int)((idx / ((int64_t)Wo * Ho)) % K);
+  const int n = (int)(idx / ((int64_t)Wo * Ho * K));
+  double acc = 0.0;
+  for (int c = 0; c < C; ++c) {
+    const float* xc = x + ((int64_t)n * C + c) * H * W;
+    const float* wk = w + ((int64_t)k * C + c) * rh * r;
+    for (int u = 0; u < rh; ++u) {
+      const int hh = p + u - padh;
+      if (hh < 0 || hh >= H) continue;
+      for (int v = 0; v < r; ++v) {
+        const int ww = q + v - pad;
+        if (ww < 0 || ww >= W) continue;
+        acc = fma((double)__ldg(xc + (int64_t)hh * W + ww), (double)__ldg(wk + u * r + v), acc);
+      }
+    }
+  }
+  y[idx] = acc;
+}
+
+int direct_conv_f64(const float* x, const float* w, double* y, int dim, int N, int C, int K,
+                    int H, int W, int pad, int r, cudaStream_t st) {
+  const int rh = (dim == 1) ? 1 : r;
+  const int padh = (dim == 1) ? 0 : pad;
+  const int Hin = (dim == 1) ? 1 : H;
+  const int Ho = (dim == 1) ? 1 : H + 2 * pad - r + 1;
+  const int Wo = W + 2 * pad - r + 1;
+  const int64_t total = (int64_t)N * K * Ho * Wo;
+  if (total == 0) return WINO_OK;
+  ProfScope ps(kKDirect, st);
+  k_direct_f64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(x, w, y, N, C, K, Hin, W, pad,
+                                                                 rh, r, padh, Ho, Wo);
+  note_launches(1);
+  WINO_CUDA_TRY(cudaGetLastError());
+  return WINO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// K6: error statistics.  Pass 1: grid-stride per-thread FP64 partials,
+// warp-shuffle then shared-memory reduction, one record per block.  Pass 2:
+// one block reduces the records in a fixed order, so the result does not
+// depend on scheduling.
+// ---------------------------------------------------------------------------
+struct Stats4 {
+  double s_err, s_ref, m_err, m_ref;
+};
+
+__device__ __forceinline__ Stats4 warp_reduce(Stats4 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.s_err += __shfl_down_sync(0xffffffffu, v.s_err, o);
+    v.s_ref += __shfl_down_sync(0xffffffffu, v.s_ref, o);
+    v.m_err = fmax(v.m_err, __shfl_down_sync(0xffffffffu, v.m_err, o));
+    v.m_ref = fmax(v.m_ref, __shfl_down_sync(0xffffffffu, v.m_ref, o));
+  }
+  return v;
+}
+
+__device__ __forceinline__ Stats4 block_reduce(Stats4 v) {
+  __shared__ Stats4 part[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_reduce(v);
+  if (lane == 0) part[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (wid == 0) {
+    v = (lane < nw) ? part[lane] : Stats4{0.0, 0.0, 0.0, 0.0};
+    v = warp_reduce(v);
+  }
+  return v;
+}
+
+__global__ void k_error_stats_pass1(const float* __restrict__ yhat, const double* __restrict__ y,
+                                    int64_t n, Stats4* __restrict__ partial) {
+  Stats4 v{0.0, 0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double ref = y[i];
+    const double e = fabs((double)yhat[i] - ref);
+    v.s_err += e;
+    v.s_ref += fabs(ref);
+    v.m_err = fmax(v.m_err, e);
+    v.m_ref = fmax(v.m_ref, fabs(ref));
+  }
+  v = block_reduce(v);
+  if (threadIdx.x == 0) partial[blockIdx.x] = v;
+}
+
+__global__ void k_error_stats_pass2(const Stats4* __restrict__ partial, int nb,
+                                    double* __restrict__ out) {
+  Stats4 v{0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    const Stats4 p = partial[i];
+    v.s_err += p.s_err;
+    v.s_ref += p.s_ref;
+    v.m_err = fmax(v.m_err, p.m_err);
+    v.m_ref = fmax(v.m_ref, p.m_ref);
+  }
+  v = block_reduce(v);
+  if (threadIdx.x == 0) {
+    out[0] = v.s_err;
+    out[1] = v.s_ref;
+    out[2] = v.m_err;
+    out[3] = v.m_ref;
+  }
+}
+
+int error_stats(const float* yhat, const double* y, int64_t n, double* out4_host,
+                cudaStream_t st) {
+  int sms = 0, dev = 0;
+  WINO_CUDA_TRY(cudaGetDevice(&dev));
+  WINO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int64_t want = (n + 255) / 256;
+  int nb = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
+  if (nb < 1) nb = 1;
+  void* buf = nullptr;
+  int rc = scratch_get(kScratchStats, sizeof(Stats4) * nb + 64, &buf);
+  if (rc != WINO_OK) return rc;
+  Stats4* partial = (Stats4*)buf;
+  double* out = (double*)((char*)buf + sizeof(Stats4) * nb);
+  k_error_stats_pass1<<<nb, 256, 0, st>>>(yhat, y, n, partial);
+  k_error_stats_pass2<<<1, 256, 0, st>>>(partial, nb, out);
+  note_launches(2);
+  WINO_CUDA_TRY(cudaGetLastError());
+  WINO_CUDA_TRY(cudaMemcpyAsync(out4_host, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WINO_CUDA_TRY(cudaStreamSynchronize(st));
+  return WINO_OK;
+}
+
+}  // namespace wino

@@ -1,0 +1,77 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every
+symbol include/wino.h declares, and its host-only logic (FP64 matrix
+construction, argument validation) behaves.  No device compute here."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2201_10369_gb300 as w
+    w.build()
+    return w
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(wino_[a-z0-9_]+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "wino_conv2d" in names and "wino_error_sweep" in names and len(names) >= 12
+    L = lib.load()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("m,r", [(2, 3), (4, 3), (6, 3), (8, 3), (2, 5), (6, 5)])
+def test_host_matrices_match_oracle(lib, orc, m, r):
+    """Host FP64 construction vs the oracle's: same definition, same rounding
+    order, so bit-identical (the parity bar is 1e-13 relative)."""
+    rng = np.random.default_rng(m * 10 + r)
+    pts = list(rng.uniform(-3, 3, m + r - 2)) + [math.inf]
+    got = lib.wino_make_matrices(pts, m, r)
+    want = orc.make_matrices(pts, m, r)
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
+
+
+def test_host_validation(lib):
+    with pytest.raises(lib.WinoError) as e:
+        lib.wino_make_matrices([0.0, 1.0, 1.0, math.inf], 2, 3)
+    assert e.value.status == lib.WINO_ESINGULAR
+    for bad in ([0.0, 1.0, -1.0, 2.0], [0.0, math.nan, 1.0, math.inf], [0.0, -math.inf, 1, 2]):
+        with pytest.raises(lib.WinoError) as e:
+            lib.wino_make_matrices(bad, 2, 3)
+        assert e.value.status == lib.WINO_EINVAL
+    assert lib.wino_workspace_bytes(1, 8, 8, 16, 16, 2, 3) > 0
+    assert lib.wino_workspace_bytes(1, 8, 8, 2, 2, 2, 9) == 0
+
+
+def test_no_cpu_fallback(lib):
+    """Without a GPU every device entry point refuses (WINO_EUNSUPPORTED)
+    instead of computing anything on the CPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert not lib.wino_device_ok()
+    L = lib.load()
+    pts = np.array([0.0, 1.0, -1.0, math.inf])
+    st = L.wino_conv2d(16, 16, 16, 1, 2, 2, 8, 8, 1, pts.ctypes.data_as(lib._DP), 2, 3, 0, None)
+    assert st == lib.WINO_EUNSUPPORTED
+    with pytest.raises(lib.WinoError) as e:
+        lib.wino_error_sweep([1.5], [(1, 2, 3, 1.0)], [0x06], 10, 0, stream=0)
+    assert e.value.status == lib.WINO_EUNSUPPORTED

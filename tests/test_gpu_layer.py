@@ -1,0 +1,114 @@
+"""GPU parity of the Winograd layer (wino_conv2d / wino_conv1d, FP32 form)
+and of the FP64 reference / error-reduction kernels, through the C ABI,
+element by element against the CPU oracle on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2201_10369_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LAVIN = [0.0, 1.0, -1.0, math.inf]
+
+
+def full_group(c, extra=()):
+    return [0.0, -1 / c, -c, c, 1 / c, *extra, math.inf]
+
+
+POINTS = {
+    2: LAVIN,
+    4: full_group(1.622),
+    6: full_group(2.0, (-1.0, 1.0)),  # P8 = {0, +-1/2, +-1, +-2, inf}
+}
+
+
+def _run2d(wino, x, w, pts, m, pad, dtype="f32"):
+    import torch
+    xt = torch.from_numpy(x).cuda()
+    wt = torch.from_numpy(w).cuda()
+    N, C, H, W = x.shape
+    K, r = w.shape[0], w.shape[-1]
+    y = torch.full((N, K, H + 2 * pad - r + 1, W + 2 * pad - r + 1), float("nan"),
+                   device="cuda")
+    wino.wino_conv2d(xt, wt, y, pts, m, r, pad, dtype)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def test_config1_f2x2_layer(wino, orc):
+    """F(2x2,3x3), points {0,1,-1,inf}, N=1, C=K=8, 16x16, pad 1, uniform
+    inputs from seed 0: bit-identical to the oracle, and at the FP32 error
+    scale against FP64 direct correlation."""
+    x, w = inputs.layer_uniform(1, 8, 8, 16, 16, seed=0)
+    y = _run2d(wino, x, w, LAVIN, 2, 1)
+    yo = orc.wino_layer(x, w, 2, 1, LAVIN, 2, 3)
+    assert np.array_equal(y, yo)
+    ref = orc.direct_f64(x, w, 2, 1, 3)
+    rel = np.abs(y - ref).sum() / np.abs(ref).sum()
+    assert rel < 1e-6
+    assert np.abs(y - ref).max() / np.abs(ref).max() < 2e-6
+
+
+@pytest.mark.parametrize("m", [2, 4, 6])
+@pytest.mark.parametrize("shape", [(2, 5, 3, 15, 17, 1), (1, 16, 70, 9, 8, 2), (1, 1, 1, 3, 3, 0),
+                                   (3, 9, 12, 13, 6, 1)])
+def test_layer_bitwise_vs_oracle(wino, orc, m, shape):
+    """Ragged tiles, channel counts off the kernels' blocking, padding 0-2."""
+    N, C, K, H, W, pad = shape
+    x, w = inputs.layer_uniform(N, C, K, H, W, seed=m)
+    y = _run2d(wino, x, w, POINTS[m], m, pad)
+    yo = orc.wino_layer(x, w, 2, pad, POINTS[m], m, 3)
+    assert np.array_equal(y, yo)
+
+
+@pytest.mark.parametrize("m,r", [(2, 3), (4, 3), (6, 3), (3, 5)])
+def test_layer_1d_bitwise_vs_oracle(wino, orc, m, r):
+    import torch
+    x, w = inputs.layer_uniform(3, 7, 5, 1, 29, r=r, seed=11, dim=1)
+    pts = [0.0, -1.5, 1.5, -1 / 1.5, 1 / 1.5, -1.0, 1.0, 2.5][: m + r - 2] + [math.inf]
+    pad = 1
+    y = torch.full((3, 5, 29 + 2 * pad - r + 1), float("nan"), device="cuda")
+    wino.wino_conv1d(torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda(), y, pts, m, r, pad)
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), orc.wino_layer(x, w, 1, pad, pts, m, r))
+
+
+def test_layer_degenerate_inputs(wino):
+    import torch
+    x = torch.zeros((0, 4, 8, 8), device="cuda")
+    w = torch.zeros((4, 4, 3, 3), device="cuda")
+    y = torch.zeros((0, 4, 8, 8), device="cuda")
+    wino.wino_conv2d(x, w, y, LAVIN, 2, 3, 1)  # N = 0: nothing to do
+    with pytest.raises(wino.WinoError) as e:
+        wino.wino_conv2d(torch.zeros((1, 4, 8, 8), device="cuda"), w,
+                         torch.zeros((1, 4, 8, 8), device="cuda"), [0.0, 1.0, 1.0, math.inf], 2, 3)
+    assert e.value.status == wino.WINO_ESINGULAR
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_direct_f64_vs_oracle(wino, orc, dim):
+    import torch
+    if dim == 2:
+        x, w = inputs.layer_uniform(2, 6, 5, 13, 11, seed=3)
+    else:
+        x, w = inputs.layer_uniform(2, 6, 5, 1, 40, seed=3, dim=1)
+    ref = orc.direct_f64(x, w, dim, 1, 3)
+    y64 = torch.zeros(ref.shape, dtype=torch.float64, device="cuda")
+    wino.wino_direct_conv_f64(torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda(), y64, 1)
+    torch.cuda.synchronize()
+    got = y64.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_error_stats_vs_numpy(wino):
+    import torch
+    rng = np.random.default_rng(5)
+    y = rng.normal(0, 1, 1_000_003)
+    yh = (y + rng.normal(0, 1e-6, y.size)).astype(np.float32)
+    got = wino.wino_error_stats(torch.from_numpy(yh).cuda(), torch.from_numpy(y).cuda())
+    e = np.abs(yh.astype(np.float64) - y)
+    want = (e.sum(), np.abs(y).sum(), e.max(), np.abs(y).max())
+    for a, b in zip(got, want):
+        assert a == pytest.approx(b, rel=1e-12)
