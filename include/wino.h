@@ -176,6 +176,53 @@ int wino_instance_matrices(const double* c_grid, int n_c, wino_size size,
                            unsigned char* singular, void* cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* Planned sweep: one persistent launch in a CUDA graph (Sec. 6.2-6.3      */
+/* searches run as explicit instance lists).                               */
+/* ---------------------------------------------------------------------- */
+
+/* One instance: sizes[size] with the point set of `mask` at parameter c
+ * (same point rule as wino_error_sweep).                                    */
+typedef struct {
+  int size;
+  unsigned char mask;
+  double c;
+} wino_instance;
+
+enum {
+  WINO_SWEEP_AUTO = 0,         /* time the modes below once, keep the best */
+  WINO_SWEEP_PERSISTENT = 1,   /* one persistent launch, LPT work queue    */
+  WINO_SWEEP_PERSISTENT3 = 2,  /* same, 3 CTAs/SM (register-capped)        */
+  WINO_SWEEP_PER_SIZE = 3      /* one launch per size                      */
+};
+
+/* Builds a plan evaluating every instance with `trials` trials of `seed`
+ * (the same trial inputs and metric as wino_error_sweep), captures it in a
+ * CUDA graph on the current device and returns an opaque handle in *plan.
+ * Instances whose mask is invalid for their size are not evaluated (NaN).
+ * With mode WINO_SWEEP_AUTO the call first times each mode on this plan
+ * (cached per plan shape for the process).  Allocates device and pinned host
+ * memory owned by the plan.                                                */
+int wino_sweep_plan_create(const wino_size* sizes, int n_sizes,
+                           const wino_instance* inst, int64_t n_inst,
+                           int trials, unsigned long long seed, int mode,
+                           void** plan);
+
+/* Optional watchdog: a later run stops taking work `max_ms` milliseconds of
+ * device time after its launch and returns WINO_ETIMEOUT (instances not
+ * reached are NaN).  0 disables it.                                         */
+int wino_sweep_plan_set_deadline(void* plan, double max_ms);
+
+/* Launches the plan's graph on `cuda_stream` (NULL = the plan's own stream),
+ * waits for it and writes err_out[n_inst] (host, FP64) in the caller's
+ * instance order.                                                          */
+int wino_sweep_plan_run(void* plan, double* err_out, void* cuda_stream);
+
+/* The mode the plan runs, its persistent grid size and its work items.    */
+int wino_sweep_plan_info(void* plan, int* mode, int* grid, int* n_items);
+
+void wino_sweep_plan_destroy(void* plan);
+
+/* ---------------------------------------------------------------------- */
 /* Library state.                                                           */
 /* ---------------------------------------------------------------------- */
 

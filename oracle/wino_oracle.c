@@ -677,3 +677,127 @@ double orc_direct_error(int dim, int m, int r, int trials, uint64_t seed) {
   free(sd.g); free(sd.d); free(sd.y);
   return e;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Selected tiles of the FP32 Winograd layer (for full-size spot checks).   */
+/* Same operation order as orc_wino_layer (f32 contraction only).           */
+/* ------------------------------------------------------------------------ */
+
+static void filter_one(int dim, int A, int r, const float* G, const float* g, float* out) {
+  if (dim == 1) {
+    for (int i = 0; i < A; ++i) {
+      float acc = 0.0f;
+      for (int q = 0; q < r; ++q) acc = fmaf(G[i * r + q], g[q], acc);
+      out[i] = acc;
+    }
+    return;
+  }
+  float Wk[ORC_MAX_ALPHA * 5];
+  for (int i = 0; i < A; ++i)
+    for (int q = 0; q < r; ++q) {
+      float acc = 0.0f;
+      for (int l = 0; l < r; ++l) acc = fmaf(G[i * r + l], g[l * r + q], acc);
+      Wk[i * r + q] = acc;
+    }
+  for (int i = 0; i < A; ++i)
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+      for (int q = 0; q < r; ++q) acc = fmaf(Wk[i * r + q], G[j * r + q], acc);
+      out[i * A + j] = acc;
+    }
+}
+
+static void input_one(int dim, int A, const float* BT, const float* d, float* out) {
+  if (dim == 1) {
+    for (int i = 0; i < A; ++i) {
+      float acc = 0.0f;
+      for (int l = 0; l < A; ++l) acc = fmaf(BT[i * A + l], d[l], acc);
+      out[i] = acc;
+    }
+    return;
+  }
+  float Tm[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int i = 0; i < A; ++i)
+    for (int l = 0; l < A; ++l) {
+      float acc = 0.0f;
+      for (int q = 0; q < A; ++q) acc = fmaf(BT[i * A + q], d[q * A + l], acc);
+      Tm[i * A + l] = acc;
+    }
+  for (int i = 0; i < A; ++i)
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+      for (int l = 0; l < A; ++l) acc = fmaf(Tm[i * A + l], BT[j * A + l], acc);
+      out[i * A + j] = acc;
+    }
+}
+
+int orc_wino_layer_tiles(const float* x, const float* w, int dim, int N, int C, int K, int H,
+                         int W, int pad, const double* points, int m, int r, int n_sel,
+                         const int64_t* sel, float* out) {
+  const int A = m + r - 1;
+  double ATd[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Gd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  double BTd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  int st = orc_make_matrices(points, m, r, ATd, Gd, BTd);
+  if (st < 0) return st;
+  float AT[ORC_MAX_ALPHA * ORC_MAX_ALPHA], G[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float BT[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int i = 0; i < m * A; ++i) AT[i] = (float)ATd[i];
+  for (int i = 0; i < A * r; ++i) G[i] = (float)Gd[i];
+  for (int i = 0; i < A * A; ++i) BT[i] = (float)BTd[i];
+  const int Hin = (dim == 1) ? 1 : H;
+  const int Ho = (dim == 1) ? 1 : H + 2 * pad - r + 1;
+  const int Wo = W + 2 * pad - r + 1;
+  const int padh = (dim == 1) ? 0 : pad;
+  const int th = (dim == 1) ? 1 : (Ho + m - 1) / m;
+  const int tw = (Wo + m - 1) / m;
+  const int F = (dim == 1) ? A : A * A;
+  const int rw = (dim == 1) ? r : r * r;
+  const int no = (dim == 1) ? m : m * m;
+  float d[ORC_MAX_ALPHA * ORC_MAX_ALPHA], U[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float Vf[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Mf[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int s = 0; s < n_sel; ++s) {
+    const int64_t t = sel[2 * s];
+    const int k = (int)sel[2 * s + 1];
+    const int n = (int)(t / ((int64_t)th * tw));
+    const int ti = (int)((t / tw) % th), tj = (int)(t % tw);
+    if (n < 0 || n >= N || k < 0 || k >= K) return -1;
+    for (int f = 0; f < F; ++f) Mf[f] = 0.0f;
+    for (int c = 0; c < C; ++c) {
+      const int pr = (dim == 1) ? 1 : A;
+      for (int i = 0; i < pr; ++i)
+        for (int j = 0; j < A; ++j) {
+          int hh = ti * m - padh + i, ww = tj * m - pad + j;
+          float v = 0.0f;
+          if (hh >= 0 && hh < Hin && ww >= 0 && ww < W)
+            v = x[(((size_t)n * C + c) * Hin + hh) * W + ww];
+          d[i * A + j] = v;
+        }
+      input_one(dim, A, BT, d, U);
+      filter_one(dim, A, r, G, w + ((size_t)k * C + c) * rw, Vf);
+      for (int f = 0; f < F; ++f) Mf[f] = fmaf(U[f], Vf[f], Mf[f]);
+    }
+    float* o = out + (size_t)s * no;
+    if (dim == 1) {
+      for (int j = 0; j < m; ++j) {
+        float acc = 0.0f;
+        for (int i = 0; i < A; ++i) acc = fmaf(AT[j * A + i], Mf[i], acc);
+        o[j] = acc;
+      }
+    } else {
+      float Z[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+      for (int a = 0; a < m; ++a)
+        for (int j = 0; j < A; ++j) {
+          float acc = 0.0f;
+          for (int i = 0; i < A; ++i) acc = fmaf(AT[a * A + i], Mf[i * A + j], acc);
+          Z[a * A + j] = acc;
+        }
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+          float acc = 0.0f;
+          for (int j = 0; j < A; ++j) acc = fmaf(Z[a * A + j], AT[b * A + j], acc);
+          o[a * m + b] = acc;
+        }
+    }
+  }
+  return 0;
+}

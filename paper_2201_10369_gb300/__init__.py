@@ -38,6 +38,13 @@ class WinoSize(ctypes.Structure):
                 ("d", ctypes.c_double)]
 
 
+class WinoInstance(ctypes.Structure):
+    """One planned-sweep instance: size index, subset mask, parameter c."""
+    _fields_ = [("size", ctypes.c_int), ("mask", ctypes.c_ubyte), ("c", ctypes.c_double)]
+
+
+WINO_SWEEP_AUTO, WINO_SWEEP_PERSISTENT, WINO_SWEEP_PERSISTENT3, WINO_SWEEP_PER_SIZE = 0, 1, 2, 3
+
 _lib = None
 _lock = threading.Lock()
 _i, _d, _vp, _sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
@@ -59,6 +66,18 @@ def _declare(L):
     L.wino_instance_matrices.argtypes = [_DP, _i, WinoSize, ctypes.c_uint, _DP, _DP, _DP,
                                          ctypes.POINTER(ctypes.c_ubyte), _vp]
     L.wino_instance_matrices.restype = _i
+    L.wino_sweep_plan_create.argtypes = [ctypes.POINTER(WinoSize), _i,
+                                         ctypes.POINTER(WinoInstance), ctypes.c_int64, _i,
+                                         ctypes.c_ulonglong, _i, ctypes.POINTER(_vp)]
+    L.wino_sweep_plan_create.restype = _i
+    L.wino_sweep_plan_set_deadline.argtypes = [_vp, _d]
+    L.wino_sweep_plan_set_deadline.restype = _i
+    L.wino_sweep_plan_run.argtypes = [_vp, _DP, _vp]
+    L.wino_sweep_plan_run.restype = _i
+    L.wino_sweep_plan_info.argtypes = [_vp] + [ctypes.POINTER(_i)] * 3
+    L.wino_sweep_plan_info.restype = _i
+    L.wino_sweep_plan_destroy.argtypes = [_vp]
+    L.wino_sweep_plan_destroy.restype = None
     L.wino_profile_enable.argtypes = [_i]
     L.wino_profile_enable.restype = _i
     L.wino_profile_read.argtypes = [ctypes.c_char_p, _DP, ctypes.POINTER(ctypes.c_int)]
@@ -249,6 +268,59 @@ def wino_instance_matrices(c_grid, size, mask: int, stream=None):
                                     sing.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
                                     _stream(stream)))
     return AT, G, BT, sing.astype(bool)
+
+
+class SweepPlan:
+    """A planned sweep (wino_sweep_plan_*): build once, run many times.
+
+    ``instances`` is a sequence of (size index, mask, c); ``run()`` returns the
+    errors in that order (NaN where the mask is invalid for its size)."""
+
+    def __init__(self, sizes, instances, trials: int, seed: int = 0, mode: int = WINO_SWEEP_AUTO):
+        L = load()
+        self._L = L
+        sz = (WinoSize * len(sizes))(*[WinoSize(int(a), int(b), int(c), float(d))
+                                       for a, b, c, d in sizes])
+        n = len(instances)
+        arr = (WinoInstance * n)()
+        for i, (s, mk, c) in enumerate(instances):
+            arr[i].size, arr[i].mask, arr[i].c = int(s), int(mk), float(c)
+        h = ctypes.c_void_p()
+        _check(L.wino_sweep_plan_create(sz, len(sizes), arr, n, trials, seed, mode,
+                                        ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    def set_deadline(self, max_ms: float):
+        _check(self._L.wino_sweep_plan_set_deadline(self._h, float(max_ms)))
+
+    def run(self, stream=None) -> np.ndarray:
+        err = np.empty(self.n)
+        st = 0 if stream is None else _stream(stream)
+        _check(self._L.wino_sweep_plan_run(self._h, err.ctypes.data_as(_DP), st or None))
+        return err
+
+    def info(self):
+        m, g, n = _i(), _i(), _i()
+        _check(self._L.wino_sweep_plan_info(self._h, ctypes.byref(m), ctypes.byref(g),
+                                            ctypes.byref(n)))
+        return {"mode": m.value, "grid": g.value, "items": n.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.wino_sweep_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid_instances(sizes, masks, c_grid):
+    """All (size, mask, c) of a full grid, in [size][mask][c] order."""
+    return [(s, int(mk), float(c)) for s in range(len(sizes)) for mk in masks for c in c_grid]
 
 
 def wino_kernel_launches() -> int:

@@ -8,20 +8,17 @@
 // Device work per size:
 //   k_sweep_prepare  one thread per trial: draws g, d (SplitMix64 counter
 //                    stream), computes the FP64 direct correlation y of the
-//                    tile and stores one record per trial
-//                    [g | d | hi(y) | lo(y)]  (hi = RN32(y), lo = RN32(y - hi))
-//                    plus per-block FP64 partial sums of |y|;
-//   k_sweep_ysum     fixed-order reduction of the partials -> sum_t ||y_t||_1;
+//                    tile, stores the trial record (sweep_eval.cuh) and a
+//                    per-block FP64 partial sum of |y|;
+//   k_sweep_ysum     fixed-order total of the partials -> sum_t ||y_t||_1;
 //   k_sweep_eval     one warp per (mask, 32 consecutive c): each lane builds
-//                    its instance's matrices in FP64 (Sec. 4.1-4.2), rounds
-//                    them once to FP32 into registers, and runs all trials
-//                    with the FP32 Winograd tile; the trial records are
-//                    warp-uniform loads.  Per trial the lane sums
-//                    |(yhat - hi) - lo| over the m (m^2) outputs in FP32
-//                    and adds that to an FP64 accumulator.
+//                    its instance's matrices in FP64, rounds them once to
+//                    FP32 into registers and runs all trials with the FP32
+//                    Winograd tile; trial records are warp-uniform loads.
 // The FP32 tile follows the library's fixed operation order (fmaf over the
 // inner index ascending, one rounded Hadamard multiply), so yhat is
-// bit-identical to any implementation of the same order.
+// bit-identical to any implementation of the same order.  sweep_plan.cu
+// runs the same evaluation as one persistent launch over all sizes.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -31,6 +28,7 @@
 
 #include "../../include/wino.h"
 #include "common.cuh"
+#include "sweep_eval.cuh"
 
 namespace wino {
 
@@ -56,25 +54,6 @@ __device__ __forceinline__ float trial_value(uint64_t seed, int dim, int m, int 
   ctr += (uint64_t)idx;
   const uint64_t z = splitmix64_at(seed, ctr + 1u);
   return (float)((int)(z >> 40)) * 0x1p-23f - 1.0f;  // exact: k < 2^24
-}
-
-__host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
-
-struct SizeShape {
-  int dim, m, r, alpha, nin_g, nin_d, nout, rec;
-};
-
-static SizeShape shape_of(int dim, int m, int r) {
-  SizeShape s;
-  s.dim = dim;
-  s.m = m;
-  s.r = r;
-  s.alpha = m + r - 1;
-  s.nin_g = dim == 1 ? r : r * r;
-  s.nin_d = dim == 1 ? s.alpha : s.alpha * s.alpha;
-  s.nout = dim == 1 ? m : m * m;
-  s.rec = round4(s.nin_g + s.nin_d + 2 * s.nout);
-  return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -111,7 +90,7 @@ __global__ void k_sweep_prepare(float* __restrict__ rec, double* __restrict__ pa
     }
     for (int i = ng + nd + 2 * no; i < recw; ++i) out[i] = 0.0f;
   }
-  // block partial of |y| (warp shuffle, then lane 0 of each warp in order)
+  // block partial of |y| (warp shuffle, then the warps' sums in order)
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   __shared__ double ws[32];
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
@@ -131,120 +110,18 @@ __global__ void k_sweep_ysum(const double* __restrict__ partial, int nb, double*
   }
 }
 
-// ---------------------------------------------------------------------------
-// Register-resident FP32 tile evaluation (compile-time sizes).
-// ---------------------------------------------------------------------------
-template <int M, int R>
-struct Mats {
-  static constexpr int A = M + R - 1;
-  float AT[M * A], G[A * R], BT[A * A];
-};
-
-// Builds the instance matrices (FP64, rounded once) into registers.
-// Returns false for coinciding points.
-template <int M, int R>
-__device__ __forceinline__ bool build_instance(unsigned mask, double c, double d, Mats<M, R>& Mx) {
-  constexpr int A = M + R - 1;
-  double pts[kMaxAlpha];
-  mask_points(mask, A, c, d, pts);
-  double ATd[M * A], Gd[A * R], BTd[A * A];
-  const bool ok = build_matrices<double>(pts, M, R, ATd, Gd, BTd);
-#pragma unroll
-  for (int i = 0; i < M * A; ++i) Mx.AT[i] = __double2float_rn(ATd[i]);
-#pragma unroll
-  for (int i = 0; i < A * R; ++i) Mx.G[i] = __double2float_rn(Gd[i]);
-#pragma unroll
-  for (int i = 0; i < A * A; ++i) Mx.BT[i] = __double2float_rn(BTd[i]);
-  return ok;
-}
-
-// |yhat - y| summed over the tile, y = hi + lo; FP32.
-__device__ __forceinline__ float abs_err(float yhat, float hi, float lo) {
-  return fabsf(__fsub_rn(__fsub_rn(yhat, hi), lo));
-}
-
-// 1D F(m, r): u = G g, v = BT d, p = u .* v, y = AT p  (Eq. (8)).
-template <int M, int R>
-__device__ __forceinline__ float tile_err_1d(const Mats<M, R>& Mx, const float* __restrict__ rc) {
-  constexpr int A = M + R - 1;
-  const float* g = rc;
-  const float* d = rc + R;
-  const float* yh = d + A;
-  const float* yl = yh + M;
-  float p[A];
-#pragma unroll
-  for (int i = 0; i < A; ++i) {
-    float u = 0.0f, v = 0.0f;
-#pragma unroll
-    for (int k = 0; k < R; ++k) u = fmaf(Mx.G[i * R + k], g[k], u);
-#pragma unroll
-    for (int l = 0; l < A; ++l) v = fmaf(Mx.BT[i * A + l], d[l], v);
-    p[i] = __fmul_rn(u, v);
+int sweep_prepare(float* rec, double* partial, double* ysum, int dim, int m, int r, int trials,
+                  uint64_t seed, cudaStream_t st) {
+  const int nb = sweep_prepare_blocks(trials);
+  {
+    ProfScope ps(kKSweepPrep, st);
+    k_sweep_prepare<<<nb, 256, 0, st>>>(rec, partial, dim, m, r, trials,
+                                        sweep_rec_width(dim, m, r), seed);
   }
-  float e = 0.0f;
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    float y = 0.0f;
-#pragma unroll
-    for (int i = 0; i < A; ++i) y = fmaf(Mx.AT[j * A + i], p[i], y);
-    e = __fadd_rn(e, abs_err(y, yh[j], yl[j]));
-  }
-  return e;
-}
-
-// 2D F(m x m, r x r), Eq. (9), streamed one frequency row i at a time:
-//   W_i = G_i g, U_i = W_i G^T, T_i = BT_i d, V_i = T_i B, P_i = U_i .* V_i,
-//   Z += AT[:, i] P_i  (i ascending),  then Y = Z A.
-template <int M, int R>
-__device__ __forceinline__ float tile_err_2d(const Mats<M, R>& Mx, const float* __restrict__ rc) {
-  constexpr int A = M + R - 1;
-  const float* g = rc;
-  const float* d = rc + R * R;
-  const float* yh = d + A * A;
-  const float* yl = yh + M * M;
-  float Z[M * A];
-#pragma unroll
-  for (int i = 0; i < A; ++i) {
-    float Wi[R], Ti[A];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int l = 0; l < R; ++l) acc = fmaf(Mx.G[i * R + l], g[l * R + k], acc);
-      Wi[k] = acc;
-    }
-#pragma unroll
-    for (int l = 0; l < A; ++l) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int k = 0; k < A; ++k) acc = fmaf(Mx.BT[i * A + k], d[k * A + l], acc);
-      Ti[l] = acc;
-    }
-#pragma unroll
-    for (int j = 0; j < A; ++j) {
-      float u = 0.0f, v = 0.0f;
-#pragma unroll
-      for (int k = 0; k < R; ++k) u = fmaf(Wi[k], Mx.G[j * R + k], u);
-#pragma unroll
-      for (int l = 0; l < A; ++l) v = fmaf(Ti[l], Mx.BT[j * A + l], v);
-      const float p = __fmul_rn(u, v);
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-        Z[a * A + j] = (i == 0) ? fmaf(Mx.AT[a * A + i], p, 0.0f)
-                                : fmaf(Mx.AT[a * A + i], p, Z[a * A + j]);
-    }
-  }
-  float e = 0.0f;
-#pragma unroll
-  for (int a = 0; a < M; ++a)
-#pragma unroll
-    for (int b = 0; b < M; ++b) {
-      float y = 0.0f;
-#pragma unroll
-      for (int j = 0; j < A; ++j) y = fmaf(Z[a * A + j], Mx.AT[b * A + j], y);
-      e = __fadd_rn(e, abs_err(y, yh[a * M + b], yl[a * M + b]));
-    }
-  return e;
+  k_sweep_ysum<<<1, 32, 0, st>>>(partial, nb, ysum);
+  note_launches(2);
+  WINO_CUDA_TRY(cudaGetLastError());
+  return WINO_OK;
 }
 
 struct MaskList {
@@ -260,11 +137,6 @@ __global__ void __launch_bounds__(128) k_sweep_eval(const float* __restrict__ re
                                                     double d, const MaskList masks,
                                                     const double* __restrict__ ysum,
                                                     double* __restrict__ err) {
-  constexpr int A = M + R - 1;
-  constexpr int NG = DIM == 1 ? R : R * R;
-  constexpr int ND = DIM == 1 ? A : A * A;
-  constexpr int NO = DIM == 1 ? M : M * M;
-  constexpr int REC = round4(NG + ND + 2 * NO);
   const int lane = threadIdx.x & 31;
   const int nblk = (n_c + 31) >> 5;
   const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -273,53 +145,17 @@ __global__ void __launch_bounds__(128) k_sweep_eval(const float* __restrict__ re
   const int ci = (item - qv * nblk) * 32 + lane;
   const bool active = ci < n_c;
   const double c = active ? c_grid[ci] : c_grid[0];
-  Mats<M, R> Mx;
-  const bool ok = build_instance<M, R>(masks.mask[qv], c, d, Mx);
-
-  double num = 0.0;
-  const float4* r4 = reinterpret_cast<const float4*>(rec);
-  for (int t = 0; t < trials; ++t) {
-    float buf[REC];
-#pragma unroll
-    for (int q = 0; q < REC / 4; ++q) {
-      const float4 v = __ldg(r4 + (int64_t)t * (REC / 4) + q);
-      buf[4 * q + 0] = v.x;
-      buf[4 * q + 1] = v.y;
-      buf[4 * q + 2] = v.z;
-      buf[4 * q + 3] = v.w;
-    }
-    const float e = (DIM == 1) ? tile_err_1d<M, R>(Mx, buf) : tile_err_2d<M, R>(Mx, buf);
-    num += (double)e;
-  }
-  if (active) {
-    double* out = err + (int64_t)masks.q[qv] * n_c + ci;
-    *out = ok ? num / *ysum : (double)INFINITY;
-  }
+  const double e = lane_error<DIM, M, R>(rec, trials, masks.mask[qv], c, d, *ysum);
+  if (active) err[(int64_t)masks.q[qv] * n_c + ci] = e;
 }
 
 typedef void (*EvalFn)(const float*, int, const double*, int, double, const MaskList,
                        const double*, double*);
 
 static EvalFn eval_kernel(int dim, int m, int r) {
-#define WINO_EVAL_CASE(D, MM, RR) \
+#define WINO_EVAL_CASE(I, D, MM, RR) \
   if (dim == D && m == MM && r == RR) return k_sweep_eval<D, MM, RR>;
-  WINO_EVAL_CASE(1, 2, 3)
-  WINO_EVAL_CASE(1, 3, 3)
-  WINO_EVAL_CASE(1, 4, 3)
-  WINO_EVAL_CASE(1, 5, 3)
-  WINO_EVAL_CASE(1, 6, 3)
-  WINO_EVAL_CASE(1, 7, 3)
-  WINO_EVAL_CASE(1, 8, 3)
-  WINO_EVAL_CASE(1, 2, 5)
-  WINO_EVAL_CASE(1, 3, 5)
-  WINO_EVAL_CASE(1, 4, 5)
-  WINO_EVAL_CASE(1, 5, 5)
-  WINO_EVAL_CASE(1, 6, 5)
-  WINO_EVAL_CASE(2, 2, 3)
-  WINO_EVAL_CASE(2, 3, 3)
-  WINO_EVAL_CASE(2, 4, 3)
-  WINO_EVAL_CASE(2, 5, 3)
-  WINO_EVAL_CASE(2, 6, 3)
+  WINO_SWEEP_SIZES(WINO_EVAL_CASE)
 #undef WINO_EVAL_CASE
   return nullptr;
 }
@@ -346,19 +182,16 @@ static MaskList valid_masks(const SweepSize& s, const unsigned char* subsets, in
 int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_sizes,
                 const unsigned char* subsets, int n_subsets, int trials, unsigned long long seed,
                 double* err_out, cudaStream_t st) {
-  std::vector<SizeShape> shp(n_sizes);
   std::vector<size_t> rec_off(n_sizes);
   size_t rec_total = 0;
-  const int prep_threads = 256;
-  const int nb_prep = (trials + prep_threads - 1) / prep_threads;
+  const int nb_prep = sweep_prepare_blocks(trials);
   for (int s = 0; s < n_sizes; ++s) {
-    shp[s] = shape_of(sizes[s].dim, sizes[s].m, sizes[s].r);
     if (!eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)) {
       set_error("sweep size not compiled: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6");
       return WINO_EUNSUPPORTED;
     }
     rec_off[s] = rec_total;
-    rec_total += (size_t)trials * shp[s].rec;
+    rec_total += (size_t)trials * sweep_rec_width(sizes[s].dim, sizes[s].m, sizes[s].r);
   }
   // scratch layout: records | partials | ysum | c_grid | err
   const size_t n_err = (size_t)n_sizes * n_subsets * n_c;
@@ -384,15 +217,11 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   WINO_CUDA_TRY(cudaMemcpyAsync(cg, c_grid, n_c * sizeof(double), cudaMemcpyHostToDevice, st));
   std::vector<MaskList> ml(n_sizes);
   for (int s = 0; s < n_sizes; ++s) {
-    const SizeShape& z = shp[s];
-    ProfScope ps(kKSweepPrep, st);
-    k_sweep_prepare<<<nb_prep, prep_threads, 0, st>>>(rec + rec_off[s], part + (size_t)s * nb_prep,
-                                                       z.dim, z.m, z.r, trials, z.rec, seed);
-    k_sweep_ysum<<<1, 32, 0, st>>>(part + (size_t)s * nb_prep, nb_prep, ysum + s);
+    rc = sweep_prepare(rec + rec_off[s], part + (size_t)s * nb_prep, ysum + s, sizes[s].dim,
+                       sizes[s].m, sizes[s].r, trials, seed, st);
+    if (rc != WINO_OK) return rc;
     ml[s] = valid_masks(sizes[s], subsets, n_subsets);
-    note_launches(2);
   }
-  WINO_CUDA_TRY(cudaGetLastError());
   const int nblk = (n_c + 31) / 32;
   for (int s = 0; s < n_sizes; ++s) {
     if (ml[s].n == 0) continue;
@@ -419,10 +248,6 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   }
   return WINO_OK;
 }
-
-}  // namespace wino
-
-namespace wino {
 
 // Device FP64 construction for a batch of instances (the sweep's matrix
 // build, exposed for parity checks): one thread per c.
@@ -462,8 +287,7 @@ int instance_matrices(const double* c_grid, int n_c, const SweepSize& s, unsigne
   WINO_CUDA_TRY(cudaMemcpyAsync(AT, dAT, nAT * sizeof(double), cudaMemcpyDeviceToHost, st));
   WINO_CUDA_TRY(cudaMemcpyAsync(G, dG, nG * sizeof(double), cudaMemcpyDeviceToHost, st));
   WINO_CUDA_TRY(cudaMemcpyAsync(BT, dBT, nBT * sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (singular)
-    WINO_CUDA_TRY(cudaMemcpyAsync(singular, ds, n_c, cudaMemcpyDeviceToHost, st));
+  if (singular) WINO_CUDA_TRY(cudaMemcpyAsync(singular, ds, n_c, cudaMemcpyDeviceToHost, st));
   WINO_CUDA_TRY(cudaStreamSynchronize(st));
   return WINO_OK;
 }

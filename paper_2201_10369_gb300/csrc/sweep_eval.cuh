@@ -1,0 +1,221 @@
+// sweep_eval.cuh -- device pieces of the point sweep shared by the per-size
+// kernels (sweep.cu) and the persistent planned sweep (sweep_plan.cu).
+//
+// Trial records: one per trial, [g | d | hi(y) | lo(y)] in FP32, padded to a
+// multiple of 4 floats, where y is the FP64 direct correlation of the tile
+// (Eq. (1)) and hi = RN32(y), lo = RN32(y - hi).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace wino {
+
+__host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
+
+template <int DIM, int M, int R>
+struct SweepShape {
+  static constexpr int A = M + R - 1;
+  static constexpr int NG = DIM == 1 ? R : R * R;
+  static constexpr int ND = DIM == 1 ? A : A * A;
+  static constexpr int NO = DIM == 1 ? M : M * M;
+  static constexpr int REC = round4(NG + ND + 2 * NO);
+};
+
+template <int M, int R>
+struct Mats {
+  static constexpr int A = M + R - 1;
+  float AT[M * A], G[A * R], BT[A * A];
+};
+
+// Builds one instance's matrices in FP64 (Sec. 4.1-4.2) and rounds them once
+// to FP32 into registers.  Returns false for coinciding points.
+template <int M, int R>
+__device__ __forceinline__ bool build_instance(unsigned mask, double c, double d,
+                                               Mats<M, R>& Mx) {
+  constexpr int A = M + R - 1;
+  double pts[kMaxAlpha];
+  mask_points(mask, A, c, d, pts);
+  double ATd[M * A], Gd[A * R], BTd[A * A];
+  const bool ok = build_matrices<double>(pts, M, R, ATd, Gd, BTd);
+#pragma unroll
+  for (int i = 0; i < M * A; ++i) Mx.AT[i] = __double2float_rn(ATd[i]);
+#pragma unroll
+  for (int i = 0; i < A * R; ++i) Mx.G[i] = __double2float_rn(Gd[i]);
+#pragma unroll
+  for (int i = 0; i < A * A; ++i) Mx.BT[i] = __double2float_rn(BTd[i]);
+  return ok;
+}
+
+// |yhat - y| with y = hi + lo, in FP32.
+__device__ __forceinline__ float abs_err(float yhat, float hi, float lo) {
+  return fabsf(__fsub_rn(__fsub_rn(yhat, hi), lo));
+}
+
+// 1D F(m, r): u = G g, v = BT d, p = u .* v, y = AT p  (Eq. (8)).
+template <int M, int R>
+__device__ __forceinline__ float tile_err_1d(const Mats<M, R>& Mx, const float* __restrict__ rc) {
+  constexpr int A = M + R - 1;
+  const float* g = rc;
+  const float* d = rc + R;
+  const float* yh = d + A;
+  const float* yl = yh + M;
+  float p[A];
+#pragma unroll
+  for (int i = 0; i < A; ++i) {
+    float u = 0.0f, v = 0.0f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) u = fmaf(Mx.G[i * R + k], g[k], u);
+#pragma unroll
+    for (int l = 0; l < A; ++l) v = fmaf(Mx.BT[i * A + l], d[l], v);
+    p[i] = __fmul_rn(u, v);
+  }
+  float e = 0.0f;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    float y = 0.0f;
+#pragma unroll
+    for (int i = 0; i < A; ++i) y = fmaf(Mx.AT[j * A + i], p[i], y);
+    e = __fadd_rn(e, abs_err(y, yh[j], yl[j]));
+  }
+  return e;
+}
+
+// 2D F(m x m, r x r), Eq. (9), streamed one frequency row i at a time:
+//   W_i = G_i g, U_i = W_i G^T, T_i = BT_i d, V_i = T_i B, P_i = U_i .* V_i,
+//   Z += AT[:, i] P_i  (i ascending),  then Y = Z A.
+template <int M, int R>
+__device__ __forceinline__ float tile_err_2d(const Mats<M, R>& Mx, const float* __restrict__ rc) {
+  constexpr int A = M + R - 1;
+  const float* g = rc;
+  const float* d = rc + R * R;
+  const float* yh = d + A * A;
+  const float* yl = yh + M * M;
+  float Z[M * A];
+#pragma unroll
+  for (int i = 0; i < A; ++i) {
+    float Wi[R], Ti[A];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int l = 0; l < R; ++l) acc = fmaf(Mx.G[i * R + l], g[l * R + k], acc);
+      Wi[k] = acc;
+    }
+#pragma unroll
+    for (int l = 0; l < A; ++l) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < A; ++k) acc = fmaf(Mx.BT[i * A + k], d[k * A + l], acc);
+      Ti[l] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      float u = 0.0f, v = 0.0f;
+#pragma unroll
+      for (int k = 0; k < R; ++k) u = fmaf(Wi[k], Mx.G[j * R + k], u);
+#pragma unroll
+      for (int l = 0; l < A; ++l) v = fmaf(Ti[l], Mx.BT[j * A + l], v);
+      const float p = __fmul_rn(u, v);
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+        Z[a * A + j] = (i == 0) ? fmaf(Mx.AT[a * A + i], p, 0.0f)
+                                : fmaf(Mx.AT[a * A + i], p, Z[a * A + j]);
+    }
+  }
+  float e = 0.0f;
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      float y = 0.0f;
+#pragma unroll
+      for (int j = 0; j < A; ++j) y = fmaf(Z[a * A + j], Mx.AT[b * A + j], y);
+      e = __fadd_rn(e, abs_err(y, yh[a * M + b], yl[a * M + b]));
+    }
+  return e;
+}
+
+// The error of one instance (mask, c) over `trials` warp-uniform trial
+// records: sum_t ||yhat_t - y_t||_1 / sum_t ||y_t||_1, +inf when two points
+// coincide.  Per trial the m (m^2) terms are summed in FP32, the trial sums
+// in FP64.
+template <int DIM, int M, int R>
+__device__ __forceinline__ double lane_error(const float* __restrict__ rec, int trials,
+                                             unsigned mask, double c, double d, double ysum) {
+  using S = SweepShape<DIM, M, R>;
+  Mats<M, R> Mx;
+  const bool ok = build_instance<M, R>(mask, c, d, Mx);
+  double num = 0.0;
+  const float4* r4 = reinterpret_cast<const float4*>(rec);
+  for (int t = 0; t < trials; ++t) {
+    float buf[S::REC];
+#pragma unroll
+    for (int q = 0; q < S::REC / 4; ++q) {
+      const float4 v = __ldg(r4 + (int64_t)t * (S::REC / 4) + q);
+      buf[4 * q + 0] = v.x;
+      buf[4 * q + 1] = v.y;
+      buf[4 * q + 2] = v.z;
+      buf[4 * q + 3] = v.w;
+    }
+    const float e = (DIM == 1) ? tile_err_1d<M, R>(Mx, buf) : tile_err_2d<M, R>(Mx, buf);
+    num += (double)e;
+  }
+  return ok ? num / ysum : (double)INFINITY;
+}
+
+// Sizes the sweep is compiled for, as (index, dim, m, r) cases.
+#define WINO_SWEEP_SIZES(X) \
+  X(0, 1, 2, 3)             \
+  X(1, 1, 3, 3)             \
+  X(2, 1, 4, 3)             \
+  X(3, 1, 5, 3)             \
+  X(4, 1, 6, 3)             \
+  X(5, 1, 7, 3)             \
+  X(6, 1, 8, 3)             \
+  X(7, 1, 2, 5)             \
+  X(8, 1, 3, 5)             \
+  X(9, 1, 4, 5)             \
+  X(10, 1, 5, 5)            \
+  X(11, 1, 6, 5)            \
+  X(12, 2, 2, 3)            \
+  X(13, 2, 3, 3)            \
+  X(14, 2, 4, 3)            \
+  X(15, 2, 5, 3)            \
+  X(16, 2, 6, 3)
+
+// Index of (dim, m, r) in WINO_SWEEP_SIZES, or -1.
+inline int sweep_kind(int dim, int m, int r) {
+#define WINO_KIND_CASE(I, D, MM, RR) \
+  if (dim == D && m == MM && r == RR) return I;
+  WINO_SWEEP_SIZES(WINO_KIND_CASE)
+#undef WINO_KIND_CASE
+  return -1;
+}
+
+// Host: record width (floats) of a size.
+inline int sweep_rec_width(int dim, int m, int r) {
+  const int a = m + r - 1;
+  const int ng = dim == 1 ? r : r * r, nd = dim == 1 ? a : a * a, no = dim == 1 ? m : m * m;
+  return round4(ng + nd + 2 * no);
+}
+
+// Dense FP32 flops of one trial of one instance (cost model for scheduling
+// and the roofline): 1D 2(a r + a^2 + m a) + a;
+// 2D 2(a r^2 + a^2 r) + 4 a^3 + a^2 + 2(m a^2 + m^2 a).
+inline double sweep_trial_flops(int dim, int m, int r) {
+  const double a = m + r - 1;
+  if (dim == 1) return 2 * (a * r + a * a + m * a) + a;
+  return 2 * (a * r * r + a * a * r) + 4 * a * a * a + a * a + 2 * (m * a * a + m * m * a);
+}
+
+// k_sweep_prepare launcher (sweep.cu): trial records and per-block partial
+// sums of |y| for one size, then their fixed-order total into *ysum.
+int sweep_prepare(float* rec, double* partial, double* ysum, int dim, int m, int r, int trials,
+                  uint64_t seed, cudaStream_t st);
+inline int sweep_prepare_blocks(int trials) { return (trials + 255) / 256; }
+
+}  // namespace wino

@@ -102,6 +102,59 @@ def test_direct_f64_vs_oracle(wino, orc, dim):
     assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
+def _fused_launches(wino, fn):
+    wino.wino_profile_enable(True)
+    wino.wino_profile_read("fused_layer")
+    try:
+        fn()
+    finally:
+        wino.wino_profile_enable(False)
+    return wino.wino_profile_read("fused_layer")[1]
+
+
+@pytest.mark.parametrize("m", [2, 4, 6])
+@pytest.mark.parametrize("shape", [(1, 13, 64, 17, 19, 1), (2, 70, 128, 9, 10, 1),
+                                   (1, 3, 192, 6, 30, 0), (1, 9, 64, 1, 1, 2)])
+def test_fused_layer_bitwise_vs_oracle(wino, orc, m, shape):
+    """The fused kernel (K a multiple of 64) on ragged tile blocks, channel
+    counts off its chunking, several k-blocks, 1x1 images with padding."""
+    N, C, K, H, W, pad = shape
+    x, w = inputs.layer_uniform(N, C, K, H, W, seed=100 + m)
+    out = {}
+    n = _fused_launches(wino, lambda: out.setdefault("y", _run2d(wino, x, w, POINTS[m], m, pad)))
+    assert n == 1, "fused kernel not taken"
+    assert np.array_equal(out["y"], orc.wino_layer(x, w, 2, pad, POINTS[m], m, 3))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("m", [4, 6])
+@pytest.mark.parametrize("layer", [0, 3])
+def test_vgg_full_size_sampled_tiles(wino, orc, m, layer):
+    """The bench's configuration (VGG16 stage, N = 32, the bench's points):
+    512 random (tile, k) pairs recomputed by the oracle match bit for bit."""
+    import torch
+    C, H = inputs.VGG16_LAYERS[layer]
+    x, w = inputs.vgg_layer_host(C, H, N=inputs.VGG_BATCH, seed=7)
+    pts = POINTS[4] if m == 4 else [0.0, -0.5, -2.0, 2.0, 0.5, -1.003, 1.003, math.inf]
+    y = torch.empty((inputs.VGG_BATCH, C, H, H), device="cuda")
+    xt, wt = torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda()
+    n = _fused_launches(wino, lambda: wino.wino_conv2d(xt, wt, y, pts, m, 3, 1))
+    assert n == 1
+    yh = y.cpu().numpy()
+    th = -(-H // m)
+    T = inputs.VGG_BATCH * th * th
+    rng = np.random.default_rng(layer * 10 + m)
+    sel = np.stack([rng.integers(0, T, 512), rng.integers(0, C, 512)], axis=1)
+    out = orc.wino_layer_tiles(x, w, 2, 1, pts, m, 3, sel)
+    for (t, k), o in zip(sel, out):
+        nn, ti, tj = t // (th * th), (t // th) % th, t % th
+        for a in range(m):
+            for b in range(m):
+                p, q = ti * m + a, tj * m + b
+                if p < H and q < H:
+                    assert o[a, b] == yh[nn, k, p, q], (t, k, a, b)
+
+
 def test_error_stats_vs_numpy(wino):
     import torch
     rng = np.random.default_rng(5)

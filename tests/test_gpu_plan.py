@@ -1,0 +1,75 @@
+"""GPU checks of the planned sweep (one persistent launch in a CUDA graph):
+every mode reproduces wino_error_sweep bit for bit, random instance lists
+match the oracle, and the device-side deadline stops a run with
+WINO_ETIMEOUT instead of letting it run unbounded."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2201_10369_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small_grid():
+    cg = np.sort(np.concatenate([inputs.c_grid(40), [1.0]]))
+    return cg, inputs.SWEEP_SIZES, inputs.sweep_masks()
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3, 0])
+def test_plan_modes_equal_grid_sweep(wino, small_grid, mode):
+    cg, sizes, masks = small_grid
+    ref = wino.wino_error_sweep(cg, sizes, masks, 200, seed=3)
+    inst = wino.grid_instances(sizes, masks, cg)
+    plan = wino.SweepPlan(sizes, inst, 200, seed=3, mode=mode)
+    try:
+        got = plan.run().reshape(ref.shape)
+        got2 = plan.run().reshape(ref.shape)
+        info = plan.info()
+    finally:
+        plan.close()
+    assert np.array_equal(got, ref, equal_nan=True)
+    assert np.array_equal(got2, ref, equal_nan=True)
+    assert info["items"] > 0 and (mode == 0 or info["mode"] == mode)
+
+
+def test_plan_random_instances_vs_oracle(wino, orc):
+    rng = np.random.default_rng(9)
+    sizes = inputs.SWEEP_SIZES + [(1, 4, 5, 1.0)]
+    masks = inputs.sweep_masks()
+    inst = []
+    for _ in range(700):
+        s = int(rng.integers(len(sizes)))
+        inst.append((s, int(rng.choice(masks)), float(np.exp(rng.uniform(np.log(0.05), np.log(20))))))
+    inst += [(2, 0x0F, 1.0), (9, 0x0F, 1.0), (0, 0x07, 1.5)]  # coinciding points; invalid mask
+    plan = wino.SweepPlan(sizes, inst, 150, seed=5, mode=1)
+    try:
+        got = plan.run()
+    finally:
+        plan.close()
+    for (s, mk, c), e in zip(inst, got):
+        eo = orc.error_sweep([c], [sizes[s]], [mk], 150, 5)[0, 0, 0]
+        if math.isnan(eo):
+            assert math.isnan(e)
+        elif math.isinf(eo):
+            assert math.isinf(e)
+        else:
+            assert abs(e - eo) <= 1e-6 * eo
+
+
+def test_plan_deadline_reports_timeout(wino):
+    cg = inputs.c_grid(256)
+    inst = wino.grid_instances([(2, 6, 3, 1.0)], [0x6F], cg)
+    plan = wino.SweepPlan([(2, 6, 3, 1.0)], inst, 1000, seed=0, mode=1)
+    try:
+        plan.set_deadline(1e-6)  # one nanosecond of device time
+        with pytest.raises(wino.WinoError) as e:
+            plan.run()
+        assert e.value.status == wino.WINO_ETIMEOUT
+        plan.set_deadline(0.0)   # the plan stays usable afterwards
+        full = plan.run()
+        assert np.all(np.isfinite(full))
+    finally:
+        plan.close()

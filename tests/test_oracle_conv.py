@@ -187,3 +187,35 @@ def test_lowp_layer_error_ordering(orc):
     assert err["bf16"] > 20 * err["f32"]
     assert err["fp16"] < err["bf16"]
     assert err["split_bf16x3"] < err["bf16"] / 20
+
+
+@pytest.mark.parametrize("dim,m", [(2, 2), (2, 4), (2, 6), (1, 4)])
+def test_layer_tiles_equals_layer(orc, dim, m):
+    """The per-tile oracle entry reproduces the full layer bit for bit on
+    every (tile, k) of a small ragged layer."""
+    rng = np.random.default_rng(20 + m)
+    c = 1.7
+    pts = [0.0, -1 / c, -c, c, 1 / c, -1.0, 1.0][: m + 1] + [math.inf]
+    if dim == 2:
+        x = rng.uniform(-1, 1, (2, 3, 11, 9)).astype(np.float32)
+        w = rng.uniform(-1, 1, (4, 3, 3, 3)).astype(np.float32)
+    else:
+        x = rng.uniform(-1, 1, (2, 3, 19)).astype(np.float32)
+        w = rng.uniform(-1, 1, (4, 3, 3)).astype(np.float32)
+    y = orc.wino_layer(x, w, dim, 1, pts, m, 3)
+    Ho = 1 if dim == 1 else y.shape[2]
+    Wo = y.shape[-1]
+    th, tw = (1 if dim == 1 else -(-Ho // m)), -(-Wo // m)
+    sel = [(t, k) for t in range(2 * th * tw) for k in range(4)]
+    out = orc.wino_layer_tiles(x, w, dim, 1, pts, m, 3, sel)
+    for (t, k), o in zip(sel, out):
+        n, ti, tj = t // (th * tw), (t // tw) % th, t % tw
+        if dim == 1:
+            for b in range(m):
+                if tj * m + b < Wo:
+                    assert o[b] == y[n, k, tj * m + b]
+        else:
+            for a in range(m):
+                for b in range(m):
+                    if ti * m + a < Ho and tj * m + b < Wo:
+                        assert o[a, b] == y[n, k, ti * m + a, tj * m + b]
