@@ -176,6 +176,36 @@ int wino_instance_matrices(const double* c_grid, int n_c, wino_size size,
                            unsigned char* singular, void* cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* FP32 layer without allocation.                                           */
+/* ---------------------------------------------------------------------- */
+
+/* Size (floats) of the fixed scratch array wino_conv2d_f32_noalloc uses:
+ * 4 Mi floats = 16 MiB of device memory, held by every device that loads
+ * the library until the process exits.                                     */
+#define WINO_NOALLOC_SCRATCH_FLOATS (1 << 22)
+
+/* wino_conv2d with dtype WINO_F32, for callers that cannot allocate device
+ * memory: code running while a stream is captured into a CUDA graph in
+ * global mode (cudaMalloc is refused there), plug-ins inside a framework
+ * whose allocator has already reserved the device's memory, and loops whose
+ * rules forbid allocation after start-up.  It allocates nothing: its only
+ * scratch (the transformed filters, alpha^2 * C * K floats) lives in a fixed
+ * array compiled into the library.  The paper has no counterpart; this is
+ * a deployment convenience around the same fused kernel.
+ * Arguments and results are those of wino_conv2d.  Supported: r = 3,
+ * m in {2, 4, 6}, K a multiple of 64, alpha^2 * C * K <=
+ * WINO_NOALLOC_SCRATCH_FLOATS; anything else returns WINO_EINVAL with the
+ * reason in wino_last_error().  The first call on each device looks up the
+ * array's device address and prepares the kernel, so make it before any
+ * stream capture.  All calls share the array: calls whose GPU work may
+ * overlap (other streams, other host threads) race on it and must be
+ * ordered by the caller.                                                   */
+int wino_conv2d_f32_noalloc(const void* x, const void* w, void* y,
+                            int N, int C, int K, int H, int W, int pad,
+                            const double* points, int m, int r,
+                            void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
 /* Planned sweep: one persistent launch in a CUDA graph (Sec. 6.2-6.3      */
 /* searches run as explicit instance lists).                               */
 /* ---------------------------------------------------------------------- */

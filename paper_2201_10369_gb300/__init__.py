@@ -66,6 +66,8 @@ def _declare(L):
     L.wino_instance_matrices.argtypes = [_DP, _i, WinoSize, ctypes.c_uint, _DP, _DP, _DP,
                                          ctypes.POINTER(ctypes.c_ubyte), _vp]
     L.wino_instance_matrices.restype = _i
+    L.wino_conv2d_f32_noalloc.argtypes = [_vp, _vp, _vp] + [_i] * 6 + [_DP, _i, _i, _vp]
+    L.wino_conv2d_f32_noalloc.restype = _i
     L.wino_sweep_plan_create.argtypes = [ctypes.POINTER(WinoSize), _i,
                                          ctypes.POINTER(WinoInstance), ctypes.c_int64, _i,
                                          ctypes.c_ulonglong, _i, ctypes.POINTER(_vp)]
@@ -197,6 +199,20 @@ def wino_conv1d(x, w, y, points, m: int, r: int, pad: int = 1, dtype="f32", stre
     pts = _points(points)
     _check(L.wino_conv1d(_ptr(x), _ptr(w), _ptr(y), N, C, K, Ln, pad, pts.ctypes.data_as(_DP),
                          m, r, _dtype(dtype), _stream(stream)))
+    return y
+
+
+def wino_conv2d_f32_noalloc(x, w, y, points, m: int, r: int, pad: int = 1, stream=None):
+    """wino_conv2d (FP32) without any device allocation: for callers that
+    cannot allocate (inside graph capture, under a framework that owns the
+    memory pool).  Uses the library's fixed 16 MiB scratch array; see
+    include/wino.h for the limits and the rule that overlapping calls race."""
+    L = load()
+    N, C, H, W = x.shape
+    K = w.shape[0]
+    pts = _points(points)
+    _check(L.wino_conv2d_f32_noalloc(_ptr(x), _ptr(w), _ptr(y), N, C, K, H, W, pad,
+                                     pts.ctypes.data_as(_DP), m, r, _stream(stream)))
     return y
 
 
