@@ -15,7 +15,15 @@
 // fused.cu; this file is the general path they fall back to.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
 
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/wino.h"
 #include "common.cuh"
 
 namespace wino {
@@ -256,6 +264,7 @@ __global__ void k_output_transform(const float* __restrict__ Mi, float* __restri
 int layer_forward_fused(const float* x, const float* w, float* y, const LayerGeom& g,
                         const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st);
 size_t fused_workspace_bytes(const LayerGeom& g);
+size_t tc_workspace_bytes(const LayerGeom& g, int dtype);
 
 size_t layer_workspace_bytes(const LayerGeom& g, int dtype) {
   const size_t F = (size_t)g.F;
@@ -263,13 +272,7 @@ size_t layer_workspace_bytes(const LayerGeom& g, int dtype) {
   const size_t u = F * g.C * (size_t)g.T * sizeof(float);
   const size_t mm = F * g.K * (size_t)g.T * sizeof(float);
   size_t general = v + u + mm + 1024;
-  if (dtype != 0) {
-    // precision form: FP32 V + 16-bit U/V operands (x2 for the split) + FP32 M
-    const size_t s16 = (dtype == 3) ? 2 : 1;
-    size_t tc = v + s16 * (F * g.C * (size_t)g.T * 2 + F * g.C * g.K * 2) + mm + 4096 +
-                F * 2 * sizeof(float);
-    return tc;
-  }
+  if (dtype != 0) return tc_workspace_bytes(g, dtype);
   return general;
 }
 
@@ -309,11 +312,117 @@ int layer_forward_general_f32(const float* x, const float* w, float* y, const La
   return 0;
 }
 
+int layer_forward_split(const float* x, const float* w, float* y, const LayerGeom& g,
+                        const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Variant choice for the FP32 layer (autotuner): the fully fused kernel
+// (fused.cu), the split transform + GEMM/output kernels (fused.cu) and the
+// general pipeline above compute the same bits; which is fastest depends
+// on the shape.  The first call for a shape times the fused and split
+// variants on the caller's stream (twice each, keeping the second) and
+// caches the faster one for the process.  Timing synchronises the stream,
+// so it is skipped while the stream is being captured into a graph (the
+// split variant is used then) and when WINO_AUTOTUNE=0.
+// WINO_LAYER_VARIANT=fused|split|general forces a variant.
+// ---------------------------------------------------------------------------
+enum LayerVariant { kVarUnknown = 0, kVarFused = 1, kVarSplit = 2, kVarGeneral = 3 };
+
+static std::mutex g_var_mu;
+static std::map<std::string, int> g_var_cache;
+
+static std::string layer_key(const LayerGeom& g, const LayerMats& M) {
+  char buf[160];
+  snprintf(buf, sizeof(buf), "d%d m%d r%d N%d C%d K%d H%d W%d p%d", g.dim, M.m, M.r, g.N, g.C,
+           g.K, g.H, g.W, g.pad);
+  return buf;
+}
+
+static int forced_variant() {
+  const char* v = getenv("WINO_LAYER_VARIANT");
+  if (!v) return kVarUnknown;
+  if (!strcmp(v, "fused")) return kVarFused;
+  if (!strcmp(v, "split")) return kVarSplit;
+  if (!strcmp(v, "general")) return kVarGeneral;
+  return kVarUnknown;
+}
+
+static int run_variant(int var, const float* x, const float* w, float* y, const LayerGeom& g,
+                       const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (var == kVarFused) return layer_forward_fused(x, w, y, g, M, ws, ws_bytes, st);
+  if (var == kVarSplit) return layer_forward_split(x, w, y, g, M, ws, ws_bytes, st);
+  return layer_forward_general_f32(x, w, y, g, M, ws, st);
+}
+
+static int tune_variant(const float* x, const float* w, float* y, const LayerGeom& g,
+                        const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st,
+                        int* out) {
+  cudaEvent_t a, b;
+  WINO_CUDA_TRY(cudaEventCreate(&a));
+  WINO_CUDA_TRY(cudaEventCreate(&b));
+  float best = 1e30f;
+  int best_var = kVarGeneral;
+  const int cands[2] = {kVarSplit, kVarFused};
+  for (int var : cands) {
+    float ms = 1e30f;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      WINO_CUDA_TRY(cudaEventRecord(a, st));
+      int rc = run_variant(var, x, w, y, g, M, ws, ws_bytes, st);
+      if (rc == kFallback) {
+        ok = false;
+        break;
+      }
+      if (rc != WINO_OK) return rc;
+      WINO_CUDA_TRY(cudaEventRecord(b, st));
+      WINO_CUDA_TRY(cudaEventSynchronize(b));
+      WINO_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+    }
+    if (ok && ms < best) {
+      best = ms;
+      best_var = var;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *out = best_var;
+  return WINO_OK;
+}
+
 int layer_forward_f32(const float* x, const float* w, float* y, const LayerGeom& g,
                       const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st) {
-  int rc = layer_forward_fused(x, w, y, g, M, ws, ws_bytes, st);
-  if (rc != kFallback) return rc;
-  return layer_forward_general_f32(x, w, y, g, M, ws, st);
+  int var = forced_variant();
+  if (var == kVarUnknown) {
+    const std::string key = layer_key(g, M);
+    {
+      std::lock_guard<std::mutex> lk(g_var_mu);
+      auto it = g_var_cache.find(key);
+      if (it != g_var_cache.end()) var = it->second;
+    }
+    if (var == kVarUnknown) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+      }
+      const char* at = getenv("WINO_AUTOTUNE");
+      if (cs == cudaStreamCaptureStatusNone && !(at && !strcmp(at, "0"))) {
+        int rc = tune_variant(x, w, y, g, M, ws, ws_bytes, st, &var);
+        if (rc != WINO_OK) return rc;
+        std::lock_guard<std::mutex> lk(g_var_mu);
+        g_var_cache[key] = var;
+      } else {
+        var = kVarSplit;
+      }
+    }
+  }
+  int rc = run_variant(var, x, w, y, g, M, ws, ws_bytes, st);
+  if (rc == kFallback && var != kVarGeneral) {
+    rc = layer_forward_split(x, w, y, g, M, ws, ws_bytes, st);
+    if (rc == kFallback) rc = layer_forward_fused(x, w, y, g, M, ws, ws_bytes, st);
+  }
+  if (rc == kFallback) rc = layer_forward_general_f32(x, w, y, g, M, ws, st);
+  return rc;
 }
 
 }  // namespace wino

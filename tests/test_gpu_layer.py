@@ -112,12 +112,15 @@ def _fused_launches(wino, fn):
     return wino.wino_profile_read("fused_layer")[1]
 
 
+@pytest.mark.parametrize("variant", ["fused", "split"])
 @pytest.mark.parametrize("m", [2, 4, 6])
 @pytest.mark.parametrize("shape", [(1, 13, 64, 17, 19, 1), (2, 70, 128, 9, 10, 1),
                                    (1, 3, 192, 6, 30, 0), (1, 9, 64, 1, 1, 2)])
-def test_fused_layer_bitwise_vs_oracle(wino, orc, m, shape):
-    """The fused kernel (K a multiple of 64) on ragged tile blocks, channel
-    counts off its chunking, several k-blocks, 1x1 images with padding."""
+def test_fused_layer_bitwise_vs_oracle(wino, orc, m, shape, variant, monkeypatch):
+    """The fused kernel and the split transform + GEMM/output kernels (K a
+    multiple of 64) on ragged tile blocks, channel counts off their chunking,
+    several k-blocks, 1x1 images with padding."""
+    monkeypatch.setenv("WINO_LAYER_VARIANT", variant)
     N, C, K, H, W, pad = shape
     x, w = inputs.layer_uniform(N, C, K, H, W, seed=100 + m)
     out = {}
@@ -127,12 +130,14 @@ def test_fused_layer_bitwise_vs_oracle(wino, orc, m, shape):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("variant", ["fused", "split"])
 @pytest.mark.parametrize("m", [4, 6])
 @pytest.mark.parametrize("layer", [0, 3])
-def test_vgg_full_size_sampled_tiles(wino, orc, m, layer):
+def test_vgg_full_size_sampled_tiles(wino, orc, m, layer, variant, monkeypatch):
     """The bench's configuration (VGG16 stage, N = 32, the bench's points):
     512 random (tile, k) pairs recomputed by the oracle match bit for bit."""
     import torch
+    monkeypatch.setenv("WINO_LAYER_VARIANT", variant)
     C, H = inputs.VGG16_LAYERS[layer]
     x, w = inputs.vgg_layer_host(C, H, N=inputs.VGG_BATCH, seed=7)
     pts = POINTS[4] if m == 4 else [0.0, -0.5, -2.0, 2.0, 0.5, -1.003, 1.003, math.inf]

@@ -1,0 +1,61 @@
+"""GPU parity of the precision form of the contraction (tcgen05 BF16 / FP16 /
+split BF16x3 with per-frequency power-of-two scaling) against the oracle's
+emulation of the same rounding.
+
+Both sides round the same FP32 transform outputs to the same 16-bit
+operands and form exact products; only the FP32 accumulation order of the
+tensor cores differs from the oracle's sequential fmaf.  Bar: max |yGPU -
+yoracle| <= 2e-5 max |yoracle| (accumulation-order differences amplified by
+the output transform), and the relative L1 error against FP64 within 5% of
+the oracle's."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2201_10369_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PTS = {4: [0.0, -1 / 1.622, -1.622, 1.622, 1 / 1.622, math.inf],
+       6: [0.0, -0.5, -2.0, 2.0, 0.5, -1.003, 1.003, math.inf],
+       2: [0.0, -1.0, 1.0, math.inf]}
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp16", "split_bf16x3"])
+@pytest.mark.parametrize("m", [4, 6, 2])
+@pytest.mark.parametrize("shape", [(2, 64, 64, 10, 10), (1, 80, 128, 9, 13), (1, 64, 256, 6, 6)])
+def test_tc_layer_vs_oracle_emulation(wino, orc, dtype, m, shape):
+    import torch
+    N, C, K, H, W = shape
+    rng = np.random.default_rng(C + K + m)
+    x = np.maximum(rng.standard_normal((N, C, H, W)), 0).astype(np.float32)
+    w = (rng.standard_normal((K, C, 3, 3)) * np.sqrt(2.0 / (9 * C))).astype(np.float32)
+    y = torch.full((N, K, H, W), float("nan"), device="cuda")
+    wino.wino_conv2d(torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda(), y, PTS[m], m, 3, 1,
+                     dtype)
+    torch.cuda.synchronize()
+    yg = y.cpu().numpy()
+    yo = orc.wino_layer(x, w, 2, 1, PTS[m], m, 3, dtype)
+    assert np.all(np.isfinite(yg))
+    scale = np.abs(yo).max()
+    assert np.abs(yg - yo).max() <= 2e-5 * scale
+    ref = orc.direct_f64(x, w, 2, 1, 3)
+    eg = np.abs(yg - ref).sum() / np.abs(ref).sum()
+    eo = np.abs(yo.astype(np.float64) - ref).sum() / np.abs(ref).sum()
+    assert abs(eg / eo - 1) < 0.05, (eg, eo)
+
+
+def test_tc_error_ordering_matches_precision(wino, orc):
+    """BF16 > FP16 > split BF16x3 > FP32 in error against FP64 (F(4x4,3x3))."""
+    import torch
+    x, w = inputs.vgg_layer_host(64, 20, N=2, seed=3)
+    xt, wt = torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda()
+    ref = orc.direct_f64(x, w, 2, 1, 3)
+    err = {}
+    for dt in ("f32", "bf16", "fp16", "split_bf16x3"):
+        y = torch.empty((2, 64, 20, 20), device="cuda")
+        wino.wino_conv2d(xt, wt, y, PTS[4], 4, 3, 1, dt)
+        torch.cuda.synchronize()
+        err[dt] = np.abs(y.cpu().numpy() - ref).sum() / np.abs(ref).sum()
+    assert err["bf16"] > err["fp16"] > err["split_bf16x3"] > err["f32"]
