@@ -40,6 +40,14 @@ C4, C6, D6 = 1.622, 2.0, 1.003
 PTS4 = [0.0, -1 / C4, -C4, C4, 1 / C4, math.inf]
 PTS6 = [0.0, -1 / C6, -C6, C6, 1 / C6, -D6, D6, math.inf]
 METRIC = "Winograd layer effective TFLOP/s at stated FP64 error; c-sweep evals/s vs plain"
+# the layer stacks of one step: key -> (m, points, contraction dtype)
+STACKS = {"f4x4": (4, PTS4, "f32"), "f6x6": (6, PTS6, "f32"),
+          "f4x4_bf16": (4, PTS4, "bf16"), "f4x4_split_bf16x3": (4, PTS4, "split_bf16x3")}
+# surrogate training: sweep labels of random instances of the sweep's sizes
+# plus 1D F(m,5), m = 2..6 (d chosen so every size has valid subsets)
+R5_SIZES = [(1, 2, 5, 1.0), (1, 3, 5, 1.0), (1, 4, 5, 1.0), (1, 5, 5, 2.478), (1, 6, 5, 1.229)]
+SURROGATE_SAMPLES = 2_000_000
+SURROGATE_EPOCHS = 200
 
 
 def load_peaks():
@@ -49,6 +57,24 @@ def load_peaks():
             d = json.load(f)
         return d, "measured"
     return PEAKS_FALLBACK, "fallback"
+
+
+def reduce_max(values, world):
+    """Per-rank timings reduced to their maximum over ranks (the bench's
+    clock for N > 1 GPUs); the identity for one rank."""
+    if world <= 1:
+        return list(values)
+    import torch
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def rank_seed(rank, layer):
+    """Input seed of (rank, layer): every rank draws its own batch (weak
+    scaling: per-GPU work fixed as ranks are added)."""
+    return 1000 * rank + layer
 
 
 def direct_flops(layers, N):
@@ -212,50 +238,74 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     # inputs resident in HBM (seeded per rank), outputs preallocated
-    X, Wt, Y4, Y6 = [], [], [], []
+    X, Wt = [], []
     for li, (C, H) in enumerate(layers):
-        x, w = inputs.vgg_layer_device(C, H, N=N, seed=1000 * rank + li, device=dev)
+        x, w = inputs.vgg_layer_device(C, H, N=N, seed=rank_seed(rank, li), device=dev)
         X.append(x)
         Wt.append(w)
-        Y4.append(torch.empty((N, C, H, H), device=dev))
-        Y6.append(torch.empty((N, C, H, H), device=dev))
+    Y = {k: [torch.empty((N, C, H, H), device=dev) for C, H in layers] for k in STACKS}
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
     cg = inputs.c_grid()
     sizes, masks = inputs.SWEEP_SIZES, inputs.sweep_masks()
 
-    def layers_f4():
+    def stack(key):
+        m, pts, dt = STACKS[key]
         for li in range(len(layers)):
-            wino.wino_conv2d(X[li], Wt[li], Y4[li], PTS4, 4, 3, 1)
-
-    def layers_f6():
-        for li in range(len(layers)):
-            wino.wino_conv2d(X[li], Wt[li], Y6[li], PTS6, 6, 3, 1)
+            wino.wino_conv2d(X[li], Wt[li], Y[key][li], pts, m, 3, 1, dt)
 
     def sweep():
         return wino.wino_error_sweep(cg, sizes, masks, inputs.SWEEP_TRIALS, seed=rank)
 
-    # FP64 error of each layer (stated beside the throughput; untimed)
-    layers_f4()
-    layers_f6()
+    # planned persistent sweep of the same grid (mode autotuned, graph captured once)
+    plan = wino.SweepPlan(sizes, wino.grid_instances(sizes, masks, cg), inputs.SWEEP_TRIALS,
+                          seed=rank)
+    # surrogate: labels from the sweep itself, trained once (reported, untimed)
     torch.cuda.synchronize()
-    fp64 = {"f4x4": [], "f6x6": []}
+    t0 = time.perf_counter()
+    _, Xs, ys = wino.surrogate_training_set(sizes + R5_SIZES, masks, SURROGATE_SAMPLES,
+                                            inputs.SWEEP_TRIALS, seed=100 + rank)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    model = wino.Surrogate(seed=rank)
+    model.set_output_bias(float(ys.mean()))
+    t0 = time.perf_counter()
+    model.train(Xs, ys, batch=4096, epochs=SURROGATE_EPOCHS, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    guided = wino.GuidedSearch(model, sizes, masks, cg, inputs.SWEEP_TRIALS, seed=rank)
+
+    # FP64 error of every stack (stated beside the throughput; untimed)
+    for key in STACKS:
+        stack(key)
+    torch.cuda.synchronize()
+    fp64 = {key: [] for key in STACKS}
     for li in range(len(layers)):
-        y64 = torch.empty(Y4[li].shape, dtype=torch.float64, device=dev)
+        y64 = torch.empty(Y["f4x4"][li].shape, dtype=torch.float64, device=dev)
         wino.wino_direct_conv_f64(X[li], Wt[li], y64, 1)
-        for key, Y in (("f4x4", Y4), ("f6x6", Y6)):
-            se, sr, me, mr = wino.wino_error_stats(Y[li], y64)
+        for key in STACKS:
+            se, sr, me, mr = wino.wino_error_stats(Y[key][li], y64)
             fp64[key].append({"rel_l1": se / sr, "max_rel_inf": me / mr})
         del y64
     torch.cuda.synchronize()
 
-    # warm-up
+    # warm-up (the first calls also run the layer and sweep autotuners)
     for _ in range(args.warmup):
-        layers_f4()
-        layers_f6()
-        sweep()
+        for key in STACKS:
+            stack(key)
+        ex = sweep()
+        plan.run(stream)
+        guided.run()
     torch.cuda.synchronize()
+    ex = np.where(np.isinf(ex), np.nan, ex)
+    ex_rows = np.any(np.isfinite(ex), axis=2)
+    exb = np.where(ex_rows, np.nanmin(np.where(ex_rows[:, :, None], ex, 1.0), axis=2), np.nan)
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    names = ("wino_gemm", "input_transform", "output_transform", "filter_transform",
+             "fused_layer", "sweep_eval", "sweep_prepare", "tc_gemm", "tc_transform")
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STACKS) + 1)]
+          for _ in range(args.steps)]
+    wall = {"sweep": 0.0, "plan": 0.0, "guided": 0.0, "step": 0.0}
+    guided_res = []
     gpu_id = str(local_rank)
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -267,93 +317,136 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks.start()
     wino.wino_profile_enable(True)
-    for k in ("wino_gemm", "input_transform", "output_transform", "filter_transform",
-              "fused_layer", "sweep_eval", "sweep_prepare"):
+    for k in names:
         wino.wino_profile_read(k)
     launches0 = wino.wino_kernel_launches()
+    torch.cuda.nvtx.range_push("timed")
     for s in range(args.steps):
-        flush.fill_(float(s))  # L2 flush between steps (outside the events)
-        e0, e1, e2, e3 = ev[s]
-        e0.record(stream)
-        layers_f4()
-        e1.record(stream)
-        layers_f6()
-        e2.record(stream)
+        flush.fill_(float(s))  # L2 flush between steps (outside the timing)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        ev[s][0].record(stream)
+        for i, key in enumerate(STACKS):
+            stack(key)
+            ev[s][i + 1].record(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         sweep()
-        e3.record(stream)
+        t1 = time.perf_counter()
+        plan.run(stream)
+        t2 = time.perf_counter()
+        guided_res.append(guided.run())
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        wall["sweep"] += t1 - t0
+        wall["plan"] += t2 - t1
+        wall["guided"] += t3 - t2
+        wall["step"] += t3 - ts
     torch.cuda.synchronize()
-    launches = wino.wino_kernel_launches() - launches0 - 0
+    torch.cuda.nvtx.range_pop()
+    launches = wino.wino_kernel_launches() - launches0
     wino.wino_profile_enable(False)
-    prof = {k: wino.wino_profile_read(k) for k in
-            ("wino_gemm", "input_transform", "output_transform", "filter_transform",
-             "fused_layer", "sweep_eval", "sweep_prepare")}
+    prof = {k: wino.wino_profile_read(k) for k in names}
     clk = clocks.stop()
-    t4 = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)) / 1e3
-    t6 = sum(ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)) / 1e3
-    tsw = sum(ev[s][2].elapsed_time(ev[s][3]) for s in range(args.steps)) / 1e3
-    ttot = sum(ev[s][0].elapsed_time(ev[s][3]) for s in range(args.steps)) / 1e3
-    if world > 1:
-        t = torch.tensor([t4, t6, tsw, ttot], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t4, t6, tsw, ttot = t.tolist()
+    tk = {key: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / 1e3
+          for i, key in enumerate(STACKS)}
+    times = [tk[k] for k in STACKS] + [wall[k] for k in ("sweep", "plan", "guided", "step")]
+    times = reduce_max(times, world)
+    for i, k in enumerate(STACKS):
+        tk[k] = times[i]
+    wall = dict(zip(("sweep", "plan", "guided", "step"), times[len(STACKS):]))
     fl = direct_flops(layers, N)
-    v4 = world * fl * args.steps / t4 / 1e12
-    v6 = world * fl * args.steps / t6 / 1e12
+    tflops = {k: world * fl * args.steps / tk[k] / 1e12 for k in STACKS}
     n_inst = 503808
-    vsw = world * n_inst * args.steps / tsw
+    vsw = world * n_inst * args.steps / wall["sweep"]
+    vplan = world * n_inst * args.steps / wall["plan"]
+    g_last = guided_res[-1]
+    rows = np.isfinite(exb)
+    ratios = g_last["best_err"][rows] / exb[rows]
+    ratio, ratio_med = float(np.nanmax(ratios)), float(np.nanmedian(ratios))
+    # rank of the guided best among the exhaustive row's errors (0 = the minimum)
+    exf = np.where(np.isfinite(ex), ex, np.inf)
+    ranks = np.array([(exf[s_, q_] < g_last["best_err"][s_, q_]).sum()
+                      for s_, q_ in zip(*np.nonzero(rows))])
 
-    # e2e: the same F(4x4) stack through the public API with host buffers
+    # e2e: the F(4x4) FP32 stack through the public API with host buffers
     xh = [x.cpu().pin_memory() for x in X]
-    yh = [torch.empty(y.shape, dtype=y.dtype).pin_memory() for y in Y4]
+    yh = [torch.empty(y.shape, dtype=y.dtype).pin_memory() for y in Y["f4x4"]]
     h2d = sum(x.numel() * 4 for x in X)
-    d2h = sum(y.numel() * 4 for y in Y4)
+    d2h = sum(y.numel() * 4 for y in Y["f4x4"])
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    m4, p4, dt4 = STACKS["f4x4"]
     for s in range(args.steps + 1):
         if s > 0:
             flush.fill_(float(s))
             ee[s - 1][0].record(stream)
         for li in range(len(layers)):
             X[li].copy_(xh[li], non_blocking=True)
-            wino.wino_conv2d(X[li], Wt[li], Y4[li], PTS4, 4, 3, 1)
-            yh[li].copy_(Y4[li], non_blocking=True)
+            wino.wino_conv2d(X[li], Wt[li], Y["f4x4"][li], p4, m4, 3, 1, dt4)
+            yh[li].copy_(Y["f4x4"][li], non_blocking=True)
         if s > 0:
             ee[s - 1][1].record(stream)
     torch.cuda.synchronize()
     te2e = sum(a.elapsed_time(b) for a, b in ee) / 1e3
     ve2e = world * fl * args.steps / te2e / 1e12
 
-    # roofline of the dominant kernel of the F(4x4) + F(6x6) stacks
-    layer_kernels = {k: v for k, v in prof.items() if k not in ("sweep_eval", "sweep_prepare")}
-    dom = max(layer_kernels, key=lambda k: layer_kernels[k][0])
-    dom_ms, dom_n = layer_kernels[dom]
-    roof = roofline_for(dom, dom_ms, dom_n, layers, N, peaks, peak_src, clk)
-    sw_ms, sw_n = prof["sweep_eval"]
-    sweep_roof = sweep_roofline(sw_ms, sw_n, args.steps, clk)
+    # rooflines: the dominant kernel of the step, and each main kernel
+    roofs = {}
+    for k, (ms, n) in prof.items():
+        if n:
+            r = kernel_roofline(k, ms, n, args.steps, layers, N, peaks, peak_src)
+            if r:
+                roofs[k] = r
+    dom = max(roofs, key=lambda k: prof[k][0])
+    plan_info = plan.info()
+    plan.close()
+    guided.close()
+    model.close()
 
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": v4, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * ttot / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": tflops["f4x4"], "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall["step"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
         "config": {
-            "workload": "VGG16 3x3 layer stack (C=64..512, H=224..14), N=32/GPU, FP32 "
-                        "Winograd F(4x4,3x3); + F(6x6,3x3) stack + full point sweep per step",
-            "points_f4x4": "{0,+-c,+-1/c,inf} c=1.622", "points_f6x6":
-                "{0,+-c,+-1/c,-d,d,inf} c=2 d=1.003", "global_batch": N * world,
+            "workload": "VGG16 3x3 layer stack (C=64..512, H=224..14), N=32/GPU, FP32 Winograd "
+                        "F(4x4,3x3) [value]; per step also the F(6x6,3x3) FP32 stack, the "
+                        "BF16 and split-BF16x3 tensor-core F(4x4) stacks, the full point sweep "
+                        "(503808 instances x 1000 trials) per-size and as one persistent graph "
+                        "launch, and the surrogate-guided search of the same grid",
+            "points_f4x4": "{0,+-c,+-1/c,inf} c=1.622",
+            "points_f6x6": "{0,+-c,+-1/c,-d,d,inf} c=2 d=1.003", "global_batch": N * world,
             "parallelism": "dp%d" % world if world > 1 else "single",
-            "l2": "256 MB flush between steps (untimed); each layer input > L2 except "
-                  "the 28x28/14x14 stages"},
-        "fp64_error": {"f4x4_rel_l1_per_layer": [r["rel_l1"] for r in fp64["f4x4"]],
-                       "f4x4_max_rel_inf": max(r["max_rel_inf"] for r in fp64["f4x4"]),
-                       "f6x6_rel_l1_per_layer": [r["rel_l1"] for r in fp64["f6x6"]],
-                       "f6x6_max_rel_inf": max(r["max_rel_inf"] for r in fp64["f6x6"])},
-        "f6x6": {"value": v6, "unit": "TFLOP/s", "ms_per_step": 1e3 * t6 / args.steps},
-        "f4x4_ms_per_step": 1e3 * t4 / args.steps,
+            "l2": "256 MB flush between steps (untimed); each layer input > L2 except the "
+                  "28x28/14x14 stages"},
+        "fp64_error": {k: {"rel_l1_per_layer": [r["rel_l1"] for r in fp64[k]],
+                           "max_rel_inf": max(r["max_rel_inf"] for r in fp64[k])} for k in STACKS},
+        "stacks": {k: {"value": tflops[k], "unit": "TFLOP/s",
+                       "ms_per_step": 1e3 * tk[k] / args.steps} for k in STACKS},
         "sweep": {"value": vsw, "unit": "evals/s", "instances": n_inst, "trials": 1000,
-                  "ms_per_step": 1e3 * tsw / args.steps, "roofline": sweep_roof},
-        "roofline": roof,
+                  "ms_per_step": 1e3 * wall["sweep"] / args.steps, "path": "per-size kernels"},
+        "sweep_plan": {"value": vplan, "unit": "evals/s",
+                       "ms_per_step": 1e3 * wall["plan"] / args.steps,
+                       "mode": {1: "persistent", 2: "persistent3", 3: "per_size"}.get(
+                           plan_info["mode"], plan_info["mode"]),
+                       "grid": plan_info["grid"], "work_items": plan_info["items"]},
+        "guided": {"wall_ms_per_step": 1e3 * wall["guided"] / args.steps,
+                   "plain_sweep_wall_ms_per_step": 1e3 * wall["sweep"] / args.steps,
+                   "speedup_vs_plain": wall["sweep"] / wall["guided"],
+                   "evaluated_instances": g_last["evaluated"], "fallback_rows": g_last["fallback_rows"],
+                   "rows": g_last["rows"], "max_best_err_ratio_vs_exhaustive": ratio,
+                   "median_best_err_ratio_vs_exhaustive": ratio_med,
+                   "best_rank_in_exhaustive_row": {"median": float(np.median(ranks)),
+                                                    "p90": float(np.percentile(ranks, 90)),
+                                                    "of": int(cg.size)},
+                   "phase_ms": g_last["phase_ms"],
+                   "training": {"samples": int(ys.numel()), "label_s": t_label,
+                                "train_s": t_train, "epochs": SURROGATE_EPOCHS, "batch": 4096}},
+        "roofline": roofs[dom],
+        "rooflines": roofs,
         "e2e": {"value": ve2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -373,49 +466,49 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def fp32_peak_tflops(clk):
+def fp32_peak_tflops():
     return SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
-def roofline_for(kernel, ms, n, layers, N, peaks, peak_src, clk):
-    """Algorithmic work per launch of the dominant layer kernel / its mean
-    event-timed duration."""
-    if n == 0:
-        return None
-    # launches alternate F(4x4) and F(6x6) stacks: average the per-launch work
-    works = []
-    for m in (4, 6):
-        a = m + 2
-        for C, H in layers:
-            th = (H + m - 1) // m
-            T = N * th * th
-            if kernel == "wino_gemm":
-                works.append(2.0 * a * a * T * C * C)
-            elif kernel == "input_transform":
-                works.append(4.0 * (N * C * H * H + a * a * C * T))
-            elif kernel == "output_transform":
-                works.append(4.0 * (a * a * C * T + N * C * H * H))
-            elif kernel == "fused_layer":
-                works.append(2.0 * a * a * T * C * C)
-            else:
-                works.append(4.0 * (9 * C * C + a * a * C * C))
-    per_launch = sum(works) / len(works)
+def _tiles(m, H, N):
+    th = (H + m - 1) // m
+    return N * th * th
+
+
+def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
+    """Algorithmic work of one launch of `kernel` (averaged over the launches
+    of one step) / its mean CUDA-event duration, against the kernel's bound."""
     sec = ms / 1e3 / n
-    if kernel in ("wino_gemm", "fused_layer"):
-        peak = fp32_peak_tflops(clk)
-        ach = per_launch / sec / 1e12
-        return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "work_per_launch": per_launch, "launches": n}
-    peak = peaks["hbm_gbs"]
-    ach = per_launch / sec / 1e9
-    return {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "traffic": None, "peak_source": peak_src + " (of %s)" % peak_src,
-            "work_per_launch": per_launch, "launches": n}
-
-
-SWEEP_FLOPS_PER_TRIAL = None
+    per_step = n / steps
+    fp32 = {"bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak_tflops(),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    hbm = {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+           "peak_source": "%s copy bandwidth (of %s)" % (peak_src, peak_src)}
+    work = None
+    if kernel == "fused_layer":  # FP32 stacks F(4x4) and F(6x6): GEMM flops per launch
+        w = [2.0 * (m + 2) ** 2 * _tiles(m, H, N) * C * C for m in (4, 6) for C, H in layers]
+        work, base = sum(w) / len(w), fp32
+    elif kernel == "input_transform":  # split variant: read x, write U (FP32 stacks)
+        w = [4.0 * (N * C * H * H + (m + 2) ** 2 * C * _tiles(m, H, N))
+             for m in (4, 6) for C, H in layers]
+        work, base = sum(w) / len(w), hbm
+    elif kernel == "tc_gemm":  # BF16 and split-BF16x3 F(4x4) stacks
+        w = [2.0 * 36 * ((_tiles(4, H, N) + 127) // 128 * 128) * C * C * f
+             for f in (1, 3) for C, H in layers]
+        work = sum(w) / len(w)
+        base = {"bound": "tensor", "unit": "TFLOP/s", "peak": peaks["bf16_tflops"],
+                "peak_source": "%s cuBLAS bf16 dense, burst (of %s)" % (peak_src, peak_src)}
+    elif kernel == "sweep_eval":  # per-size sweep kernels + the persistent launch
+        work = 2 * sweep_flops_total() / per_step
+        base = fp32
+    if work is None:
+        return None
+    scale = 1e9 if base["unit"] == "GB/s" else 1e12
+    ach = work / sec / scale
+    return dict(kernel=kernel, bound=base["bound"], achieved=ach, peak=base["peak"],
+                unit=base["unit"], frac=ach / base["peak"], traffic=None,
+                peak_source=base["peak_source"], work_per_launch=work, launches_per_step=per_step,
+                mean_launch_ms=ms / n)
 
 
 def sweep_flops_total():
@@ -438,18 +531,6 @@ def sweep_flops_total():
             f = 2 * (a * r * r + a * a * r) + 4 * a ** 3 + a * a + 2 * (m * a * a + m * m * a)
         tot += nmask * 4096 * 1000 * f
     return tot
-
-
-def sweep_roofline(ms, n, steps, clk):
-    if n == 0:
-        return None
-    sec = ms / 1e3 / steps  # the per-size eval launches of one sweep
-    ach = sweep_flops_total() / sec / 1e12
-    peak = fp32_peak_tflops(clk)
-    return {"kernel": "sweep_eval", "bound": "alu", "achieved": ach, "peak": peak,
-            "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-            "launches_per_sweep": n // steps}
 
 
 def profile_case(name):

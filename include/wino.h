@@ -156,6 +156,10 @@ typedef struct {
  * FP32 Winograd (transforms and Hadamard product in FP32, matrices built in
  * FP64 and rounded once) and scored against the FP64 direct correlation:
  *   err = sum_t ||yhat_t - y_t||_1 / sum_t ||y_t||_1.
+ * Summation order (the same in wino_error_sweep and every planned-sweep
+ * mode, so all return the same bits): per trial the terms in FP32, trials in
+ * chunks of 128 summed in FP64 from zero, chunk sums added in ascending
+ * order.
  * err_out is a caller-owned HOST array [n_sizes][n_subsets][n_c] (FP64).
  * c_grid, sizes, subsets are host arrays.  Synchronises `cuda_stream`.     */
 int wino_error_sweep(const double* c_grid, int n_c,
@@ -247,10 +251,67 @@ int wino_sweep_plan_set_deadline(void* plan, double max_ms);
  * instance order.                                                          */
 int wino_sweep_plan_run(void* plan, double* err_out, void* cuda_stream);
 
+/* Replaces the c of every instance (c[n_inst], host, the caller's instance
+ * order) keeping sizes and masks, so the plan and its graph are reused;
+ * synchronises the plan's stream.                                          */
+int wino_sweep_plan_set_c(void* plan, const double* c, int64_t n);
+
 /* The mode the plan runs, its persistent grid size and its work items.    */
 int wino_sweep_plan_info(void* plan, int* mode, int* grid, int* n_items);
 
 void wino_sweep_plan_destroy(void* plan);
+
+/* ---------------------------------------------------------------------- */
+/* Learned surrogate of the sweep.  The paper has no surrogate; its         */
+/* observation that the error curve over c is roughly smooth (Sec. 6.1)     */
+/* motivates ranking a dense c grid with a small network and evaluating     */
+/* only the best candidates exactly.                                        */
+/* ---------------------------------------------------------------------- */
+
+#define WINO_MLP_INPUTS 16
+#define WINO_MLP_HIDDEN 64
+#define WINO_MLP_PARAMS 1153 /* W1 64x16 | b1 64 | w2 64 | b2 1 */
+
+/* f(x) = w2 . gelu(W1 x + b1) + b2, gelu(z) = z (1 + erf(z / sqrt 2)) / 2,
+ * predicting log10 of an instance's sweep error.  FP32 master parameters,
+ * BF16-rounded working copy used by the forward and backward passes; MSE
+ * loss; Adam (beta1 0.9, beta2 0.999, eps 1e-8).  Creates a network with
+ * uniform(-sqrt(6/fan_in), +) weights and zero biases from `seed`.       */
+int wino_mlp_create(unsigned long long seed, void** mlp);
+/* Host arrays of WINO_MLP_PARAMS floats; set resets the Adam state.      */
+int wino_mlp_set_params(void* mlp, const float* params);
+int wino_mlp_get_params(void* mlp, float* params, int working);
+/* Features X[n][16] (device) of instances (host array):
+ * [m/8, (r-3)/2, mask bits 0..7, u, dim - 1, u^2, |u|, u^3, 0] with
+ * u = ln c / ln 20.
+ * Synchronises `cuda_stream`.                                              */
+int wino_mlp_features(const wino_size* sizes, int n_sizes,
+                      const wino_instance* inst, int64_t n, float* X,
+                      void* cuda_stream);
+/* Features of a grid (device X[n_rows * n_c][16], row-major): row q is
+ * (sizes[row_size[q]], row_mask[q]) at every c of c_grid.  Host inputs;
+ * synchronises `cuda_stream`.                                              */
+int wino_mlp_grid_features(const wino_size* sizes, int n_sizes,
+                           const int* row_size, const unsigned char* row_mask,
+                           int n_rows, const double* c_grid, int n_c, float* X,
+                           void* cuda_stream);
+/* Mean squared error of the batch (X[B][16], y[B] device) at the working
+ * weights and its gradient (host, WINO_MLP_PARAMS floats).               */
+int wino_mlp_loss_grad(void* mlp, const float* X, const float* y, int B,
+                       float* grad, double* loss, void* cuda_stream);
+/* `epochs` passes over n samples (device) in whole batches of `batch`, in
+ * order; one epoch is captured as a CUDA graph and replayed.              */
+int wino_mlp_train(void* mlp, const float* X, const float* y, int64_t n,
+                   int batch, int epochs, float lr, void* cuda_stream);
+/* out[n] (device) = f(X[n][16]) at the working weights.                  */
+int wino_mlp_predict(void* mlp, const float* X, int64_t n, float* out,
+                     void* cuda_stream);
+/* Indices of the k smallest values of each row of vals[rows][cols]
+ * (device, ascending, ties by index, NaN last) into idx[rows][k] (device);
+ * cols <= 8192.                                                            */
+int wino_topk_rows(const float* vals, int rows, int cols, int k, int* idx,
+                   void* cuda_stream);
+void wino_mlp_destroy(void* mlp);
 
 /* ---------------------------------------------------------------------- */
 /* Library state.                                                           */

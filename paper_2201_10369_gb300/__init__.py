@@ -80,6 +80,27 @@ def _declare(L):
     L.wino_sweep_plan_info.restype = _i
     L.wino_sweep_plan_destroy.argtypes = [_vp]
     L.wino_sweep_plan_destroy.restype = None
+    _FP = ctypes.POINTER(ctypes.c_float)
+    L.wino_mlp_create.argtypes = [ctypes.c_ulonglong, ctypes.POINTER(_vp)]
+    L.wino_mlp_set_params.argtypes = [_vp, _FP]
+    L.wino_mlp_get_params.argtypes = [_vp, _FP, _i]
+    L.wino_mlp_features.argtypes = [ctypes.POINTER(WinoSize), _i, ctypes.POINTER(WinoInstance),
+                                    ctypes.c_int64, _vp, _vp]
+    L.wino_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _i, _FP, _DP, _vp]
+    L.wino_mlp_train.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _i, _i, ctypes.c_float, _vp]
+    L.wino_mlp_predict.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+    L.wino_topk_rows.argtypes = [_vp, _i, _i, _i, _vp, _vp]
+    L.wino_mlp_grid_features.argtypes = [ctypes.POINTER(WinoSize), _i, ctypes.POINTER(_i),
+                                         ctypes.POINTER(ctypes.c_ubyte), _i, _DP, _i, _vp, _vp]
+    L.wino_mlp_grid_features.restype = _i
+    L.wino_sweep_plan_set_c.argtypes = [_vp, _DP, ctypes.c_int64]
+    L.wino_sweep_plan_set_c.restype = _i
+    for nm in ("wino_mlp_create", "wino_mlp_set_params", "wino_mlp_get_params",
+               "wino_mlp_features", "wino_mlp_loss_grad", "wino_mlp_train", "wino_mlp_predict",
+               "wino_topk_rows"):
+        getattr(L, nm).restype = _i
+    L.wino_mlp_destroy.argtypes = [_vp]
+    L.wino_mlp_destroy.restype = None
     L.wino_profile_enable.argtypes = [_i]
     L.wino_profile_enable.restype = _i
     L.wino_profile_read.argtypes = [ctypes.c_char_p, _DP, ctypes.POINTER(ctypes.c_int)]
@@ -297,12 +318,10 @@ class SweepPlan:
         self._L = L
         sz = (WinoSize * len(sizes))(*[WinoSize(int(a), int(b), int(c), float(d))
                                        for a, b, c, d in sizes])
-        n = len(instances)
-        arr = (WinoInstance * n)()
-        for i, (s, mk, c) in enumerate(instances):
-            arr[i].size, arr[i].mask, arr[i].c = int(s), int(mk), float(c)
+        arr, ptr = _instances(instances)
+        n = arr.size
         h = ctypes.c_void_p()
-        _check(L.wino_sweep_plan_create(sz, len(sizes), arr, n, trials, seed, mode,
+        _check(L.wino_sweep_plan_create(sz, len(sizes), ptr, n, trials, seed, mode,
                                         ctypes.byref(h)))
         self._h = h
         self.n = n
@@ -332,6 +351,307 @@ class SweepPlan:
             self.close()
         except Exception:
             pass
+
+
+MLP_PARAMS = 1153
+
+
+# numpy layout of wino_instance (int size, unsigned char mask, padding, double c)
+INSTANCE_DTYPE = np.dtype([("size", "<i4"), ("mask", "u1"), ("pad", "u1", (3,)), ("c", "<f8")])
+
+
+def instance_array(size_idx, mask, c) -> np.ndarray:
+    """Instances as an INSTANCE_DTYPE array (broadcasting the three fields)."""
+    c = np.asarray(c, dtype=np.float64)
+    size_idx, mask, c = np.broadcast_arrays(np.asarray(size_idx), np.asarray(mask), c)
+    a = np.zeros(c.size, dtype=INSTANCE_DTYPE)
+    a["size"] = size_idx.ravel()
+    a["mask"] = mask.ravel()
+    a["c"] = c.ravel()
+    return a
+
+
+def _instances(instances):
+    """(array, ctypes pointer) of wino_instance records from (size, mask, c)
+    tuples or an INSTANCE_DTYPE array."""
+    if isinstance(instances, np.ndarray) and instances.dtype == INSTANCE_DTYPE:
+        a = np.ascontiguousarray(instances)
+    else:
+        s, m, c = zip(*instances) if len(instances) else ((), (), ())
+        a = instance_array(np.array(s, dtype=np.int32), np.array(m, dtype=np.uint8),
+                           np.array(c, dtype=np.float64))
+    return a, a.ctypes.data_as(ctypes.POINTER(WinoInstance))
+
+
+def _sizes(sizes):
+    return (WinoSize * len(sizes))(*[WinoSize(int(a), int(b), int(c), float(d))
+                                     for a, b, c, d in sizes])
+
+
+class Surrogate:
+    """The learned surrogate (wino_mlp_*): a 16-64-1 GELU network on the
+    device predicting log10 of an instance's sweep error."""
+
+    def __init__(self, seed: int = 0):
+        L = load()
+        self._L = L
+        h = ctypes.c_void_p()
+        _check(L.wino_mlp_create(seed, ctypes.byref(h)))
+        self._h = h
+
+    def params(self, working: bool = False) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(self._L.wino_mlp_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           1 if working else 0))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self._L.wino_mlp_set_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def features(self, sizes, instances, stream=None):
+        return instance_features(sizes, instances, stream)
+
+    def loss_grad(self, X, y, stream=None):
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(self._L.wino_mlp_loss_grad(self._h, _ptr(X), _ptr(y), X.shape[0],
+                                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          ctypes.byref(loss), _stream(stream)))
+        return loss.value, g
+
+    def set_output_bias(self, b: float):
+        """Starts the output bias at b (e.g. the label mean); resets Adam."""
+        p = self.params()
+        p[-1] = b
+        self.set_params(p)
+
+    def train(self, X, y, batch: int = 4096, epochs: int = 1, lr: float = 1e-3, stream=None):
+        _check(self._L.wino_mlp_train(self._h, _ptr(X), _ptr(y), X.shape[0], batch, epochs, lr,
+                                      _stream(stream)))
+
+    def predict(self, X, stream=None):
+        import torch
+        out = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        _check(self._L.wino_mlp_predict(self._h, _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.wino_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wino_topk_rows(vals, k: int, stream=None):
+    """Indices (CUDA int32 [rows][k]) of the k smallest values of each row."""
+    import torch
+    rows, cols = vals.shape
+    idx = torch.empty((rows, k), dtype=torch.int32, device="cuda")
+    _check(load().wino_topk_rows(_ptr(vals), rows, cols, k, _ptr(idx), _stream(stream)))
+    return idx
+
+
+def valid_masks(size, masks):
+    """The masks of `masks` valid for size (dim, m, r, d): popcount alpha - 2,
+    and bits 4 and 7 unused when |d| = 1 (the rule of wino_error_sweep)."""
+    dim, m, r, d = size
+    out = []
+    for mk in masks:
+        mk = int(mk)
+        if bin(mk).count("1") != m + r - 3:
+            continue
+        if abs(d) == 1.0 and (mk & 0x90):
+            continue
+        out.append(mk)
+    return out
+
+
+LABEL_CLIP = -3.0  # labels are min(log10 err, -3)
+
+
+def instance_features(sizes, instances, stream=None):
+    """Surrogate features (device [n][16]) of instances (tuples or an
+    INSTANCE_DTYPE array)."""
+    import torch
+    arr, ptr = _instances(instances)
+    X = torch.empty((arr.size, 16), dtype=torch.float32, device="cuda")
+    _check(load().wino_mlp_features(_sizes(sizes), len(sizes), ptr, arr.size, _ptr(X),
+                                    _stream(stream)))
+    return X
+
+
+def surrogate_training_set(sizes, masks, n: int, trials: int, seed: int = 0, c_lo=0.05, c_hi=20.0):
+    """n random instances (size, valid mask, c log-uniform in [c_lo, c_hi]),
+    their sweep errors from one planned launch, and labels min(log10 err,
+    LABEL_CLIP); instances whose points coincide are dropped.  Returns
+    (instances as an INSTANCE_DTYPE array, X, y) with X, y on the device."""
+    import torch
+    rng = np.random.default_rng(seed)
+    per = [np.array(valid_masks(s, masks), dtype=np.uint8) for s in sizes]
+    cand = np.array([i for i, p in enumerate(per) if p.size], dtype=np.int32)
+    sidx = cand[rng.integers(cand.size, size=n)]
+    mk = np.empty(n, dtype=np.uint8)
+    for s in cand:
+        sel = sidx == s
+        mk[sel] = per[s][rng.integers(per[s].size, size=int(sel.sum()))]
+    c = np.exp(rng.uniform(np.log(c_lo), np.log(c_hi), n))
+    inst = instance_array(sidx, mk, c)
+    plan = SweepPlan(sizes, inst, trials, seed=seed, mode=WINO_SWEEP_PERSISTENT)
+    try:
+        err = plan.run()
+    finally:
+        plan.close()
+    keep = np.isfinite(err) & (err > 0)
+    inst = inst[keep]
+    # errors above 1e-3 are far from any useful point set; clipping them keeps
+    # the rare near-singular spikes from dominating the squared loss
+    y = torch.from_numpy(np.minimum(np.log10(err[keep]), LABEL_CLIP).astype(np.float32)).cuda()
+    return inst, instance_features(sizes, inst), y
+
+
+class GuidedSearch:
+    """Surrogate-guided search of a c grid for every valid (size, mask) row.
+
+    Built once: the grid's features (device), the rows, and two planned
+    sweeps whose graphs are captured once.  Each run():
+      1. the network ranks every c of every row (predict kernel) and the
+         `top` best predictions per row (top-k kernel) plus `probe` random
+         grid points per row are evaluated exactly in one graph launch;
+      2. the `2 refine + 1` grid points around each row's best verified c
+         are evaluated in a second launch (the error curve is smooth at
+         large scale but noisy between neighbouring c, Sec. 6.1);
+      3. a row whose proposals' best is worse than `guard` x its probe's
+         best (the network failed there) is searched exhaustively.
+    """
+
+    def __init__(self, model, sizes, masks, c_grid, trials: int, seed: int = 0, top: int = 64,
+                 probe: int = 64, refine: int = 32, guard: float = 1.01):
+        import torch
+        L = load()
+        self.model, self.sizes, self.trials, self.seed = model, list(sizes), trials, seed
+        self.top, self.probe, self.refine, self.guard = top, probe, refine, guard
+        self.cg = np.ascontiguousarray(c_grid, dtype=np.float64)
+        self.masks = [int(mk) for mk in masks]
+        self.rows = [(s, mk) for s in range(len(sizes)) for mk in valid_masks(sizes[s], self.masks)]
+        rs = np.array([s for s, _ in self.rows], dtype=np.int32)
+        rm = np.array([mk for _, mk in self.rows], dtype=np.uint8)
+        self.rs, self.rm = rs, rm
+        self.X = torch.empty((len(self.rows) * self.cg.size, 16), dtype=torch.float32,
+                             device="cuda")
+        _check(L.wino_mlp_grid_features(_sizes(sizes), len(sizes),
+                                        rs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        rm.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                        len(self.rows), self.cg.ctypes.data_as(_DP), self.cg.size,
+                                        _ptr(self.X), _stream(None)))
+        nr = len(self.rows)
+        c0 = float(self.cg[self.cg.size // 3])
+        self.verify = SweepPlan(sizes, instance_array(np.repeat(rs, top + probe),
+                                                      np.repeat(rm, top + probe), c0),
+                                trials, seed=seed, mode=WINO_SWEEP_PERSISTENT)
+        self.local = SweepPlan(sizes, instance_array(np.repeat(rs, 2 * refine + 1),
+                                                     np.repeat(rm, 2 * refine + 1), c0),
+                               trials, seed=seed, mode=WINO_SWEEP_PERSISTENT)
+        self.rng = np.random.default_rng(seed + 1)
+        self.nr = nr
+
+    def _run_plan(self, plan, sel):
+        c = self.cg[sel].ravel()
+        _check(plan._L.wino_sweep_plan_set_c(plan._h, c.ctypes.data_as(_DP), c.size))
+        err = plan.run().reshape(sel.shape)
+        return np.where(np.isfinite(err), err, np.inf)
+
+    def run(self):
+        import time
+        t0 = time.perf_counter()
+        nr, nc = self.nr, self.cg.size
+        pred = self.model.predict(self.X).reshape(nr, nc)
+        idx = wino_topk_rows(pred, self.top).cpu().numpy()
+        t1 = time.perf_counter()
+        probe = self.rng.integers(0, nc, (nr, self.probe))
+        sel = np.concatenate([idx, probe], axis=1)
+        ev = self._run_plan(self.verify, sel)
+        t2 = time.perf_counter()
+        r_idx = np.arange(nr)
+        vt = ev[:, :self.top].min(axis=1)
+        vp = ev[:, self.top:].min(axis=1)
+        bi = sel[r_idx, np.argmin(ev, axis=1)]
+        # local refinement around each row's best verified grid point
+        off = np.arange(-self.refine, self.refine + 1)
+        lsel = np.clip(bi[:, None] + off[None, :], 0, nc - 1)
+        le = self._run_plan(self.local, lsel)
+        lb = np.argmin(le, axis=1)
+        use_l = le[r_idx, lb] < ev[r_idx, np.argmin(ev, axis=1)]
+        best_e = np.where(use_l, le[r_idx, lb], ev.min(axis=1))
+        best_i = np.where(use_l, lsel[r_idx, lb], bi)
+        evaluated = sel.size + lsel.size
+        t3 = time.perf_counter()
+        # rows where the network's proposals lost to the random probe: exhaustive
+        fallback = np.nonzero(vt > self.guard * vp)[0]
+        by_size = {}
+        for r in fallback:
+            by_size.setdefault(int(self.rs[r]), []).append(r)
+        for s, rlist in by_size.items():
+            e = wino_error_sweep(self.cg, [self.sizes[s]], [int(self.rm[r]) for r in rlist],
+                                 self.trials, self.seed)[0]
+            e = np.where(np.isfinite(e), e, np.inf)
+            for j, r in enumerate(rlist):
+                k = int(np.argmin(e[j]))
+                best_e[r], best_i[r] = e[j, k], k
+            evaluated += len(rlist) * nc
+        t4 = time.perf_counter()
+        best = np.full((len(self.sizes), len(self.masks)), np.nan)
+        best_c = np.full_like(best, np.nan)
+        for r, (s, mk) in enumerate(self.rows):
+            q = self.masks.index(mk)
+            best[s, q], best_c[s, q] = best_e[r], self.cg[best_i[r]]
+        return {"best_err": best, "best_c": best_c, "evaluated": int(evaluated),
+                "fallback_rows": int(fallback.size), "rows": nr,
+                "phase_ms": {"rank": 1e3 * (t1 - t0), "verify": 1e3 * (t2 - t1),
+                             "refine": 1e3 * (t3 - t2), "fallback": 1e3 * (t4 - t3)}}
+
+    def close(self):
+        self.verify.close()
+        self.local.close()
+
+
+def random_search(sizes, masks, c_grid, trials: int, budget: int, seed: int = 0):
+    """The search without the network, at a given per-row budget: `budget`
+    random grid points per valid (size, mask) row, evaluated in one planned
+    launch.  Returns best_err [n_sizes][n_masks]."""
+    cg = np.ascontiguousarray(c_grid, dtype=np.float64)
+    masks = [int(mk) for mk in masks]
+    rows = [(s, mk) for s in range(len(sizes)) for mk in valid_masks(sizes[s], masks)]
+    rng = np.random.default_rng(seed + 2)
+    sel = rng.integers(0, cg.size, (len(rows), budget))
+    rs = np.repeat(np.array([s for s, _ in rows], dtype=np.int32), budget)
+    rm = np.repeat(np.array([mk for _, mk in rows], dtype=np.uint8), budget)
+    plan = SweepPlan(sizes, instance_array(rs, rm, cg[sel].ravel()), trials, seed=seed,
+                     mode=WINO_SWEEP_PERSISTENT)
+    try:
+        err = plan.run().reshape(len(rows), budget)
+    finally:
+        plan.close()
+    err = np.where(np.isfinite(err), err, np.inf)
+    best = np.full((len(sizes), len(masks)), np.nan)
+    for r, (s, mk) in enumerate(rows):
+        best[s, masks.index(mk)] = err[r].min()
+    return best
+
+
+def guided_sweep(model, sizes, masks, c_grid, trials: int, seed: int = 0, top: int = 64,
+                 probe: int = 64, refine: int = 32, guard: float = 1.01):
+    """One surrogate-guided search (GuidedSearch built, run once, closed)."""
+    gs = GuidedSearch(model, sizes, masks, c_grid, trials, seed, top, probe, refine, guard)
+    try:
+        return gs.run()
+    finally:
+        gs.close()
 
 
 def grid_instances(sizes, masks, c_grid):

@@ -15,6 +15,9 @@
 //                    its instance's matrices in FP64, rounds them once to
 //                    FP32 into registers and runs all trials with the FP32
 //                    Winograd tile; trial records are warp-uniform loads.
+//                    A size with too few instances to fill the GPU spreads
+//                    each instance's trial chunks over several warps
+//                    (k_sweep_combine adds their partials in fixed order).
 // The FP32 tile follows the library's fixed operation order (fmaf over the
 // inner index ascending, one rounded Hadamard multiply), so yhat is
 // bit-identical to any implementation of the same order.  sweep_plan.cu
@@ -24,6 +27,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/wino.h"
@@ -130,27 +134,76 @@ struct MaskList {
   int n;
 };
 
-// One warp per (valid mask, block of 32 c values); lanes own instances.
+// One warp per (valid mask, block of 32 c values, chunk group); lanes own
+// instances.  split == 1: each lane runs every trial and writes its error to
+// err.  split > 1: the trial chunks are spread over `split` warps of ch_per
+// chunks each, which write partial sums to part (chunk stride n_out, the
+// size of the err block); k_sweep_combine turns them into errors.
 template <int DIM, int M, int R>
 __global__ void __launch_bounds__(128) k_sweep_eval(const float* __restrict__ rec, int trials,
                                                     const double* __restrict__ c_grid, int n_c,
                                                     double d, const MaskList masks,
                                                     const double* __restrict__ ysum,
-                                                    double* __restrict__ err) {
+                                                    double* __restrict__ err, int split,
+                                                    int ch_per, double* __restrict__ part,
+                                                    int64_t n_out) {
   const int lane = threadIdx.x & 31;
   const int nblk = (n_c + 31) >> 5;
-  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (item >= masks.n * nblk) return;
-  const int qv = item / nblk;
-  const int ci = (item - qv * nblk) * 32 + lane;
+  const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= (int64_t)masks.n * nblk * split) return;
+  const int grp = (int)(item % split);
+  const int cell = (int)(item / split);
+  const int qv = cell / nblk;
+  const int ci = (cell - qv * nblk) * 32 + lane;
   const bool active = ci < n_c;
   const double c = active ? c_grid[ci] : c_grid[0];
-  const double e = lane_error<DIM, M, R>(rec, trials, masks.mask[qv], c, d, *ysum);
-  if (active) err[(int64_t)masks.q[qv] * n_c + ci] = e;
+  const int64_t o = (int64_t)masks.q[qv] * n_c + ci;
+  const int nch = trial_chunks(trials);
+  const int ch0 = split == 1 ? 0 : grp * ch_per;
+  const int ch1 = split == 1 ? nch : min(ch0 + ch_per, nch);
+  lane_eval<DIM, M, R>(rec, trials, masks.mask[qv], c, d, ch0, ch1, *ysum, split > 1,
+                       split == 1 ? err + o : part + o, n_out, active);
 }
 
 typedef void (*EvalFn)(const float*, int, const double*, int, double, const MaskList,
-                       const double*, double*);
+                       const double*, double*, int, int, double*, int64_t);
+
+// err[i] = (sum over chunks ascending of part[ch * stride + i]) / ysum of the
+// instance's size.
+__global__ void k_sweep_combine(const double* __restrict__ part, int n_chunks, int64_t stride,
+                                int64_t n, const unsigned char* __restrict__ size_of,
+                                const double* __restrict__ ysum, double* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double num = 0.0;
+  for (int ch = 0; ch < n_chunks; ++ch) num += part[(int64_t)ch * stride + i];
+  err[i] = num / ysum[size_of ? size_of[i] : 0];
+}
+
+int sweep_combine(const double* part, int n_chunks, int64_t stride, int64_t n,
+                  const unsigned char* size_of, const double* ysum, double* err, cudaStream_t st) {
+  if (n <= 0) return WINO_OK;
+  k_sweep_combine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, n_chunks, stride, n, size_of,
+                                                              ysum, err);
+  note_launches(1);
+  WINO_CUDA_TRY(cudaGetLastError());
+  return WINO_OK;
+}
+
+int sweep_target_warps() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      sms = 1;
+    }
+  }
+  // 8 resident warps per SM (2 CTAs x 4 warps at the sweep's register use),
+  // four rounds of them
+  return sms * 8 * 4;
+}
 
 static EvalFn eval_kernel(int dim, int m, int r) {
 #define WINO_EVAL_CASE(I, D, MM, RR) \
@@ -193,7 +246,21 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
     rec_off[s] = rec_total;
     rec_total += (size_t)trials * sweep_rec_width(sizes[s].dim, sizes[s].m, sizes[s].r);
   }
-  // scratch layout: records | partials | ysum | c_grid | err
+  // per size: its valid masks and, when its items alone cannot fill the
+  // GPU, how many warps share each instance's trial chunks
+  std::vector<MaskList> ml(n_sizes);
+  std::vector<int> split(n_sizes, 1);
+  const int nblk = (n_c + 31) / 32;
+  const int n_chunks = trial_chunks(trials);
+  size_t n_part = 0;
+  for (int s = 0; s < n_sizes; ++s) {
+    ml[s] = valid_masks(sizes[s], subsets, n_subsets);
+    const int items = ml[s].n * nblk;
+    if (items > 0 && items < sweep_target_warps())
+      split[s] = std::min(n_chunks, (sweep_target_warps() + items - 1) / items);
+    if (split[s] > 1) n_part = std::max(n_part, (size_t)n_chunks * n_subsets * n_c);
+  }
+  // scratch layout: records | partials | ysum | c_grid | err | chunk partials
   const size_t n_err = (size_t)n_sizes * n_subsets * n_c;
   size_t off_part = rec_total * sizeof(float);
   off_part = (off_part + 255) & ~(size_t)255;
@@ -203,7 +270,9 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   off_c = (off_c + 255) & ~(size_t)255;
   size_t off_err = off_c + (size_t)n_c * sizeof(double);
   off_err = (off_err + 255) & ~(size_t)255;
-  const size_t total = off_err + n_err * sizeof(double);
+  size_t off_chunk = off_err + n_err * sizeof(double);
+  off_chunk = (off_chunk + 255) & ~(size_t)255;
+  const size_t total = off_chunk + n_part * sizeof(double);
   void* base = nullptr;
   int rc = scratch_get(kScratchSweep, total, &base);
   if (rc != WINO_OK) return rc;
@@ -213,26 +282,35 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   double* ysum = (double*)(b + off_ysum);
   double* cg = (double*)(b + off_c);
   double* err = (double*)(b + off_err);
+  double* chunk = (double*)(b + off_chunk);
 
   WINO_CUDA_TRY(cudaMemcpyAsync(cg, c_grid, n_c * sizeof(double), cudaMemcpyHostToDevice, st));
-  std::vector<MaskList> ml(n_sizes);
   for (int s = 0; s < n_sizes; ++s) {
     rc = sweep_prepare(rec + rec_off[s], part + (size_t)s * nb_prep, ysum + s, sizes[s].dim,
                        sizes[s].m, sizes[s].r, trials, seed, st);
     if (rc != WINO_OK) return rc;
-    ml[s] = valid_masks(sizes[s], subsets, n_subsets);
   }
-  const int nblk = (n_c + 31) / 32;
   for (int s = 0; s < n_sizes; ++s) {
     if (ml[s].n == 0) continue;
-    const int items = ml[s].n * nblk;
+    const int64_t n_out = (int64_t)n_subsets * n_c;
+    const int ch_per = (n_chunks + split[s] - 1) / split[s];
+    const int sp = (n_chunks + ch_per - 1) / ch_per;  // groups actually holding chunks
+    const int64_t warps = (int64_t)ml[s].n * nblk * (split[s] > 1 ? sp : 1);
     const int warps_per_block = 4;
-    const int grid = (items + warps_per_block - 1) / warps_per_block;
+    const unsigned grid = (unsigned)((warps + warps_per_block - 1) / warps_per_block);
     EvalFn fn = eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r);
-    ProfScope ps(kKSweepEval, st);
-    fn<<<grid, 32 * warps_per_block, 0, st>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
-                                               ml[s], ysum + s, err + (size_t)s * n_subsets * n_c);
-    note_launches(1);
+    double* es = err + (size_t)s * n_out;
+    {
+      ProfScope ps(kKSweepEval, st);
+      fn<<<grid, 32 * warps_per_block, 0, st>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
+                                                 ml[s], ysum + s, es, split[s] > 1 ? sp : 1,
+                                                 ch_per, chunk, n_out);
+      note_launches(1);
+    }
+    if (split[s] > 1) {
+      rc = sweep_combine(chunk, n_chunks, n_out, n_out, nullptr, ysum + s, es, st);
+      if (rc != WINO_OK) return rc;
+    }
   }
   WINO_CUDA_TRY(cudaGetLastError());
   WINO_CUDA_TRY(

@@ -139,19 +139,26 @@ __device__ __forceinline__ float tile_err_2d(const Mats<M, R>& Mx, const float* 
   return e;
 }
 
-// The error of one instance (mask, c) over `trials` warp-uniform trial
-// records: sum_t ||yhat_t - y_t||_1 / sum_t ||y_t||_1, +inf when two points
-// coincide.  Per trial the m (m^2) terms are summed in FP32, the trial sums
-// in FP64.
+// Summation order of the error's numerator, fixed for every execution path:
+// trials are taken in chunks of kTrialChunk; each chunk's per-trial FP32
+// sums are added in FP64 starting from zero, and the chunk sums are added in
+// ascending chunk order.  A path may therefore evaluate the chunks of one
+// instance in different warps (partials in memory, combined by
+// k_sweep_combine) and still return the same bits as one lane running them
+// all.
+constexpr int kTrialChunk = 128;
+__host__ __device__ constexpr int trial_chunks(int trials) {
+  return (trials + kTrialChunk - 1) / kTrialChunk;
+}
+
+// FP64 sum over trials [t0, t1) of the per-trial FP32 L1 error.
 template <int DIM, int M, int R>
-__device__ __forceinline__ double lane_error(const float* __restrict__ rec, int trials,
-                                             unsigned mask, double c, double d, double ysum) {
+__device__ __forceinline__ double chunk_error(const Mats<M, R>& Mx, const float* __restrict__ rec,
+                                              int t0, int t1) {
   using S = SweepShape<DIM, M, R>;
-  Mats<M, R> Mx;
-  const bool ok = build_instance<M, R>(mask, c, d, Mx);
   double num = 0.0;
   const float4* r4 = reinterpret_cast<const float4*>(rec);
-  for (int t = 0; t < trials; ++t) {
+  for (int t = t0; t < t1; ++t) {
     float buf[S::REC];
 #pragma unroll
     for (int q = 0; q < S::REC / 4; ++q) {
@@ -164,8 +171,44 @@ __device__ __forceinline__ double lane_error(const float* __restrict__ rec, int 
     const float e = (DIM == 1) ? tile_err_1d<M, R>(Mx, buf) : tile_err_2d<M, R>(Mx, buf);
     num += (double)e;
   }
-  return ok ? num / ysum : (double)INFINITY;
+  return num;
 }
+
+// One lane's instance (mask, c) over trial chunks [ch0, ch1) of `trials`
+// warp-uniform trial records.  partial == false (the lane owns every chunk):
+// *out = sum_t ||yhat_t - y_t||_1 / sum_t ||y_t||_1, +inf when two points
+// coincide.  partial == true: out[ch * stride] = the chunk's sum (+inf when
+// two points coincide), for k_sweep_combine.  Per trial the m (m^2) terms are
+// summed in FP32, the trial sums in FP64 in the chunked order above.
+template <int DIM, int M, int R>
+__device__ __forceinline__ void lane_eval(const float* __restrict__ rec, int trials,
+                                          unsigned mask, double c, double d, int ch0, int ch1,
+                                          double ysum, bool partial, double* __restrict__ out,
+                                          int64_t stride, bool active) {
+  Mats<M, R> Mx;
+  const bool ok = build_instance<M, R>(mask, c, d, Mx);
+  double num = 0.0;
+  for (int ch = ch0; ch < ch1; ++ch) {
+    const int t0 = ch * kTrialChunk;
+    const double s = chunk_error<DIM, M, R>(Mx, rec, t0, min(t0 + kTrialChunk, trials));
+    if (partial) {
+      if (active) out[(int64_t)ch * stride] = ok ? s : (double)INFINITY;
+    } else {
+      num += s;
+    }
+  }
+  if (!partial && active) *out = ok ? num / ysum : (double)INFINITY;
+}
+
+// Partial chunk sums -> errors: err[i] = (sum over chunks ascending of
+// part[ch * stride + i]) / ysum of the instance's size, where the size is
+// size_of[i] (or 0 when size_of is null).  sweep.cu.
+int sweep_combine(const double* part, int n_chunks, int64_t stride, int64_t n,
+                  const unsigned char* size_of, const double* ysum, double* err, cudaStream_t st);
+
+// How many warps a chunk-split sweep launch aims for: enough items that a
+// launch of few instances still fills every SM several times over.
+int sweep_target_warps();
 
 // Sizes the sweep is compiled for, as (index, dim, m, r) cases.
 #define WINO_SWEEP_SIZES(X) \

@@ -6,7 +6,11 @@
 // by decreasing cost (trials x dense flops per trial: longest first, so the
 // last items to start are the cheapest).  A persistent grid of warps pulls
 // items from an atomic counter; each item dispatches to the size's
-// compile-time evaluator (sweep_eval.cuh).  A device-side deadline
+// compile-time evaluator (sweep_eval.cuh).  A plan too small to fill the
+// GPU (fewer groups of 32 than four rounds of resident warps) gives each
+// group several items, one per range of trial chunks; their partial sums
+// are combined in fixed order afterwards, so the errors are the same bits
+// either way.  A device-side deadline
 // (%globaltimer) lets the kernel stop taking work and report WINO_ETIMEOUT
 // instead of running unbounded; there is no spin-wait anywhere.  The graph
 // holds the counter/status resets, the trial records of every size
@@ -35,8 +39,11 @@
 
 namespace wino {
 
+// 32 instances of one size (sorted positions first .. first + count - 1)
+// and the trial chunks [c0, c1) this item runs for them.
 struct WorkItem {
-  int size, first, count, pad;
+  int size, first;
+  unsigned short count, pad, c0, c1;
 };
 
 struct PlanDev {
@@ -53,7 +60,10 @@ struct PlanDev {
   const double* dval;      // per size
   const double* ysum;      // per size
   double* err;             // per sorted instance
+  double* part;            // chunk partials [chunk][sorted instance] when split
+  int64_t n_sorted;
   int trials;
+  int split;               // 1: items cover all chunks and write err directly
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -67,9 +77,10 @@ __device__ __noinline__ void eval_item_as(const PlanDev& P, const WorkItem& w, i
   const int i = w.first + lane;
   const bool active = lane < w.count;
   const int ii = active ? i : w.first;
-  const double e = lane_error<D, MM, RR>(P.rec + P.rec_off[w.size], P.trials, P.inst_mask[ii],
-                                         P.inst_c[ii], P.dval[w.size], P.ysum[w.size]);
-  if (active) P.err[i] = e;
+  const bool partial = P.split > 1;
+  lane_eval<D, MM, RR>(P.rec + P.rec_off[w.size], P.trials, P.inst_mask[ii], P.inst_c[ii],
+                       P.dval[w.size], w.c0, w.c1, P.ysum[w.size], partial,
+                       partial ? P.part + i : P.err + i, P.n_sorted, active);
 }
 
 __device__ __forceinline__ void eval_item(const PlanDev& P, const WorkItem& w, int lane) {
@@ -158,6 +169,7 @@ struct SweepPlan {
   std::vector<SweepSize> sizes;
   std::vector<int> kind;
   std::vector<int64_t> order;      // sorted position -> caller's instance index
+  unsigned char* size_of = nullptr;  // device: size index per sorted instance
   std::vector<char> invalid;       // per caller instance: mask invalid for its size
   std::vector<WorkItem> items;     // LPT order
   std::vector<int> size_first, size_count;  // items of each size (per-size mode)
@@ -224,6 +236,11 @@ static int plan_enqueue(SweepPlan* p, int mode, cudaStream_t st) {
     }
   }
   WINO_CUDA_TRY(cudaGetLastError());
+  if (p->P.split > 1) {
+    int rc = sweep_combine(p->P.part, trial_chunks(p->trials), p->P.n_sorted, p->P.n_sorted,
+                           p->size_of, p->ysum, p->P.err, st);
+    if (rc != WINO_OK) return rc;
+  }
   WINO_CUDA_TRY(cudaMemcpyAsync(p->err_h, p->P.err, sizeof(double) * (size_t)p->n_inst,
                                 cudaMemcpyDeviceToHost, st));
   WINO_CUDA_TRY(
@@ -376,14 +393,29 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   }
   p->size_first.assign(n_sizes, 0);
   p->size_count.assign(n_sizes, 0);
+  // a plan of few instances spreads each group's trial chunks over several
+  // items so that the launch still fills the GPU
+  const int n_chunks = trial_chunks(trials);
+  int64_t base_items = 0;
+  for (int s = 0; s < n_sizes; ++s) base_items += ((int64_t)by_size[s].size() + 31) / 32;
+  int split = 1;
+  if (base_items > 0 && base_items < sweep_target_warps())
+    split = (int)std::min<int64_t>(n_chunks, (sweep_target_warps() + base_items - 1) / base_items);
+  const int ch_per = (n_chunks + split - 1) / split;
+  const int groups = (n_chunks + ch_per - 1) / ch_per;
   std::vector<std::pair<double, WorkItem>> tmp;
   for (int s = 0; s < n_sizes; ++s) {
-    const double cost =
-        sweep_trial_flops(p->sizes[s].dim, p->sizes[s].m, p->sizes[s].r) * trials;
+    const double flops = sweep_trial_flops(p->sizes[s].dim, p->sizes[s].m, p->sizes[s].r);
     for (size_t j = 0; j < by_size[s].size(); j += 32) {
-      WorkItem w{s, (int)p->order.size(), (int)std::min<size_t>(32, by_size[s].size() - j), 0};
-      for (int l = 0; l < w.count; ++l) p->order.push_back(by_size[s][j + l]);
-      tmp.push_back({cost * w.count / 32.0 + 1e-9 * s, w});
+      const int first = (int)p->order.size();
+      const int count = (int)std::min<size_t>(32, by_size[s].size() - j);
+      for (int l = 0; l < count; ++l) p->order.push_back(by_size[s][j + l]);
+      for (int g = 0; g < groups; ++g) {
+        const int c0 = g * ch_per, c1 = std::min(c0 + ch_per, n_chunks);
+        const int t_in = std::min(c1 * kTrialChunk, trials) - c0 * kTrialChunk;
+        WorkItem w{s, first, (unsigned short)count, 0, (unsigned short)c0, (unsigned short)c1};
+        tmp.push_back({flops * t_in * count / 32.0 + 1e-9 * s, w});
+      }
     }
   }
   std::stable_sort(tmp.begin(), tmp.end(),
@@ -443,6 +475,10 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   o = al(o + (size_t)n_inst * 8);
   const size_t o_items = o;
   o = al(o + std::max<size_t>(p->items.size(), 1) * sizeof(WorkItem));
+  const size_t o_isz = o;
+  o = al(o + (size_t)std::max<int64_t>(n_sorted, 1));
+  const size_t o_chunk = o;
+  if (groups > 1) o = al(o + (size_t)n_chunks * n_sorted * 8);
   const size_t o_ctr = o;
   o = al(o + 64);
   if (cudaMalloc(&p->dbuf, o) != cudaSuccess) {
@@ -456,11 +492,13 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   p->part = (double*)(b + o_part);
   p->ysum = (double*)(b + o_ysum);
   p->deadline = (unsigned long long*)(b + o_ctr + 16);
+  p->size_of = (unsigned char*)(b + o_isz);
   std::vector<double> cs(n_sorted), dv(n_sizes);
-  std::vector<unsigned char> ms(n_sorted);
+  std::vector<unsigned char> ms(n_sorted), zs(n_sorted);
   for (int64_t j = 0; j < n_sorted; ++j) {
     cs[j] = inst[p->order[j]].c;
     ms[j] = inst[p->order[j]].mask;
+    zs[j] = (unsigned char)inst[p->order[j]].size;
   }
   for (int s = 0; s < n_sizes; ++s) dv[s] = p->sizes[s].d;
   cudaError_t e = cudaSuccess;
@@ -471,6 +509,8 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
     e = cudaMemcpy(b + o_c, cs.data(), n_sorted * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && n_sorted)
     e = cudaMemcpy(b + o_mask, ms.data(), n_sorted, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n_sorted)
+    e = cudaMemcpy(b + o_isz, zs.data(), n_sorted, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !p->items.empty())
     e = cudaMemcpy(b + o_items, p->items.data(), p->items.size() * sizeof(WorkItem),
                    cudaMemcpyHostToDevice);
@@ -499,7 +539,10 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   P.dval = (const double*)(b + o_dval);
   P.ysum = p->ysum;
   P.err = (double*)(b + o_err);
+  P.part = (double*)(b + o_chunk);
+  P.n_sorted = n_sorted;
   P.trials = trials;
+  P.split = groups;
 
   if (mode == WINO_SWEEP_AUTO) {
     rc = plan_autotune(p);
@@ -549,6 +592,28 @@ int wino_sweep_plan_run(void* plan, double* err_out, void* cuda_stream) {
     set_error("sweep stopped at its deadline before all instances were evaluated");
     return WINO_ETIMEOUT;
   }
+  return WINO_OK;
+}
+
+int wino_sweep_plan_set_c(void* plan, const double* c, int64_t n) {
+  SweepPlan* p = (SweepPlan*)plan;
+  if (!p || !c || n != p->n_inst) {
+    set_error("wino_sweep_plan_set_c needs one c per instance of the plan");
+    return WINO_EINVAL;
+  }
+  std::vector<double> cs(p->order.size());
+  for (size_t j = 0; j < p->order.size(); ++j) {
+    const double v = c[p->order[j]];
+    if (!(v > 0.0) || isinf(v)) {
+      set_error("c values must be finite and > 0");
+      return WINO_EINVAL;
+    }
+    cs[j] = v;
+  }
+  if (!cs.empty())
+    WINO_CUDA_TRY(cudaMemcpyAsync((void*)p->P.inst_c, cs.data(), cs.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, p->st));
+  WINO_CUDA_TRY(cudaStreamSynchronize(p->st));
   return WINO_OK;
 }
 

@@ -162,6 +162,131 @@ __global__ void __launch_bounds__(256) k_quant_input(const float* __restrict__ x
     }
 }
 
+// Tiled form of the same input quantisation: one block = 16 tiles x 16
+// channels; a thread transforms one (tile, channel) with tiles fastest
+// (neighbouring patches share input rows), the 16-bit results meet in
+// shared memory and leave as 32-byte rows of 16 channels.
+constexpr int kQT = 16, kQC = 16;
+template <int MM>
+__global__ void __launch_bounds__(kQT* kQC) k_quant_input_tiled(
+    const float* __restrict__ x, const LayerGeom g, const LayerMats Mx, const TcScales S, int Cp,
+    int64_t Tp, uint16_t* __restrict__ Uh, uint16_t* __restrict__ Ul, int mode) {
+  constexpr int A = MM + 2, F = A * A;
+  extern __shared__ __align__(16) uint16_t qs[];  // [2][F][kQT][kQC]
+  const int tl = threadIdx.x % kQT, cl = threadIdx.x / kQT;
+  const int64_t t = (int64_t)blockIdx.x * kQT + tl;
+  const int c = blockIdx.y * kQC + cl;
+  const bool live = t < g.T && c < g.C;
+  float d[A][A];
+  if (live) {
+    const int tpi = g.th * g.tw;
+    const int n = (int)(t / tpi);
+    const int rem = (int)(t - (int64_t)n * tpi);
+    const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
+    const int h0 = ti * MM - g.pad, w0 = tj * MM - g.pad;
+    const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
+#pragma unroll
+    for (int i = 0; i < A; ++i)
+#pragma unroll
+      for (int j = 0; j < A; ++j) {
+        const int hh = h0 + i, ww = w0 + j;
+        d[i][j] = ((unsigned)hh < (unsigned)g.H && (unsigned)ww < (unsigned)g.W)
+                      ? __ldg(xc + (int64_t)hh * g.W + ww)
+                      : 0.0f;
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < A; ++i)
+#pragma unroll
+      for (int j = 0; j < A; ++j) d[i][j] = 0.0f;
+  }
+  float tm[A][A];
+#pragma unroll
+  for (int i = 0; i < A; ++i)
+#pragma unroll
+    for (int l = 0; l < A; ++l) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < A; ++q) acc = fmaf(Mx.BT[i * A + q], d[q][l], acc);
+      tm[i][l] = acc;
+    }
+  uint16_t* sh = qs;
+  uint16_t* sl = qs + F * kQT * kQC;
+#pragma unroll
+  for (int i = 0; i < A; ++i)
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int l = 0; l < A; ++l) acc = fmaf(tm[i][l], Mx.BT[j * A + l], acc);
+      const int f = i * A + j;
+      const float v = live ? acc * S.sU[f] : 0.0f;
+      const uint16_t h = round16(v, mode);
+      sh[(f * kQT + tl) * kQC + cl] = h;
+      if (mode == 3) sl[(f * kQT + tl) * kQC + cl] = round16(v - widen16(h, mode), mode);
+    }
+  __syncthreads();
+  // rows (f, tile) of 16 channels = 32 bytes = two 16-byte stores
+  const int64_t plane = Tp * Cp;
+  const int64_t tb = (int64_t)blockIdx.x * kQT;
+  const int c0 = blockIdx.y * kQC;
+  for (int e = threadIdx.x; e < F * kQT * 2; e += kQT * kQC) {
+    const int half = e & 1, row = e >> 1;  // row = f * kQT + tl
+    const int f = row / kQT, tr = row % kQT;
+    const int64_t dst = f * plane + (tb + tr) * Cp + c0 + half * 8;
+    *reinterpret_cast<uint4*>(Uh + dst) = *reinterpret_cast<const uint4*>(sh + row * kQC + half * 8);
+    if (mode == 3)
+      *reinterpret_cast<uint4*>(Ul + dst) =
+          *reinterpret_cast<const uint4*>(sl + row * kQC + half * 8);
+  }
+}
+
+// Output transform A^T M A with compile-time sizes, M [F][K][T]: one thread
+// per (k, tile), tiles fastest (coalesced M reads, adjacent output segments).
+template <int MM>
+__global__ void __launch_bounds__(256) k_output_transform_r3(const float* __restrict__ Mi,
+                                                             float* __restrict__ y,
+                                                             const LayerGeom g,
+                                                             const LayerMats Mx) {
+  constexpr int A = MM + 2;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)g.K * g.T) return;
+  const int64_t t = idx % g.T;
+  const int k = (int)(idx / g.T);
+  const int64_t plane = (int64_t)g.K * g.T;
+  const float* in = Mi + (int64_t)k * g.T + t;
+  float Mv[A * A];
+#pragma unroll
+  for (int f = 0; f < A * A; ++f) Mv[f] = in[f * plane];
+  float Z[MM][A];
+#pragma unroll
+  for (int a = 0; a < MM; ++a)
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int i = 0; i < A; ++i) acc = fmaf(Mx.AT[a * A + i], Mv[i * A + j], acc);
+      Z[a][j] = acc;
+    }
+  const int tpi = g.th * g.tw;
+  const int n = (int)(t / tpi);
+  const int rem = (int)(t - (int64_t)n * tpi);
+  const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
+  float* yk = y + ((int64_t)n * g.K + k) * g.Ho * g.Wo;
+#pragma unroll
+  for (int a = 0; a < MM; ++a) {
+    const int p = ti * MM + a;
+#pragma unroll
+    for (int b = 0; b < MM; ++b) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < A; ++j) acc = fmaf(Z[a][j], Mx.AT[b * A + j], acc);
+      const int q = tj * MM + b;
+      if (p < g.Ho && q < g.Wo) yk[(int64_t)p * g.Wo + q] = acc;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // tcgen05 contraction.
 // ---------------------------------------------------------------------------
@@ -467,14 +592,26 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     const int64_t nq = (int64_t)g.F * g.K * Cp;
     k_quant_v<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(V32, g.C, g.K, Cp, g.F, vmax, sV, Vh,
                                                             Vl, mode);
-    const int64_t nu = Tp * Cp;
-    const unsigned gu = (unsigned)((nu + 255) / 256);
+    const dim3 gq((unsigned)(Tp / kQT), (unsigned)(Cp / kQC));
+    const size_t qsm = (size_t)2 * g.F * kQT * kQC * sizeof(uint16_t);
+    static bool qattr[16] = {false};
+    int qdev = 0;
+    WINO_CUDA_TRY(cudaGetDevice(&qdev));
+    if (qdev < 16 && !qattr[qdev]) {
+      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<6>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+      qattr[qdev] = true;
+    }
     if (M.m == 2)
-      k_quant_input<2><<<gu, 256, 0, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
+      k_quant_input_tiled<2><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
     else if (M.m == 4)
-      k_quant_input<4><<<gu, 256, 0, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
+      k_quant_input_tiled<4><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
     else
-      k_quant_input<6><<<gu, 256, 0, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
+      k_quant_input_tiled<6><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
     note_launches(4);
   }
   TcGemmArgs P;
@@ -511,7 +648,13 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
   {
     ProfScope ps(kKOutput, st);
     const int64_t n = (int64_t)g.K * g.T;
-    k_output_transform<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Mb, y, g, M);
+    const unsigned go = (unsigned)((n + 255) / 256);
+    if (M.m == 2)
+      k_output_transform_r3<2><<<go, 256, 0, st>>>(Mb, y, g, M);
+    else if (M.m == 4)
+      k_output_transform_r3<4><<<go, 256, 0, st>>>(Mb, y, g, M);
+    else
+      k_output_transform_r3<6><<<go, 256, 0, st>>>(Mb, y, g, M);
     note_launches(1);
   }
   WINO_CUDA_TRY(cudaGetLastError());

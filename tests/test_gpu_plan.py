@@ -73,3 +73,28 @@ def test_plan_deadline_reports_timeout(wino):
         assert np.all(np.isfinite(full))
     finally:
         plan.close()
+
+
+def test_chunk_split_is_bit_identical(wino):
+    """A plan large enough to fill the GPU runs every trial of an instance in
+    one lane; a small plan spreads each instance's 128-trial chunks over
+    several warps and adds their partial sums afterwards.  Both use the same
+    fixed summation order, so the same instance gives the same bits (300
+    trials: two full chunks and a ragged one)."""
+    sizes = [(1, 2, 3, 1.0)]
+    masks = np.array(wino.valid_masks(sizes[0], inputs.sweep_masks()), dtype=np.uint8)
+    rng = np.random.default_rng(21)
+    n = 32 * 152 * 8 * 4 + 77  # more groups of 32 than four rounds of resident warps
+    inst = wino.instance_array(np.zeros(n, np.int32), masks[rng.integers(masks.size, size=n)],
+                               np.exp(rng.uniform(np.log(0.05), np.log(20), n)))
+    big = wino.SweepPlan(sizes, inst, 300, seed=4, mode=1)
+    sub = inst[rng.choice(n, 500, replace=False)]
+    small = wino.SweepPlan(sizes, sub, 300, seed=4, mode=1)
+    try:
+        want = big.run()
+        got = small.run()
+    finally:
+        big.close()
+        small.close()
+    key = {(int(q["mask"]), float(q["c"])): e for q, e in zip(inst, want)}
+    assert np.array_equal(got, np.array([key[(int(q["mask"]), float(q["c"]))] for q in sub]))
