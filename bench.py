@@ -492,12 +492,18 @@ def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
         w = [4.0 * (N * C * H * H + (m + 2) ** 2 * C * _tiles(m, H, N))
              for m in (4, 6) for C, H in layers]
         work, base = sum(w) / len(w), hbm
-    elif kernel == "tc_gemm":  # BF16 and split-BF16x3 F(4x4) stacks
-        w = [2.0 * 36 * ((_tiles(4, H, N) + 127) // 128 * 128) * C * C * f
-             for f in (1, 3) for C, H in layers]
-        work = sum(w) / len(w)
-        base = {"bound": "tensor", "unit": "TFLOP/s", "peak": peaks["bf16_tflops"],
-                "peak_source": "%s cuBLAS bf16 dense, burst (of %s)" % (peak_src, peak_src)}
+    elif kernel == "tc_gemm":
+        # BF16 and split-BF16x3 F(4x4) stacks.  Per frequency 2 T C K flops on
+        # 2 T C + 2 C K + 4 T K bytes: at most 171 flop/byte (C = K = 512),
+        # below the ridge of the measured peaks (~288), so every VGG stage is
+        # HBM-bound: the roofline counts U and V read (16-bit; hi and lo for
+        # the split form) and M written (FP32).
+        w = []
+        for f in (1, 2):
+            for C, H in layers:
+                Tp = (_tiles(4, H, N) + 127) // 128 * 128
+                w.append(36 * (2.0 * f * (Tp * C + C * C) + 4.0 * _tiles(4, H, N) * C))
+        work, base = sum(w) / len(w), hbm
     elif kernel == "sweep_eval":  # per-size sweep kernels + the persistent launch
         work = 2 * sweep_flops_total() / per_step
         base = fp32
@@ -506,9 +512,36 @@ def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
     scale = 1e9 if base["unit"] == "GB/s" else 1e12
     ach = work / sec / scale
     return dict(kernel=kernel, bound=base["bound"], achieved=ach, peak=base["peak"],
-                unit=base["unit"], frac=ach / base["peak"], traffic=None,
+                unit=base["unit"], frac=ach / base["peak"], traffic=kernel_traffic(kernel, layers, N),
                 peak_source=base["peak_source"], work_per_launch=work, launches_per_step=per_step,
                 mean_launch_ms=ms / n)
+
+
+# DRAM bytes (read + write) of one ncu capture of each kernel on a smaller
+# case (profiles/), and the same case's algorithmic bytes; traffic of a bench
+# launch = that ratio x the launch's algorithmic bytes (traffic grows in
+# proportion to the bytes the launch must move).
+NCU_TRAFFIC = {
+    # k_gemm_otx F(4x4), C = K = 64, 224x224, N = 8: U read + y written
+    "fused_layer": (307.66e6, 36 * 25088 * 64 * 4 + 8 * 64 * 224 * 224 * 4),
+    # k_tc_gemm BF16, same layer: U + V read (16-bit), M written (FP32)
+    "tc_gemm": (289.35e6, 36 * (2 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
+}
+
+
+def kernel_traffic(kernel, layers, N):
+    """Mean DRAM bytes per launch, scaled from the kernel's ncu capture, or
+    None when no capture covers it."""
+    if kernel not in NCU_TRAFFIC:
+        return None
+    meas, alg = NCU_TRAFFIC[kernel]
+    if kernel == "fused_layer":
+        b = [4.0 * ((m + 2) ** 2 * _tiles(m, H, N) * C + N * C * H * H)
+             for m in (4, 6) for C, H in layers]
+    else:
+        b = [36 * (2.0 * f * ((_tiles(4, H, N) + 127) // 128 * 128 * C + C * C) +
+                   4.0 * _tiles(4, H, N) * C) for f in (1, 2) for C, H in layers]
+    return meas / alg * sum(b) / len(b)
 
 
 def sweep_flops_total():
@@ -541,13 +574,17 @@ def profile_case(name):
     from paper_2201_10369_gb300 import inputs
     wino.build()
     wino.load()
-    if name in ("f4x4", "f6x6", "f4x4_bf16", "f4x4_split"):
-        x, w = inputs.vgg_layer_device(64, 224, N=8, seed=0)
-        y = torch.empty_like(x)
-        m, pts = (4, PTS4) if name.startswith("f4x4") else (6, PTS6)
-        dt = {"f4x4_bf16": "bf16", "f4x4_split": "split_bf16x3"}.get(name, "f32")
+    base = name[:-4] if name.endswith("_vgg") else name
+    if base in ("f4x4", "f6x6", "f4x4_bf16", "f4x4_split"):
+        # one layer (64 ch, 224x224), or with _vgg the five VGG16 stages, N=8
+        shapes = inputs.VGG16_LAYERS if name.endswith("_vgg") else [(64, 224)]
+        xs = [inputs.vgg_layer_device(C, H, N=8, seed=i) for i, (C, H) in enumerate(shapes)]
+        ys = [torch.empty_like(x) for x, _ in xs]
+        m, pts = (4, PTS4) if base.startswith("f4x4") else (6, PTS6)
+        dt = {"f4x4_bf16": "bf16", "f4x4_split": "split_bf16x3"}.get(base, "f32")
         for _ in range(4):
-            wino.wino_conv2d(x, w, y, pts, m, 3, 1, dt)
+            for (x, w), y in zip(xs, ys):
+                wino.wino_conv2d(x, w, y, pts, m, 3, 1, dt)
     elif name == "sweep":
         cg = inputs.c_grid()
         for _ in range(4):
@@ -567,7 +604,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     help="run one small workload a few times for an ncu capture: "
-                         "f4x4 | f6x6 (VGG 64ch 224x224, N=8) | sweep (2D F(4x4), 15 masks)")
+                         "f4x4 | f6x6 | f4x4_bf16 | f4x4_split (VGG 64ch 224x224, N=8; "
+                         "suffix _vgg: the five VGG16 stages, N=8) | sweep (2D F(4x4), "
+                         "all masks, 4096 c)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -29,6 +29,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "../../include/wino.h"
 #include "common.cuh"
 
@@ -72,12 +74,27 @@ struct TcScales {
 // ---------------------------------------------------------------------------
 // Operand preparation.
 // ---------------------------------------------------------------------------
-__global__ void k_vmax(const float* __restrict__ V, int64_t plane, int F,
-                       unsigned* __restrict__ vmax_bits) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= plane * F) return;
-  const int f = (int)(idx / plane);
-  atomicMax(vmax_bits + f, __float_as_uint(fabsf(V[idx])));
+// max |V| of each frequency plane: block (x, f) reduces a grid-stride slice
+// of plane f (warp shuffles, then shared memory) and issues ONE atomicMax on
+// the bit pattern (non-negative floats order like their bits), so a plane of
+// C K values costs gridDim.x atomics, not C K.
+constexpr int kVmaxThreads = 256;
+__global__ void __launch_bounds__(kVmaxThreads) k_vmax(const float* __restrict__ V, int64_t plane,
+                                                       unsigned* __restrict__ vmax_bits) {
+  const int f = blockIdx.y;
+  const float* p = V + (int64_t)f * plane;
+  float mx = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * kVmaxThreads + threadIdx.x; i < plane;
+       i += (int64_t)gridDim.x * kVmaxThreads)
+    mx = fmaxf(mx, fabsf(p[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ float wm[kVmaxThreads / 32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kVmaxThreads / 32; ++w) mx = fmaxf(mx, wm[w]);
+    atomicMax(vmax_bits + f, __float_as_uint(mx));
+  }
 }
 
 // V32[f][c][k] -> Vh/Vl[f][k][c] (c padded to Cp with zeros), scaled.
@@ -587,8 +604,10 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     ProfScope ps(kKTcTransform, st);
     const int64_t n = (int64_t)g.C * g.K;
     k_filter_transform<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, V32, g.dim, g.C, g.K, M);
-    const int64_t nv = (int64_t)g.F * g.C * g.K;
-    k_vmax<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(V32, (int64_t)g.C * g.K, g.F, vmax);
+    const int64_t plane = (int64_t)g.C * g.K;
+    const unsigned bx = (unsigned)std::min<int64_t>(256, (plane + 8 * kVmaxThreads - 1) /
+                                                            (8 * kVmaxThreads));
+    k_vmax<<<dim3(bx, (unsigned)g.F), kVmaxThreads, 0, st>>>(V32, plane, vmax);
     const int64_t nq = (int64_t)g.F * g.K * Cp;
     k_quant_v<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(V32, g.C, g.K, Cp, g.F, vmax, sV, Vh,
                                                             Vl, mode);
