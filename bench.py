@@ -42,7 +42,11 @@ PTS6 = [0.0, -1 / C6, -C6, C6, 1 / C6, -D6, D6, math.inf]
 METRIC = "Winograd layer effective TFLOP/s at stated FP64 error; c-sweep evals/s vs plain"
 # the layer stacks of one step: key -> (m, points, contraction dtype)
 STACKS = {"f4x4": (4, PTS4, "f32"), "f6x6": (6, PTS6, "f32"),
-          "f4x4_bf16": (4, PTS4, "bf16"), "f4x4_split_bf16x3": (4, PTS4, "split_bf16x3")}
+          "f4x4_bf16": (4, PTS4, "bf16"), "f4x4_split_bf16x3": (4, PTS4, "split_bf16x3"),
+          "f4x4_split_bf16x6": (4, PTS4, "split_bf16x6"),
+          "f6x6_split_bf16x6": (6, PTS6, "split_bf16x6")}
+# 16-bit operand parts of each tensor-core dtype
+TC_PARTS = {"bf16": 1, "fp16": 1, "split_bf16x3": 2, "split_bf16x6": 3}
 # surrogate training: sweep labels of random instances of the sweep's sizes
 # plus 1D F(m,5), m = 2..6 (d chosen so every size has valid subsets)
 R5_SIZES = [(1, 2, 5, 1.0), (1, 3, 5, 1.0), (1, 4, 5, 1.0), (1, 5, 5, 2.478), (1, 6, 5, 1.229)]
@@ -414,7 +418,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {
             "workload": "VGG16 3x3 layer stack (C=64..512, H=224..14), N=32/GPU, FP32 Winograd "
                         "F(4x4,3x3) [value]; per step also the F(6x6,3x3) FP32 stack, the "
-                        "BF16 and split-BF16x3 tensor-core F(4x4) stacks, the full point sweep "
+                        "BF16, split-BF16x3 and split-BF16x6 tensor-core F(4x4) stacks, the "
+                        "split-BF16x6 F(6x6) stack, the full point sweep "
                         "(503808 instances x 1000 trials) per-size and as one persistent graph "
                         "launch, and the surrogate-guided search of the same grid",
             "points_f4x4": "{0,+-c,+-1/c,inf} c=1.622",
@@ -498,12 +503,7 @@ def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
         # below the ridge of the measured peaks (~288), so every VGG stage is
         # HBM-bound: the roofline counts U and V read (16-bit; hi and lo for
         # the split form) and M written (FP32).
-        w = []
-        for f in (1, 2):
-            for C, H in layers:
-                Tp = (_tiles(4, H, N) + 127) // 128 * 128
-                w.append(36 * (2.0 * f * (Tp * C + C * C) + 4.0 * _tiles(4, H, N) * C))
-        work, base = sum(w) / len(w), hbm
+        work, base = tc_bytes_per_launch(layers, N), hbm
     elif kernel == "sweep_eval":  # per-size sweep kernels + the persistent launch
         work = 2 * sweep_flops_total() / per_step
         base = fp32
@@ -538,10 +538,24 @@ def kernel_traffic(kernel, layers, N):
     if kernel == "fused_layer":
         b = [4.0 * ((m + 2) ** 2 * _tiles(m, H, N) * C + N * C * H * H)
              for m in (4, 6) for C, H in layers]
-    else:
-        b = [36 * (2.0 * f * ((_tiles(4, H, N) + 127) // 128 * 128 * C + C * C) +
-                   4.0 * _tiles(4, H, N) * C) for f in (1, 2) for C, H in layers]
-    return meas / alg * sum(b) / len(b)
+        return meas / alg * sum(b) / len(b)
+    return meas / alg * tc_bytes_per_launch(layers, N)
+
+
+def tc_bytes_per_launch(layers, N):
+    """Mean algorithmic bytes of one tcgen05 GEMM launch over the step's
+    tensor-core stacks: every 16-bit part of U [F][Tp][C] and V [F][K][C]
+    read once, M [F][K][T] written once in FP32."""
+    b = []
+    for m, _, dt in STACKS.values():
+        if dt not in TC_PARTS:
+            continue
+        F = (m + 2) ** 2
+        for C, H in layers:
+            T = _tiles(m, H, N)
+            Tp = (T + 127) // 128 * 128
+            b.append(F * (2.0 * TC_PARTS[dt] * (Tp * C + C * C) + 4.0 * T * C))
+    return sum(b) / len(b)
 
 
 def sweep_flops_total():

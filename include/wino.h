@@ -52,7 +52,11 @@ typedef enum {
   WINO_F32 = 0,            /* FP32 SIMT fused multiply-add                  */
   WINO_BF16_TC = 1,        /* BF16 operands on tcgen05, FP32 accumulate     */
   WINO_FP16_TC = 2,        /* FP16 operands on tcgen05, FP32 accumulate     */
-  WINO_SPLIT_BF16X3 = 3    /* hi/lo BF16 split, 3 tcgen05 products, FP32 acc */
+  WINO_SPLIT_BF16X3 = 3,   /* hi/lo BF16 split, 3 tcgen05 products, FP32 acc */
+  WINO_SPLIT_BF16X6 = 4    /* hi/mid/lo BF16 split (all 24 bits of an FP32
+                              operand), the 6 tcgen05 products down to 2^-16
+                              relative: hh into one FP32 accumulator, hm, mh,
+                              hl, lh, mm into a second, added at the end    */
 } wino_dtype;
 
 /* Largest alpha = m + r - 1 the library accepts. */

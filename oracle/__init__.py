@@ -162,7 +162,7 @@ def tile_direct_f32(dim: int, m: int, r: int, g, d):
     return y if dim == 1 else y.reshape(m, m)
 
 
-LOWP = {"f32": 0, "bf16": 1, "fp16": 2, "split_bf16x3": 3}
+LOWP = {"f32": 0, "bf16": 1, "fp16": 2, "split_bf16x3": 3, "split_bf16x6": 4}
 
 
 def wino_layer(x, w, dim: int, pad: int, points, m: int, r: int, lowp: str = "f32"):

@@ -443,7 +443,7 @@ int orc_wino_layer(const float* x, const float* w, float* y, int dim,
     const int ti = (int)((t / tw) % th), tj = (int)(t % tw);
     for (int k = 0; k < K; ++k) {
       for (int f = 0; f < F; ++f) {
-        float acc = 0.0f;
+        float acc = 0.0f, acc_lo = 0.0f;  /* acc_lo: split x6's small products */
         for (int c = 0; c < C; ++c) {
           float u = U[((size_t)f * T + t) * C + c];
           float v = V[((size_t)f * C + c) * K + k];
@@ -452,15 +452,32 @@ int orc_wino_layer(const float* x, const float* w, float* y, int dim,
           } else if (lowp == 1 || lowp == 2) {
             float uq = round_mode(u * sU[f], lowp), vq = round_mode(v * sV[f], lowp);
             acc = fmaf(uq, vq, acc);
-          } else {
+          } else if (lowp == 3) {
             float us = u * sU[f], vs = v * sV[f];
             float uh = orc_round_bf16(us), vh = orc_round_bf16(vs);
             float ul = orc_round_bf16(us - uh), vl = orc_round_bf16(vs - vh);
             acc = fmaf(uh, vh, acc);
             acc = fmaf(uh, vl, acc);
             acc = fmaf(ul, vh, acc);
+          } else {
+            /* three-part split: hi, mid = RN(a - hi), lo = RN((a - hi) - mid);
+               the differences are exact in FP32 */
+            float us = u * sU[f], vs = v * sV[f];
+            float uh = orc_round_bf16(us), vh = orc_round_bf16(vs);
+            float ur = us - uh, vr = vs - vh;
+            float um = orc_round_bf16(ur), vm = orc_round_bf16(vr);
+            float ul = orc_round_bf16(ur - um), vl = orc_round_bf16(vr - vm);
+            /* hh in one accumulator, the five smaller products (below
+               2^-7 of hh) in a second one, added at the end */
+            acc = fmaf(uh, vh, acc);
+            acc_lo = fmaf(uh, vm, acc_lo);
+            acc_lo = fmaf(um, vh, acc_lo);
+            acc_lo = fmaf(uh, vl, acc_lo);
+            acc_lo = fmaf(ul, vh, acc_lo);
+            acc_lo = fmaf(um, vm, acc_lo);
           }
         }
+        if (lowp == 4) acc = acc + acc_lo;
         if (lowp != 0) acc = acc / (sU[f] * sV[f]); /* exact: powers of two */
         Mf[f] = acc;
       }

@@ -54,7 +54,9 @@ void orc_tile_direct_f32(int dim, int m, int r, const float* g,
 /* FP32 Winograd layer (Eq. (9) per m x m tile, alpha^2 Hadamard products
  * summed over C in ascending c with fmaf).  dim = 1 uses H = 1 and w[K][C][r].
  * `lowp` selects the contraction operands: 0 FP32, 1 BF16, 2 FP16 (with the
- * per-frequency power-of-two scales of the precision form), 3 split BF16x3.
+ * per-frequency power-of-two scales of the precision form), 3 split BF16x3,
+ * 4 split BF16x6 (hi, mid, lo; hh summed in one accumulator, hm, mh, hl, lh,
+ * mm in a second, the two added at the end).
  * Returns 0, or -1 / -2 like orc_make_matrices.
  * Pinned by: FP64 direct within the FP32 Winograd error scale; equals the
  * tile function bit for bit when C = K = 1.                                */

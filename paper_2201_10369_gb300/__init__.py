@@ -19,9 +19,9 @@ from . import _build
 
 WINO_OK, WINO_EINVAL, WINO_ESINGULAR, WINO_ENOMEM = 0, -1, -2, -3
 WINO_ECUDA, WINO_ETIMEOUT, WINO_EUNSUPPORTED = -4, -5, -6
-WINO_F32, WINO_BF16_TC, WINO_FP16_TC, WINO_SPLIT_BF16X3 = 0, 1, 2, 3
+WINO_F32, WINO_BF16_TC, WINO_FP16_TC, WINO_SPLIT_BF16X3, WINO_SPLIT_BF16X6 = 0, 1, 2, 3, 4
 DTYPES = {"f32": WINO_F32, "bf16": WINO_BF16_TC, "fp16": WINO_FP16_TC,
-          "split_bf16x3": WINO_SPLIT_BF16X3}
+          "split_bf16x3": WINO_SPLIT_BF16X3, "split_bf16x6": WINO_SPLIT_BF16X6}
 _STATUS = {0: "WINO_OK", -1: "WINO_EINVAL", -2: "WINO_ESINGULAR", -3: "WINO_ENOMEM",
            -4: "WINO_ECUDA", -5: "WINO_ETIMEOUT", -6: "WINO_EUNSUPPORTED"}
 

@@ -209,7 +209,7 @@ int wino_make_matrices(const double* points, int m, int r, double* AT, double* G
 static int conv_common(int dim, const void* x, const void* w, void* y, int N, int C, int K,
                        int H, int W, int pad, const double* points, int m, int r, int dtype,
                        void* stream) {
-  if (dtype < WINO_F32 || dtype > WINO_SPLIT_BF16X3) {
+  if (dtype < WINO_F32 || dtype > WINO_SPLIT_BF16X6) {
     set_error("unknown dtype");
     return WINO_EINVAL;
   }

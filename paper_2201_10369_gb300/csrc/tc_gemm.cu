@@ -8,6 +8,16 @@
 //   WINO_SPLIT_BF16X3  a = hi + lo with hi = RN_bf16(a), lo = RN_bf16(a - hi);
 //                      U V ~ Uhi Vhi + Uhi Vlo + Ulo Vhi (three MMAs into one
 //                      accumulator)
+//   WINO_SPLIT_BF16X6  a = hi + mid + lo with mid = RN_bf16(a - hi),
+//                      lo = RN_bf16(a - hi - mid) (the differences are exact in
+//                      FP32, so the three parts hold every bit of the FP32
+//                      operand); U V ~ hh + hm + mh + hl + lh + mm (six MMAs;
+//                      the dropped terms are below 2^-23 of hh).  hh goes to
+//                      one TMEM accumulator and the five small products to a
+//                      second (their rounding is 2^-7 smaller), added in the
+//                      epilogue: the error falls below the FP32 SIMT layer's
+// The operand parts are stored in order (hi, then lo or mid, then lo), one
+// [F][rows][Cp] 16-bit array each.
 // Per-frequency scaling (exact powers of two, undone before the output
 // transform): U[f] by the power of two that brings |BT_i|_1 |BT_j|_1 into
 // [1, 2), V[f] by the one that brings max |V[f]| into [1, 2).  This keeps FP16
@@ -47,7 +57,7 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// 16-bit rounding of a scaled FP32 value; mode 1/3 BF16, 2 FP16.
+// 16-bit rounding of a scaled FP32 value; mode 2 FP16, every other mode BF16.
 __device__ __forceinline__ uint16_t round16(float v, int mode) {
   if (mode == 2) return __half_as_ushort(__float2half_rn(v));
   return __bfloat16_as_ushort(__float2bfloat16_rn(v));
@@ -63,6 +73,23 @@ __device__ __forceinline__ float pow2_normaliser(float m) {
   int e;
   frexpf(m, &e);
   return ldexpf(1.0f, 1 - e);
+}
+
+// Number of 16-bit parts an operand is split into.
+__host__ __device__ __forceinline__ int tc_parts(int mode) {
+  return mode == 3 ? 2 : (mode == 4 ? 3 : 1);
+}
+
+// The parts of a (scaled) FP32 value, hi first.
+__device__ __forceinline__ void split_parts(float v, int mode, uint16_t out[3]) {
+  out[0] = round16(v, mode);
+  if (mode == 3) {
+    out[1] = round16(v - widen16(out[0], mode), mode);
+  } else if (mode == 4) {
+    const float r1 = v - widen16(out[0], mode);  // exact
+    out[1] = round16(r1, mode);
+    out[2] = round16(r1 - widen16(out[1], mode), mode);  // exact difference
+  }
 }
 
 }  // namespace
@@ -97,10 +124,11 @@ __global__ void __launch_bounds__(kVmaxThreads) k_vmax(const float* __restrict__
   }
 }
 
-// V32[f][c][k] -> Vh/Vl[f][k][c] (c padded to Cp with zeros), scaled.
+// V32[f][c][k] -> parts V0/V1/V2 [f][k][c] (c padded to Cp with zeros), scaled.
 __global__ void k_quant_v(const float* __restrict__ V, int C, int K, int Cp, int F,
                           const unsigned* __restrict__ vmax_bits, float* __restrict__ sV,
-                          uint16_t* __restrict__ Vh, uint16_t* __restrict__ Vl, int mode) {
+                          uint16_t* __restrict__ V0, uint16_t* __restrict__ V1,
+                          uint16_t* __restrict__ V2, int mode) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)F * K * Cp;
   if (idx >= total) return;
@@ -111,85 +139,29 @@ __global__ void k_quant_v(const float* __restrict__ V, int C, int K, int Cp, int
   if (c == 0 && k == 0) sV[f] = s;
   float v = 0.0f;
   if (c < C) v = V[((int64_t)f * C + c) * K + k] * s;
-  const uint16_t h = round16(v, mode);
-  Vh[idx] = h;
-  if (mode == 3) Vl[idx] = round16(v - widen16(h, mode), mode);
+  uint16_t q[3];
+  split_parts(v, mode, q);
+  V0[idx] = q[0];
+  if (mode == 3 || mode == 4) V1[idx] = q[1];
+  if (mode == 4) V2[idx] = q[2];
 }
 
-// Input transform (FP32, the FP32 layer's order) -> Uh/Ul[f][t][c], scaled.
-// One thread per (t, c), c fastest: each frequency row is written
-// contiguously; rows t >= T and columns c >= C are zero.
-template <int MM>
-__global__ void __launch_bounds__(256) k_quant_input(const float* __restrict__ x, const LayerGeom g,
-                                                     const LayerMats Mx, const TcScales S, int Cp,
-                                                     int64_t Tp, uint16_t* __restrict__ Uh,
-                                                     uint16_t* __restrict__ Ul, int mode) {
-  constexpr int A = MM + 2;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Tp * Cp) return;
-  const int c = (int)(idx % Cp);
-  const int64_t t = idx / Cp;
-  float d[A][A];
-  const bool live = t < g.T && c < g.C;
-  if (live) {
-    const int tpi = g.th * g.tw;
-    const int n = (int)(t / tpi);
-    const int rem = (int)(t - (int64_t)n * tpi);
-    const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
-    const int h0 = ti * MM - g.pad, w0 = tj * MM - g.pad;
-    const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
-#pragma unroll
-    for (int i = 0; i < A; ++i)
-#pragma unroll
-      for (int j = 0; j < A; ++j) {
-        const int hh = h0 + i, ww = w0 + j;
-        d[i][j] = ((unsigned)hh < (unsigned)g.H && (unsigned)ww < (unsigned)g.W)
-                      ? __ldg(xc + (int64_t)hh * g.W + ww)
-                      : 0.0f;
-      }
-  } else {
-#pragma unroll
-    for (int i = 0; i < A; ++i)
-#pragma unroll
-      for (int j = 0; j < A; ++j) d[i][j] = 0.0f;
-  }
-  float tm[A][A];
-#pragma unroll
-  for (int i = 0; i < A; ++i)
-#pragma unroll
-    for (int l = 0; l < A; ++l) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int q = 0; q < A; ++q) acc = fmaf(Mx.BT[i * A + q], d[q][l], acc);
-      tm[i][l] = acc;
-    }
-  const int64_t plane = Tp * Cp;
-#pragma unroll
-  for (int i = 0; i < A; ++i)
-#pragma unroll
-    for (int j = 0; j < A; ++j) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int l = 0; l < A; ++l) acc = fmaf(tm[i][l], Mx.BT[j * A + l], acc);
-      const int f = i * A + j;
-      const float v = live ? acc * S.sU[f] : 0.0f;
-      const uint16_t h = round16(v, mode);
-      Uh[f * plane + idx] = h;
-      if (mode == 3) Ul[f * plane + idx] = round16(v - widen16(h, mode), mode);
-    }
-}
-
-// Tiled form of the same input quantisation: one block = 16 tiles x 16
-// channels; a thread transforms one (tile, channel) with tiles fastest
-// (neighbouring patches share input rows), the 16-bit results meet in
-// shared memory and leave as 32-byte rows of 16 channels.
+// Input transform (FP32, the FP32 layer's order) -> operand parts
+// U0/U1/U2 [f][t][c], scaled; rows t >= T and columns c >= C are zero.
+// One block = 16 tiles x 16 channels; a thread transforms one (tile,
+// channel) with tiles fastest (neighbouring patches share input rows), the
+// 16-bit results meet in shared memory and leave as 32-byte rows of 16
+// channels.
 constexpr int kQT = 16, kQC = 16;
+// largest staging: three parts of F = 64 frequencies (m = 6)
+constexpr int kQuantSmemMax = 3 * 64 * kQT * kQC * 2;
 template <int MM>
 __global__ void __launch_bounds__(kQT* kQC) k_quant_input_tiled(
     const float* __restrict__ x, const LayerGeom g, const LayerMats Mx, const TcScales S, int Cp,
-    int64_t Tp, uint16_t* __restrict__ Uh, uint16_t* __restrict__ Ul, int mode) {
+    int64_t Tp, uint16_t* __restrict__ U0, uint16_t* __restrict__ U1, uint16_t* __restrict__ U2,
+    int mode) {
   constexpr int A = MM + 2, F = A * A;
-  extern __shared__ __align__(16) uint16_t qs[];  // [2][F][kQT][kQC]
+  extern __shared__ __align__(16) uint16_t qs[];  // [parts][F][kQT][kQC]
   const int tl = threadIdx.x % kQT, cl = threadIdx.x / kQT;
   const int64_t t = (int64_t)blockIdx.x * kQT + tl;
   const int c = blockIdx.y * kQC + cl;
@@ -227,8 +199,8 @@ __global__ void __launch_bounds__(kQT* kQC) k_quant_input_tiled(
       for (int q = 0; q < A; ++q) acc = fmaf(Mx.BT[i * A + q], d[q][l], acc);
       tm[i][l] = acc;
     }
-  uint16_t* sh = qs;
-  uint16_t* sl = qs + F * kQT * kQC;
+  const int parts = tc_parts(mode);
+  constexpr int kPart = F * kQT * kQC;  // one part's staging, in 16-bit values
 #pragma unroll
   for (int i = 0; i < A; ++i)
 #pragma unroll
@@ -238,23 +210,26 @@ __global__ void __launch_bounds__(kQT* kQC) k_quant_input_tiled(
       for (int l = 0; l < A; ++l) acc = fmaf(tm[i][l], Mx.BT[j * A + l], acc);
       const int f = i * A + j;
       const float v = live ? acc * S.sU[f] : 0.0f;
-      const uint16_t h = round16(v, mode);
-      sh[(f * kQT + tl) * kQC + cl] = h;
-      if (mode == 3) sl[(f * kQT + tl) * kQC + cl] = round16(v - widen16(h, mode), mode);
+      uint16_t q[3];
+      split_parts(v, mode, q);
+      const int o = (f * kQT + tl) * kQC + cl;
+      qs[o] = q[0];
+      if (parts > 1) qs[kPart + o] = q[1];
+      if (parts > 2) qs[2 * kPart + o] = q[2];
     }
   __syncthreads();
-  // rows (f, tile) of 16 channels = 32 bytes = two 16-byte stores
+  // rows (f, tile) of 16 channels = 32 bytes = two 16-byte stores per part
   const int64_t plane = Tp * Cp;
   const int64_t tb = (int64_t)blockIdx.x * kQT;
   const int c0 = blockIdx.y * kQC;
+  uint16_t* const dsts[3] = {U0, U1, U2};
   for (int e = threadIdx.x; e < F * kQT * 2; e += kQT * kQC) {
     const int half = e & 1, row = e >> 1;  // row = f * kQT + tl
     const int f = row / kQT, tr = row % kQT;
     const int64_t dst = f * plane + (tb + tr) * Cp + c0 + half * 8;
-    *reinterpret_cast<uint4*>(Uh + dst) = *reinterpret_cast<const uint4*>(sh + row * kQC + half * 8);
-    if (mode == 3)
-      *reinterpret_cast<uint4*>(Ul + dst) =
-          *reinterpret_cast<const uint4*>(sl + row * kQC + half * 8);
+    for (int pp = 0; pp < parts; ++pp)
+      *reinterpret_cast<uint4*>(dsts[pp] + dst) =
+          *reinterpret_cast<const uint4*>(qs + pp * kPart + row * kQC + half * 8);
   }
 }
 
@@ -355,6 +330,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// 32 lanes x 16 consecutive FP32 columns of TMEM, one row per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
 }
@@ -366,7 +353,8 @@ constexpr int kTcKc = 64;    // channels per chunk: one 128-byte row per operand
 constexpr int kTcThreads = 128;
 
 struct TcGemmArgs {
-  const uint16_t *Uh, *Ul, *Vh, *Vl;
+  const uint16_t* U[3];  // operand parts (hi first), [F][Tp][Cp]
+  const uint16_t* V[3];  // [F][K][Cp]
   const float* sV;
   float* M;  // [F][K][T]
   int* err;  // set to 1 when a bounded wait gives up
@@ -375,9 +363,14 @@ struct TcGemmArgs {
   int K, Cp, NB, ncols, mode;
 };
 
-// Dynamic shared memory: per operand a 1024-byte-aligned tile: A 128 x 64 and
-// B NB x 64 16-bit values (hi, and lo for the split form), then the
-// mbarrier and the TMEM address.
+// Dynamic shared memory: per operand part a 1024-byte-aligned tile: A parts
+// 128 x 64, then B parts NB x 64 16-bit values, then the mbarrier and the
+// TMEM address.  Products per 16-channel step, as (A part, B part):
+//   1 part  (BF16, FP16): (0,0)
+//   2 parts (split x3):   (0,0) (0,1) (1,0)
+//   3 parts (split x6):   (0,0) into accumulator D, then (0,1) (1,0) (0,2)
+//                         (2,0) (1,1) into a second accumulator D' (TMEM
+//                         columns NB..2NB-1); the epilogue adds D + D'
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   // the swizzled tiles must start on 1024-byte boundaries (the host asks for
@@ -387,13 +380,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
   const int64_t t0 = (int64_t)blockIdx.x * kTcM;
   const int n0 = blockIdx.y * P.NB;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool split = P.mode == 3;
+  const int parts = tc_parts(P.mode);
   const uint32_t a_bytes = kTcM * 128, b_bytes = P.NB * 128;
-  unsigned char* Ah = tsm;
-  unsigned char* Bh = Ah + a_bytes;
-  unsigned char* Al = Bh + b_bytes;
-  unsigned char* Bl = Al + (split ? a_bytes : 0);
-  unsigned char* tail = Bl + (split ? b_bytes : 0);
+  unsigned char* As = tsm;                        // part p at As + p * a_bytes
+  unsigned char* Bs = As + parts * a_bytes;       // part p at Bs + p * b_bytes
+  unsigned char* tail = Bs + parts * b_bytes;
   uint64_t* bar = reinterpret_cast<uint64_t*>(tail);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 8);
   const uint32_t bar_a = smem_addr(bar);
@@ -427,15 +418,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
       const int r = e >> 3, j = e & 7;
       const uint32_t off = r * 128 + ((j ^ (r & 7)) << 4);
       const int64_t g = f * aplane + (t0 + r) * P.Cp + c0 + j * 8;
-      cp_async16_tc(smem_addr(Ah + off), P.Uh + g);
-      if (split) cp_async16_tc(smem_addr(Al + off), P.Ul + g);
+      for (int pp = 0; pp < parts; ++pp)
+        cp_async16_tc(smem_addr(As + pp * a_bytes + off), P.U[pp] + g);
     }
     for (int e = tid; e < P.NB * 8; e += kTcThreads) {
       const int r = e >> 3, j = e & 7;
       const uint32_t off = r * 128 + ((j ^ (r & 7)) << 4);
       const int64_t g = f * bplane + (int64_t)(n0 + r) * P.Cp + c0 + j * 8;
-      cp_async16_tc(smem_addr(Bh + off), P.Vh + g);
-      if (split) cp_async16_tc(smem_addr(Bl + off), P.Vl + g);
+      for (int pp = 0; pp < parts; ++pp)
+        cp_async16_tc(smem_addr(Bs + pp * b_bytes + off), P.V[pp] + g);
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -445,14 +436,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
 #pragma unroll
       for (int kk = 0; kk < kTcKc / 16; ++kk) {
         const uint32_t acc = (ch > 0 || kk > 0) ? 1u : 0u;
-        const uint64_t ah = sw128_desc(smem_addr(Ah) + kk * 32);
-        const uint64_t bh = sw128_desc(smem_addr(Bh) + kk * 32);
-        mma_f16(tmem, ah, bh, idesc, acc);
-        if (split) {
-          const uint64_t al = sw128_desc(smem_addr(Al) + kk * 32);
-          const uint64_t bl = sw128_desc(smem_addr(Bl) + kk * 32);
-          mma_f16(tmem, ah, bl, idesc, 1u);
-          mma_f16(tmem, al, bh, idesc, 1u);
+        uint64_t ad[3], bd[3];
+        for (int pp = 0; pp < parts; ++pp) {
+          ad[pp] = sw128_desc(smem_addr(As + pp * a_bytes) + kk * 32);
+          bd[pp] = sw128_desc(smem_addr(Bs + pp * b_bytes) + kk * 32);
+        }
+        mma_f16(tmem, ad[0], bd[0], idesc, acc);
+        if (parts == 2) {
+          mma_f16(tmem, ad[0], bd[1], idesc, 1u);
+          mma_f16(tmem, ad[1], bd[0], idesc, 1u);
+        } else if (parts == 3) {
+          const uint32_t tlo = tmem + (uint32_t)P.NB;  // second accumulator
+          mma_f16(tlo, ad[0], bd[1], idesc, acc);
+          mma_f16(tlo, ad[1], bd[0], idesc, 1u);
+          mma_f16(tlo, ad[0], bd[2], idesc, 1u);
+          mma_f16(tlo, ad[2], bd[0], idesc, 1u);
+          mma_f16(tlo, ad[1], bd[1], idesc, 1u);
         }
       }
       asm volatile(
@@ -474,16 +473,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
     const float inv = 1.0f / (P.S.sU[f] * P.sV[f]);  // exact: powers of two
     const int64_t t = t0 + warp * 32 + lane;
     for (int col = 0; col < P.NB; col += 16) {
-      uint32_t v[16];
+      uint32_t v[16], w[16];
       const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-          "%14,%15}, [%16];\n"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(ta));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      tmem_ld16(ta, v);
+      if (parts == 3) {
+        tmem_ld16(ta + (uint32_t)P.NB, w);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          v[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[j]), __uint_as_float(w[j])));
+      }
       if (t < P.T) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
@@ -500,23 +498,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
   }
 }
 
-static size_t tc_smem_bytes(int NB, bool split) {
+// TMEM columns of one CTA: NB FP32 accumulator columns (two accumulators for
+// the split x6 form), at least 32.
+static int tc_ncols(int NB, int parts) {
+  const int c = parts == 3 ? 2 * NB : NB;
+  return c < 32 ? 32 : c;
+}
+
+static size_t tc_smem_bytes(int NB, int parts) {
   const size_t a = (size_t)kTcM * 128, b = (size_t)NB * 128;
-  size_t s = (a + b) * (split ? 2 : 1) + 64 + 1024;
+  size_t s = (a + b) * parts + 64 + 1024;
+  // a CTA holding more than half of TMEM (512 columns) must be alone on its
+  // SM: ask for more than half of the shared memory
+  if (tc_ncols(NB, parts) > 256 && s < 120 * 1024) s = 120 * 1024;
   // at most two CTAs per SM, so their TMEM columns (NB <= 256 each) fit
   return s < 80 * 1024 ? 80 * 1024 : s;
 }
 
 // Workspace layout of the precision form (bytes), all 1024-aligned.
 struct TcLayout {
-  size_t V32, vmax, sV, err, Vh, Vl, Uh, Ul, M, total;
+  size_t V32, vmax, sV, err, V[3], U[3], M, total;
 };
 
 static TcLayout tc_layout(const LayerGeom& g, int dtype) {
   auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
   const int64_t Tp = (g.T + kTcM - 1) / kTcM * kTcM;
   const int Cp = (g.C + kTcKc - 1) / kTcKc * kTcKc;
-  const bool split = dtype == WINO_SPLIT_BF16X3;
+  const int parts = tc_parts(dtype);
   TcLayout L;
   size_t o = 0;
   L.V32 = o;
@@ -527,14 +535,14 @@ static TcLayout tc_layout(const LayerGeom& g, int dtype) {
   o = al(o + (size_t)g.F * 4);
   L.err = o;
   o = al(o + 64);
-  L.Vh = o;
-  o = al(o + (size_t)g.F * g.K * Cp * 2);
-  L.Vl = o;
-  o = al(o + (split ? (size_t)g.F * g.K * Cp * 2 : 0));
-  L.Uh = o;
-  o = al(o + (size_t)g.F * Tp * Cp * 2);
-  L.Ul = o;
-  o = al(o + (split ? (size_t)g.F * Tp * Cp * 2 : 0));
+  for (int pp = 0; pp < 3; ++pp) {
+    L.V[pp] = o;
+    o = al(o + (pp < parts ? (size_t)g.F * g.K * Cp * 2 : 0));
+  }
+  for (int pp = 0; pp < 3; ++pp) {
+    L.U[pp] = o;
+    o = al(o + (pp < parts ? (size_t)g.F * Tp * Cp * 2 : 0));
+  }
   L.M = o;
   o = al(o + (size_t)g.F * g.K * g.T * 4);
   L.total = o;
@@ -566,20 +574,21 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     set_error("workspace too small for the tensor-core form");
     return WINO_ENOMEM;
   }
-  const int mode = dtype;  // 1 bf16, 2 fp16, 3 split bf16
+  const int mode = dtype;  // 1 bf16, 2 fp16, 3 split bf16 x3, 4 split bf16 x6
+  const int parts = tc_parts(mode);
   char* b = (char*)ws;
   float* V32 = (float*)(b + L.V32);
   unsigned* vmax = (unsigned*)(b + L.vmax);
   float* sV = (float*)(b + L.sV);
   int* err = (int*)(b + L.err);
-  uint16_t* Vh = (uint16_t*)(b + L.Vh);
-  uint16_t* Vl = (uint16_t*)(b + L.Vl);
-  uint16_t* Uh = (uint16_t*)(b + L.Uh);
-  uint16_t* Ul = (uint16_t*)(b + L.Ul);
+  uint16_t *Vp[3], *Up[3];
+  for (int pp = 0; pp < 3; ++pp) {
+    Vp[pp] = (uint16_t*)(b + L.V[pp]);
+    Up[pp] = (uint16_t*)(b + L.U[pp]);
+  }
   float* Mb = (float*)(b + L.M);
   const int64_t Tp = (g.T + kTcM - 1) / kTcM * kTcM;
   const int Cp = (g.C + kTcKc - 1) / kTcKc * kTcKc;
-  const bool split = dtype == WINO_SPLIT_BF16X3;
 
   // per-frequency scale of U from the transform's row norms (host, exact)
   TcScales S;
@@ -609,35 +618,38 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
                                                             (8 * kVmaxThreads));
     k_vmax<<<dim3(bx, (unsigned)g.F), kVmaxThreads, 0, st>>>(V32, plane, vmax);
     const int64_t nq = (int64_t)g.F * g.K * Cp;
-    k_quant_v<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(V32, g.C, g.K, Cp, g.F, vmax, sV, Vh,
-                                                            Vl, mode);
+    k_quant_v<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(V32, g.C, g.K, Cp, g.F, vmax, sV,
+                                                            Vp[0], Vp[1], Vp[2], mode);
     const dim3 gq((unsigned)(Tp / kQT), (unsigned)(Cp / kQC));
-    const size_t qsm = (size_t)2 * g.F * kQT * kQC * sizeof(uint16_t);
+    const size_t qsm = (size_t)parts * g.F * kQT * kQC * sizeof(uint16_t);
     static bool qattr[16] = {false};
     int qdev = 0;
     WINO_CUDA_TRY(cudaGetDevice(&qdev));
     if (qdev < 16 && !qattr[qdev]) {
       WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
       WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<4>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
       WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<6>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
       qattr[qdev] = true;
     }
     if (M.m == 2)
-      k_quant_input_tiled<2><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
+      k_quant_input_tiled<2><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                         mode);
     else if (M.m == 4)
-      k_quant_input_tiled<4><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
+      k_quant_input_tiled<4><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                         mode);
     else
-      k_quant_input_tiled<6><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Uh, Ul, mode);
+      k_quant_input_tiled<6><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                         mode);
     note_launches(4);
   }
   TcGemmArgs P;
-  P.Uh = Uh;
-  P.Ul = Ul;
-  P.Vh = Vh;
-  P.Vl = Vl;
+  for (int pp = 0; pp < 3; ++pp) {
+    P.U[pp] = Up[pp];
+    P.V[pp] = Vp[pp];
+  }
   P.sV = sV;
   P.M = Mb;
   P.err = err;
@@ -647,9 +659,9 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
   P.K = g.K;
   P.Cp = Cp;
   P.NB = NB;
-  P.ncols = NB < 32 ? 32 : NB;
+  P.ncols = tc_ncols(NB, parts);
   P.mode = mode;
-  const size_t smem = tc_smem_bytes(NB, split);
+  const size_t smem = tc_smem_bytes(NB, parts);
   static bool attr_set[16] = {false};
   int dev = 0;
   WINO_CUDA_TRY(cudaGetDevice(&dev));

@@ -1,13 +1,15 @@
 """GPU parity of the precision form of the contraction (tcgen05 BF16 / FP16 /
-split BF16x3 with per-frequency power-of-two scaling) against the oracle's
-emulation of the same rounding.
+split BF16x3 / split BF16x6 with per-frequency power-of-two scaling) against
+the oracle's emulation of the same rounding.
 
 Both sides round the same FP32 transform outputs to the same 16-bit
 operands and form exact products; only the FP32 accumulation order of the
 tensor cores differs from the oracle's sequential fmaf.  Bar: max |yGPU -
 yoracle| <= 2e-5 max |yoracle| (accumulation-order differences amplified by
 the output transform), and the relative L1 error against FP64 within 5% of
-the oracle's."""
+the oracle's (split BF16x6: at most 5% above it -- its operands are exact to
+2^-24, so the accumulation order dominates its error, and the tensor cores'
+order may beat the oracle's sequential fmaf)."""
 import math
 
 import numpy as np
@@ -22,7 +24,7 @@ PTS = {4: [0.0, -1 / 1.622, -1.622, 1.622, 1 / 1.622, math.inf],
        2: [0.0, -1.0, 1.0, math.inf]}
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "fp16", "split_bf16x3"])
+@pytest.mark.parametrize("dtype", ["bf16", "fp16", "split_bf16x3", "split_bf16x6"])
 @pytest.mark.parametrize("m", [4, 6, 2])
 @pytest.mark.parametrize("shape", [(2, 64, 64, 10, 10), (1, 80, 128, 9, 13), (1, 64, 256, 6, 6)])
 def test_tc_layer_vs_oracle_emulation(wino, orc, dtype, m, shape):
@@ -43,19 +45,25 @@ def test_tc_layer_vs_oracle_emulation(wino, orc, dtype, m, shape):
     ref = orc.direct_f64(x, w, 2, 1, 3)
     eg = np.abs(yg - ref).sum() / np.abs(ref).sum()
     eo = np.abs(yo.astype(np.float64) - ref).sum() / np.abs(ref).sum()
-    assert abs(eg / eo - 1) < 0.05, (eg, eo)
+    if dtype == "split_bf16x6":
+        # operands exact to 2^-24: the accumulation order is the dominant
+        # error term, and the tensor cores' order may be the better one
+        assert eg <= 1.05 * eo, (eg, eo)
+    else:
+        assert abs(eg / eo - 1) < 0.05, (eg, eo)
 
 
 def test_tc_error_ordering_matches_precision(wino, orc):
-    """BF16 > FP16 > split BF16x3 > FP32 in error against FP64 (F(4x4,3x3))."""
+    """BF16 > FP16 > split BF16x3 > FP32 >= split BF16x6 in error against FP64
+    (F(4x4,3x3))."""
     import torch
     x, w = inputs.vgg_layer_host(64, 20, N=2, seed=3)
     xt, wt = torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda()
     ref = orc.direct_f64(x, w, 2, 1, 3)
     err = {}
-    for dt in ("f32", "bf16", "fp16", "split_bf16x3"):
+    for dt in ("f32", "bf16", "fp16", "split_bf16x3", "split_bf16x6"):
         y = torch.empty((2, 64, 20, 20), device="cuda")
         wino.wino_conv2d(xt, wt, y, PTS[4], 4, 3, 1, dt)
         torch.cuda.synchronize()
         err[dt] = np.abs(y.cpu().numpy() - ref).sum() / np.abs(ref).sum()
-    assert err["bf16"] > err["fp16"] > err["split_bf16x3"] > err["f32"]
+    assert err["bf16"] > err["fp16"] > err["split_bf16x3"] > err["f32"] >= err["split_bf16x6"]

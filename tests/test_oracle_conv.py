@@ -189,6 +189,43 @@ def test_lowp_layer_error_ordering(orc):
     assert err["split_bf16x3"] < err["bf16"] / 20
 
 
+@pytest.mark.parametrize("xs,ws,C", [(1000, 300, 1), (200, 200, 3)])
+def test_split_bf16x6_exact_on_integer_operands(orc, xs, ws, C):
+    """Exact regime: integer inputs and the points {0, -1, 1, inf} (exact FP32
+    matrices) keep every FP32 step of the layer exact, so the FP32 layer
+    equals the FP64 direct correlation.  The three-part split holds every bit
+    of each operand and keeps every nonzero product of operands with at most
+    16 significant bits, so split BF16x6 must reproduce it bit for bit, while
+    split BF16x3 (lo x lo dropped) must not -- a dropped or misplaced part or
+    product fails here."""
+    rng = np.random.default_rng(5)
+    x = rng.integers(-xs, xs + 1, (1, C, 8, 8)).astype(np.float32)
+    w = rng.integers(-ws, ws + 1, (2, C, 3, 3)).astype(np.float32)
+    pts = [0.0, -1.0, 1.0, math.inf]
+    ref = orc.direct_f64(x, w, 2, 1, 3)
+    y32 = orc.wino_layer(x, w, 2, 1, pts, 2, 3, "f32")
+    assert np.array_equal(y32.astype(np.float64), ref)
+    assert np.array_equal(orc.wino_layer(x, w, 2, 1, pts, 2, 3, "split_bf16x6"), y32)
+    assert not np.array_equal(orc.wino_layer(x, w, 2, 1, pts, 2, 3, "split_bf16x3"), y32)
+
+
+@pytest.mark.parametrize("C,H,m", [(16, 12, 4), (64, 20, 6)])
+def test_split_bf16x6_error_not_above_fp32(orc, C, H, m):
+    """Split BF16x6 with its two accumulators (hh alone; the five small
+    products apart) is at least as accurate against FP64 as the FP32 layer."""
+    from paper_2201_10369_gb300 import inputs
+    x, w = inputs.vgg_layer_host(C, H, N=2, seed=3)
+    c = 1.622
+    pts = {4: [0.0, -1 / c, -c, c, 1 / c, math.inf],
+           6: [0.0, -0.5, -2.0, 2.0, 0.5, -1.003, 1.003, math.inf]}[m]
+    ref = orc.direct_f64(x, w, 2, 1, 3)
+    err = {}
+    for mode in ("f32", "split_bf16x6"):
+        y = orc.wino_layer(x, w, 2, 1, pts, m, 3, mode).astype(np.float64)
+        err[mode] = np.abs(y - ref).sum() / np.abs(ref).sum()
+    assert err["split_bf16x6"] <= err["f32"], err
+
+
 @pytest.mark.parametrize("dim,m", [(2, 2), (2, 4), (2, 6), (1, 4)])
 def test_layer_tiles_equals_layer(orc, dim, m):
     """The per-tile oracle entry reproduces the full layer bit for bit on
