@@ -522,8 +522,8 @@ def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
 # launch = that ratio x the launch's algorithmic bytes (traffic grows in
 # proportion to the bytes the launch must move).
 NCU_TRAFFIC = {
-    # k_gemm_otx F(4x4), C = K = 64, 224x224, N = 8: U read + y written
-    "fused_layer": (307.66e6, 36 * 25088 * 64 * 4 + 8 * 64 * 224 * 224 * 4),
+    # k_gemm_otx F(4x4) tile shape 1, C = K = 64, 224x224, N = 8: U read + y written
+    "fused_layer": (311.44e6, 36 * 25088 * 64 * 4 + 8 * 64 * 224 * 224 * 4),
     # k_tc_gemm BF16, same layer: U + V read (16-bit), M written (FP32)
     "tc_gemm": (289.35e6, 36 * (2 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
 }
@@ -588,11 +588,14 @@ def profile_case(name):
     from paper_2201_10369_gb300 import inputs
     wino.build()
     wino.load()
-    base = name[:-4] if name.endswith("_vgg") else name
+    base, shapes, nimg = name, [(64, 224)], 8
+    if name.endswith("_vgg"):  # the five VGG16 stages, N=8
+        base, shapes = name[:-4], inputs.VGG16_LAYERS
+    elif name[-3:-1] == "_l":  # one VGG16 stage at the bench's N=32
+        base, shapes, nimg = name[:-3], [inputs.VGG16_LAYERS[int(name[-1])]], 32
     if base in ("f4x4", "f6x6", "f4x4_bf16", "f4x4_split"):
-        # one layer (64 ch, 224x224), or with _vgg the five VGG16 stages, N=8
-        shapes = inputs.VGG16_LAYERS if name.endswith("_vgg") else [(64, 224)]
-        xs = [inputs.vgg_layer_device(C, H, N=8, seed=i) for i, (C, H) in enumerate(shapes)]
+        # one layer (64 ch, 224x224, N=8) unless a suffix says otherwise
+        xs = [inputs.vgg_layer_device(C, H, N=nimg, seed=i) for i, (C, H) in enumerate(shapes)]
         ys = [torch.empty_like(x) for x, _ in xs]
         m, pts = (4, PTS4) if base.startswith("f4x4") else (6, PTS6)
         dt = {"f4x4_bf16": "bf16", "f4x4_split": "split_bf16x3"}.get(base, "f32")
@@ -619,8 +622,8 @@ def main():
     ap.add_argument("--profile-case", default=None,
                     help="run one small workload a few times for an ncu capture: "
                          "f4x4 | f6x6 | f4x4_bf16 | f4x4_split (VGG 64ch 224x224, N=8; "
-                         "suffix _vgg: the five VGG16 stages, N=8) | sweep (2D F(4x4), "
-                         "all masks, 4096 c)")
+                         "suffix _vgg: the five VGG16 stages, N=8; suffix _l0.._l4: that "
+                         "VGG16 stage at N=32) | sweep (2D F(4x4), all masks, 4096 c)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -335,6 +335,16 @@ int wino_profile_read(const char* kernel, double* total_ms, int* launches);
  * devices); a diagnostic for counting launches inside a timed region.      */
 unsigned long long wino_kernel_launches(void);
 
+/* Device-side failure detection.  Layer kernels that wait on hardware
+ * completion (the tensor-core contraction's mbarrier, the FP32 layer's bulk
+ * copies) bound every wait; a wait that gives up sets a per-device flag and
+ * the kernel abandons its tile (its output is then incomplete) instead of
+ * hanging.  Because layer calls return before their kernels run, the flag
+ * is reported here: *flag = 1 when any wait gave up on the current device
+ * since the last call, else 0; the flag is cleared.  Synchronises the
+ * device.                                                                  */
+int wino_wait_error(int* flag);
+
 const char* wino_last_error(void);  /* thread-local message, never NULL  */
 int wino_device_ok(void);           /* 1 when an sm_103 device is usable  */
 void wino_shutdown(void);           /* frees internal scratch and graphs  */

@@ -109,6 +109,8 @@ def _declare(L):
     L.wino_kernel_launches.argtypes = []
     L.wino_last_error.restype = ctypes.c_char_p
     L.wino_device_ok.restype = _i
+    L.wino_wait_error.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    L.wino_wait_error.restype = _i
     L.wino_shutdown.restype = None
     for name in ("wino_make_matrices", "wino_conv1d", "wino_conv2d", "wino_set_workspace",
                  "wino_direct_conv_f64", "wino_error_stats", "wino_error_sweep"):
@@ -681,6 +683,15 @@ def wino_last_error() -> str:
 
 def wino_device_ok() -> bool:
     return bool(load().wino_device_ok())
+
+
+def wino_wait_error() -> bool:
+    """True when a bounded device wait in a layer kernel gave up on the
+    current device since the last call (that layer's output is incomplete);
+    clears the flag.  Synchronises the device."""
+    f = ctypes.c_int(0)
+    _check(load().wino_wait_error(ctypes.byref(f)))
+    return bool(f.value)
 
 
 def wino_shutdown():

@@ -43,6 +43,7 @@ Scratch g_scratch[kMaxDev][kNumScratch];
 void* g_user_ws = nullptr;
 size_t g_user_ws_bytes = 0;
 int g_dev_ok[kMaxDev] = {0};  // 0 unknown, 1 ok, -1 not ok
+int* g_wait_flag[kMaxDev] = {nullptr};
 }  // namespace
 
 int scratch_get(int slot, size_t bytes, void** ptr) {
@@ -73,6 +74,25 @@ int scratch_get(int slot, size_t bytes, void** ptr) {
     s.bytes = want;
   }
   *ptr = s.ptr;
+  return WINO_OK;
+}
+
+int wait_error_flag(int** ptr) {
+  int* (&flags)[kMaxDev] = g_wait_flag;
+  int dev = 0;
+  WINO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) {
+    set_error("device index out of range");
+    return WINO_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!flags[dev]) {
+    int* p = nullptr;
+    WINO_CUDA_TRY(cudaMalloc(&p, sizeof(int)));
+    WINO_CUDA_TRY(cudaMemset(p, 0, sizeof(int)));
+    flags[dev] = p;
+  }
+  *ptr = flags[dev];
   return WINO_OK;
 }
 
@@ -367,6 +387,22 @@ const char* wino_last_error(void) { return g_last_error.c_str(); }
 
 int wino_device_ok(void) { return check_device() == WINO_OK ? 1 : 0; }
 
+int wino_wait_error(int* flag) {
+  if (!flag) {
+    set_error("flag is NULL");
+    return WINO_EINVAL;
+  }
+  int st = check_device();
+  if (st != WINO_OK) return st;
+  int* d = nullptr;
+  st = wait_error_flag(&d);
+  if (st != WINO_OK) return st;
+  WINO_CUDA_TRY(cudaDeviceSynchronize());
+  WINO_CUDA_TRY(cudaMemcpy(flag, d, sizeof(int), cudaMemcpyDeviceToHost));
+  WINO_CUDA_TRY(cudaMemset(d, 0, sizeof(int)));
+  return WINO_OK;
+}
+
 void wino_shutdown(void) {
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   int cur = 0;
@@ -384,6 +420,11 @@ void wino_shutdown(void) {
         g_scratch[d][s].ptr = nullptr;
         g_scratch[d][s].bytes = 0;
       }
+  for (int d = 0; d < kMaxDev; ++d)
+    if (g_wait_flag[d]) {
+      if (cudaSetDevice(d) == cudaSuccess) (void)cudaFree(g_wait_flag[d]);
+      g_wait_flag[d] = nullptr;
+    }
   (void)cudaSetDevice(cur);
   (void)cudaGetLastError();
 }

@@ -33,6 +33,45 @@ struct LayerGeom {
 // general path" (never returned through the ABI).
 constexpr int kFallback = 1;
 
+// Filter transform of one (c, k) kernel g (r taps in 1D, r x r in 2D), FP32
+// in the layer's fixed order: 1D v_i = sum_q G[i][q] g[q]; 2D W = G g, then
+// V[i][j] = sum_q W[i][q] G[j][q]; every sum from zero with fmaf, inner
+// index ascending.  sink(f, v) receives frequency f = i (1D) or i alpha + j.
+template <class Sink>
+__device__ __forceinline__ void filter_transform_one(const float* __restrict__ g, int dim,
+                                                     const LayerMats& M, Sink sink) {
+  const int A = M.alpha, r = M.r;
+  const int taps = (dim == 1) ? r : r * r;
+  float gl[kMaxR * kMaxR];
+  for (int i = 0; i < taps; ++i) gl[i] = g[i];
+  if (dim == 1) {
+    for (int i = 0; i < A; ++i) {
+      float acc = 0.0f;
+      for (int q = 0; q < r; ++q) acc = fmaf(M.G[i * r + q], gl[q], acc);
+      sink(i, acc);
+    }
+    return;
+  }
+  float Wk[kMaxAlpha * kMaxR];
+  for (int i = 0; i < A; ++i)
+    for (int q = 0; q < r; ++q) {
+      float acc = 0.0f;
+      for (int l = 0; l < r; ++l) acc = fmaf(M.G[i * r + l], gl[l * r + q], acc);
+      Wk[i * r + q] = acc;
+    }
+  for (int i = 0; i < A; ++i)
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+      for (int q = 0; q < r; ++q) acc = fmaf(Wk[i * r + q], M.G[j * r + q], acc);
+      sink(i * A + j, acc);
+    }
+}
+
+// Per-device int in device memory, zero until a kernel's bounded wait gives
+// up (the kernel then stores 1 and abandons its tile); wino_wait_error
+// reads and clears it.
+int wait_error_flag(int** ptr);
+
 // Error reporting (thread-local text, see wino_last_error).
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);

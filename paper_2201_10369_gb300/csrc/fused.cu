@@ -43,6 +43,32 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool v
                "r"(valid ? 16 : 0));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+
+// Two FP32 values in one 64-bit register (low half first).  fma.rn.f32x2
+// computes each half as an IEEE fused multiply-add with one rounding --
+// exactly fmaf -- so a microkernel written with it gives the same bits as
+// the scalar one, in half the FMA instructions.
+__device__ __forceinline__ unsigned long long pack_dup(float a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
@@ -199,13 +225,14 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
   const int lt = (lane / LK) % LT;
   const int lk = lane % LK;
   const int f0 = (warp * LX + lx) * FPL;  // first of this lane's FPL frequencies
-  float acc[FPL][MT][MK];
+  // acc[q][i][j2] holds output channels (2 j2, 2 j2 + 1) of tile i
+  unsigned long long acc[FPL][MT][MK / 2];
 #pragma unroll
   for (int q = 0; q < FPL; ++q)
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int j = 0; j < MK; ++j) acc[q][i][j] = 0.0f;
+      for (int j = 0; j < MK / 2; ++j) acc[q][i][j] = 0ull;
 
   load_chunk(0, 0);
   cp_async_wait_all();
@@ -223,7 +250,8 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
       for (int q = 0; q < FPL; ++q) {
         const float* up = Us + (f0 + q) * Cfg::UPL + cc * TB + lt * MT;
         const float* vp = vbase + (f0 + q) * Cfg::VPL + cc * KB;
-        float a[MT], b[MK];
+        float a[MT];
+        unsigned long long b2[MK / 2];  // channel pairs
 #pragma unroll
         for (int i = 0; i < MT; i += 4) {
           const float4 v = *reinterpret_cast<const float4*>(up + i);
@@ -234,16 +262,16 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
         }
 #pragma unroll
         for (int s4 = 0; s4 < MK / 4; ++s4) {
-          const float4 v = *reinterpret_cast<const float4*>(vp + s4 * 4 * LK);
-          b[4 * s4] = v.x;
-          b[4 * s4 + 1] = v.y;
-          b[4 * s4 + 2] = v.z;
-          b[4 * s4 + 3] = v.w;
+          const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(vp + s4 * 4 * LK);
+          b2[2 * s4] = v.x;
+          b2[2 * s4 + 1] = v.y;
         }
 #pragma unroll
-        for (int i = 0; i < MT; ++i)
+        for (int i = 0; i < MT; ++i) {
+          const unsigned long long ai = pack_dup(a[i]);
 #pragma unroll
-          for (int j = 0; j < MK; ++j) acc[q][i][j] = fmaf(a[i], b[j], acc[q][i][j]);
+          for (int j = 0; j < MK / 2; ++j) acc[q][i][j] = fma2(ai, b2[j], acc[q][i][j]);
+        }
       }
     }
     cp_async_wait_all();
@@ -266,9 +294,8 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
 #pragma unroll
       for (int s4 = 0; s4 < MK / 4; ++s4) {
         float* dst = Es + ((size_t)(f0 + q) * TB + lt * MT + i) * Cfg::EKB + s4 * 4 * LK + lk * 4;
-        *reinterpret_cast<float4*>(dst) =
-            make_float4(acc[q][i][4 * s4], acc[q][i][4 * s4 + 1], acc[q][i][4 * s4 + 2],
-                        acc[q][i][4 * s4 + 3]);
+        const float2 lo = unpack2(acc[q][i][2 * s4]), hi = unpack2(acc[q][i][2 * s4 + 1]);
+        *reinterpret_cast<float4*>(dst) = make_float4(lo.x, lo.y, hi.x, hi.y);
       }
   __syncthreads();
   for (int p = tid; p < TB * KB; p += NT) {
@@ -365,41 +392,121 @@ int layer_forward_fused(const float* x, const float* w, float* y, const LayerGeo
 // ===========================================================================
 // Split variant: a memory-bound input-transform kernel writes U once, then a
 // compute-bound kernel runs the alpha^2 contractions with the output
-// transform fused into its epilogue (M never leaves the SM).  The main loop
-// only streams contiguous U / V rows (16-byte cp.async, double-buffered) and
-// issues FFMAs.  Same operation order as the fused kernel, bit for bit.
-// U is stored [F][C][Tp], Tp = T rounded up to a multiple of 4.
+// transform fused into its epilogue (M never leaves the SM).
+//
+// U and V are written in a blocked layout, so that everything one CTA needs
+// for one chunk of CC input channels is ONE contiguous run per operand:
+//   Ub[tile block][chunk][f][UPL]   UPL = CC TB + 4 (row cc at cc TB)
+//   Vb[k block][chunk][f][VPL]      VPL = CC KB + 16 (row cc at cc KB)
+// (channels past C are zero; the padding words are never read).  The GEMM
+// kernel streams chunks with two bulk copies (cp.async.bulk, the TMA's 1D
+// form) per chunk into an NS-stage ring of shared-memory stages whose
+// mbarriers count the bytes: no per-thread copy instructions, and NS - 1
+// chunks in flight.  The inner product order is that of the fused kernel
+// (c ascending, fused multiply-add), bit for bit.
 // ===========================================================================
 
-// One thread per (c, tile), tile fastest: coalesced U rows; the input patch
-// loads of neighbouring tiles overlap and hit L1.
+namespace {
+
+__device__ __forceinline__ void mbar_init1(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// One bulk copy global -> shared, completion counted on `bar` in bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Waits for phase `parity` of `bar` to complete, at most 2^22 polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+// Blocked layout geometry of one split tile shape.
+struct SplitGeom {
+  int TB, KB, CC, UPL, VPL, nch, ntb, nkb;
+  int64_t ub_floats() const { return (int64_t)ntb * nch * F_ * UPL; }
+  int64_t vb_floats() const { return (int64_t)nkb * nch * F_ * VPL; }
+  int F_;
+};
+
+static SplitGeom split_geom(const LayerGeom& g, int TB, int KB, int CC) {
+  SplitGeom s;
+  s.TB = TB;
+  s.KB = KB;
+  s.CC = CC;
+  s.UPL = CC * TB + 4;
+  s.VPL = CC * KB + 16;
+  s.nch = (g.C + CC - 1) / CC;
+  s.ntb = (int)((g.T + TB - 1) / TB);
+  s.nkb = g.K / KB;
+  s.F_ = g.F;
+  return s;
+}
+
+// Input transform into Ub: one CTA per (tile block, chunk), one thread per
+// (channel, tile) of it (tiles fastest: neighbouring tiles share input rows
+// in L1).  The chunk's F x UPL floats are staged in shared memory and leave
+// as one contiguous run of 16-byte stores (the chunk's rows are UPL floats
+// apart, not a multiple of the 128-byte line, so per-row stores would split
+// lines).  Launch: grid (ntb, nch), blockDim = CC x TB, dynamic shared
+// memory F x UPL floats.
 template <int MM>
-__global__ void __launch_bounds__(256) k_input_transform_r3(const float* __restrict__ x,
-                                                            float* __restrict__ U,
-                                                            const LayerGeom g, const LayerMats Mx,
-                                                            int64_t Tp) {
-  constexpr int A = MM + 2;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)g.C * Tp) return;
-  const int64_t t = idx % Tp;
-  const int c = (int)(idx / Tp);
-  if (t >= g.T) return;
-  const int tpi = g.th * g.tw;
-  const int n = (int)(t / tpi);
-  const int rem = (int)(t - (int64_t)n * tpi);
-  const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
-  const int h0 = ti * MM - g.pad, w0 = tj * MM - g.pad;
-  const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
+__global__ void __launch_bounds__(256) k_input_transform_blk(const float* __restrict__ x,
+                                                             float* __restrict__ Ub,
+                                                             const LayerGeom g,
+                                                             const LayerMats Mx,
+                                                             const SplitGeom sg) {
+  constexpr int A = MM + 2, F = A * A;
+  extern __shared__ __align__(16) float cs[];  // [F][UPL]
+  const int tb = blockIdx.x, ch = blockIdx.y;
+  const int tl = threadIdx.x % sg.TB, cc = threadIdx.x / sg.TB;
+  const int64_t t = (int64_t)tb * sg.TB + tl;
+  const int c = ch * sg.CC + cc;
   float d[A][A];
+  const bool live = t < g.T && c < g.C;
+  if (live) {
+    const int tpi = g.th * g.tw;
+    const int n = (int)(t / tpi);
+    const int rem = (int)(t - (int64_t)n * tpi);
+    const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
+    const int h0 = ti * MM - g.pad, w0 = tj * MM - g.pad;
+    const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
 #pragma unroll
-  for (int i = 0; i < A; ++i)
+    for (int i = 0; i < A; ++i)
 #pragma unroll
-    for (int j = 0; j < A; ++j) {
-      const int hh = h0 + i, ww = w0 + j;
-      d[i][j] = ((unsigned)hh < (unsigned)g.H && (unsigned)ww < (unsigned)g.W)
-                    ? __ldg(xc + (int64_t)hh * g.W + ww)
-                    : 0.0f;
-    }
+      for (int j = 0; j < A; ++j) {
+        const int hh = h0 + i, ww = w0 + j;
+        d[i][j] = ((unsigned)hh < (unsigned)g.H && (unsigned)ww < (unsigned)g.W)
+                      ? __ldg(xc + (int64_t)hh * g.W + ww)
+                      : 0.0f;
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < A; ++i)
+#pragma unroll
+      for (int j = 0; j < A; ++j) d[i][j] = 0.0f;
+  }
   float tm[A][A];
 #pragma unroll
   for (int i = 0; i < A; ++i)
@@ -410,8 +517,7 @@ __global__ void __launch_bounds__(256) k_input_transform_r3(const float* __restr
       for (int q = 0; q < A; ++q) acc = fmaf(Mx.BT[i * A + q], d[q][l], acc);
       tm[i][l] = acc;
     }
-  const int64_t plane = (int64_t)g.C * Tp;
-  float* out = U + (int64_t)c * Tp + t;
+  float* row = cs + cc * sg.TB + tl;
 #pragma unroll
   for (int i = 0; i < A; ++i)
 #pragma unroll
@@ -419,118 +525,194 @@ __global__ void __launch_bounds__(256) k_input_transform_r3(const float* __restr
       float acc = 0.0f;
 #pragma unroll
       for (int l = 0; l < A; ++l) acc = fmaf(tm[i][l], Mx.BT[j * A + l], acc);
-      out[(i * A + j) * plane] = acc;
+      row[(i * A + j) * sg.UPL] = live ? acc : 0.0f;
     }
+  __syncthreads();
+  // the chunk, padding words included, as 16-byte stores (F UPL is a
+  // multiple of 4 floats and the chunk starts 16-byte aligned)
+  const int n4 = F * sg.UPL / 4;
+  float4* dst = reinterpret_cast<float4*>(Ub + ((int64_t)tb * sg.nch + ch) * F * sg.UPL);
+  const float4* src = reinterpret_cast<const float4*>(cs);
+  for (int e = threadIdx.x; e < n4; e += blockDim.x) dst[e] = src[e];
 }
 
-template <FUSED_TPARAMS>
+// Filter transform into Vb: one thread per (channel, output channel) over
+// the padded channel range, output channels fastest.
+__global__ void __launch_bounds__(256) k_filter_transform_blk(const float* __restrict__ w,
+                                                              float* __restrict__ Vb, int C,
+                                                              int K, const LayerMats M,
+                                                              const SplitGeom sg) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)sg.nch * sg.CC * K) return;
+  const int k = (int)(idx % K), c = (int)(idx / K);
+  const int kb = k / sg.KB, kl = k - kb * sg.KB;
+  const int ch = c / sg.CC, cc = c - ch * sg.CC;
+  float* out = Vb + ((int64_t)kb * sg.nch + ch) * sg.F_ * sg.VPL + cc * sg.KB + kl;
+  if (c >= C) {
+    for (int f = 0; f < sg.F_; ++f) out[(int64_t)f * sg.VPL] = 0.0f;
+    return;
+  }
+  filter_transform_one(w + ((int64_t)k * C + c) * M.r * M.r, 2, M,
+                       [&](int f, float v) { out[(int64_t)f * sg.VPL] = v; });
+}
+
+// NS stages of (U chunk, V chunk) in shared memory.
+template <FUSED_TPARAMS, int NS>
 struct SplitCfg {
   using Base = FusedCfg<FUSED_TARGS>;
-  static constexpr int STAGE = Base::F * Base::UPL + Base::F * Base::VPL;
-  static constexpr int MAIN_FL = 2 * STAGE;
+  static constexpr int SU = Base::F * Base::UPL;  // U chunk (floats)
+  static constexpr int SV = Base::F * Base::VPL;  // V chunk (floats)
+  static constexpr int STAGE = SU + SV;
+  static constexpr int MAIN_FL = NS * STAGE;
   static constexpr int SMEM_FL = MAIN_FL > Base::EPI_FL ? MAIN_FL : Base::EPI_FL;
   static constexpr size_t SMEM = (size_t)SMEM_FL * sizeof(float);
+  static_assert(NS >= 2, "at least double buffering");
+  static_assert((SU * 4) % 16 == 0 && (SV * 4) % 16 == 0, "bulk copies move 16-byte multiples");
 };
 
-template <FUSED_TPARAMS>
+#define SPLIT_TPARAMS FUSED_TPARAMS, int NS
+#define SPLIT_TARGS FUSED_TARGS, NS
+
+template <SPLIT_TPARAMS>
 __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
-    k_gemm_otx(const float* __restrict__ U, const float* __restrict__ V, float* __restrict__ y,
-               const LayerGeom g, const LayerMats Mx, int64_t Tp) {
+    k_gemm_otx(const float* __restrict__ Ub, const float* __restrict__ Vb, float* __restrict__ y,
+               const LayerGeom g, const LayerMats Mx, const SplitGeom sg, int* err) {
   using Cfg = FusedCfg<FUSED_TARGS>;
-  using SC = SplitCfg<FUSED_TARGS>;
+  using SC = SplitCfg<SPLIT_TARGS>;
   constexpr int A = Cfg::A, F = Cfg::F, NT = Cfg::NT, TB = Cfg::TB, KB = Cfg::KB;
-  extern __shared__ __align__(16) float sm[];
+  extern __shared__ __align__(128) float sm[];
+  __shared__ __align__(8) uint64_t full[NS];
   const int tid = threadIdx.x;
   const int nkb = g.K / KB;
-  const int k0 = (int)(blockIdx.x % nkb) * KB;
-  const int64_t t0 = (int64_t)(blockIdx.x / nkb) * TB;
-  const int nchunks = (g.C + CC - 1) / CC;
+  const int kb = (int)(blockIdx.x % nkb);
+  const int tb = (int)(blockIdx.x / nkb);
+  const int k0 = kb * KB;
+  const int64_t t0 = (int64_t)tb * TB;
+  const int nchunks = sg.nch;
+  const float* ublk = Ub + (int64_t)tb * nchunks * SC::SU;
+  const float* vblk = Vb + (int64_t)kb * nchunks * SC::SV;
 
-  auto load_chunk = [&](int ch, int buf) {
-    const int c0 = ch * CC;
-    float* us = sm + buf * SC::STAGE;
-    float* vs = us + F * Cfg::UPL;
-    constexpr int NU4 = F * CC * (TB / 4);
-    for (int e = tid; e < NU4; e += NT) {
-      const int q = e % (TB / 4);
-      const int cc = (e / (TB / 4)) % CC;
-      const int f = e / ((TB / 4) * CC);
-      const int c = c0 + cc;
-      const bool ok = c < g.C && t0 + 4 * q < Tp;
-      const float* src = ok ? U + ((int64_t)f * g.C + c) * Tp + t0 + 4 * q : U;
-      cp_async16(smem_u32(us + f * Cfg::UPL + cc * TB + 4 * q), src, ok);
+  // per-tile output coordinates for the epilogue, computed once
+  __shared__ int64_t s_ybase[TB];  // offset of y[n][0][ti m][tj m]
+  __shared__ int s_rows[TB], s_cols[TB];  // valid output rows / columns (0: no tile)
+  if (tid < TB) {
+    const int64_t tg = t0 + tid;
+    if (tg < g.T) {
+      const int tpi = g.th * g.tw;
+      const int n = (int)(tg / tpi);
+      const int rem = (int)(tg - (int64_t)n * tpi);
+      const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
+      s_ybase[tid] = (int64_t)n * g.K * g.Ho * g.Wo + (int64_t)ti * MM * g.Wo + tj * MM;
+      s_rows[tid] = min(MM, g.Ho - ti * MM);
+      s_cols[tid] = min(MM, g.Wo - tj * MM);
+    } else {
+      s_ybase[tid] = 0;
+      s_rows[tid] = 0;
+      s_cols[tid] = 0;
     }
-    constexpr int NV4 = F * CC * (KB / 4);
-    for (int e = tid; e < NV4; e += NT) {
-      const int q = e % (KB / 4);
-      const int cc = (e / (KB / 4)) % CC;
-      const int f = e / ((KB / 4) * CC);
-      const int c = c0 + cc;
-      const bool ok = c < g.C;
-      const float* src = ok ? V + ((int64_t)f * g.C + c) * g.K + k0 + 4 * q : V;
-      cp_async16(smem_u32(vs + f * Cfg::VPL + cc * KB + 4 * q), src, ok);
-    }
-    cp_async_commit();
+  }
+  if (tid == 0) {
+#pragma unroll
+    for (int st = 0; st < NS; ++st) mbar_init1((uint32_t)__cvta_generic_to_shared(&full[st]));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // thread 0 refills stage `st` with chunk `ch`
+  auto issue = [&](int ch, int st) {
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&full[st]);
+    const uint32_t dst = smem_u32(sm + st * SC::STAGE);
+    mbar_expect_tx(bar, (uint32_t)(SC::STAGE * 4));
+    bulk_g2s(dst, ublk + (int64_t)ch * SC::SU, (uint32_t)(SC::SU * 4), bar);
+    bulk_g2s(dst + SC::SU * 4, vblk + (int64_t)ch * SC::SV, (uint32_t)(SC::SV * 4), bar);
   };
+  // chunks [0, issued) are in flight or landed
+  int issued = nchunks < NS - 1 ? nchunks : NS - 1;
+  if (tid == 0) {
+    for (int st = 0; st < issued; ++st) issue(st, st);
+  }
 
   const int warp = tid >> 5, lane = tid & 31;
   const int lx = lane / (LT * LK);
   const int lt = (lane / LK) % LT;
   const int lk = lane % LK;
   const int f0 = (warp * LX + lx) * FPL;
-  float acc[FPL][MT][MK];
+  // acc[q][i][j2] holds output channels (2 j2, 2 j2 + 1) of tile i
+  unsigned long long acc[FPL][MT][MK / 2];
 #pragma unroll
   for (int q = 0; q < FPL; ++q)
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int j = 0; j < MK; ++j) acc[q][i][j] = 0.0f;
+      for (int j = 0; j < MK / 2; ++j) acc[q][i][j] = 0ull;
 
-  load_chunk(0, 0);
+  bool ok = true;
   for (int ch = 0; ch < nchunks; ++ch) {
-    const int buf = ch & 1;
-    if (ch + 1 < nchunks) {
-      load_chunk(ch + 1, buf ^ 1);
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    } else {
-      cp_async_wait_all();
+    const int st = ch % NS;
+    const bool got =
+        mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&full[st]), (uint32_t)((ch / NS) & 1));
+    // chunk ch landed for everyone (or someone gave up); every thread is done
+    // with chunk ch - 1, whose stage the refill below overwrites
+    ok = __syncthreads_and(got ? 1 : 0) != 0;
+    if (!ok) {
+      // drain the copies still in flight (bounded), then abandon the tile
+      if (tid == 0) {
+        atomicExch(err, 1);
+        for (int c2 = ch; c2 < issued; ++c2)
+          (void)mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&full[c2 % NS]),
+                                  (uint32_t)((c2 / NS) & 1));
+      }
+      return;
     }
-    __syncthreads();
-    const float* us = sm + buf * SC::STAGE;
-    const float* vbase = us + F * Cfg::UPL + lk * 4;
+    if (ch + NS - 1 < nchunks) {
+      if (tid == 0) {
+        // the stage's previous contents were read through the generic proxy
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        issue(ch + NS - 1, (ch + NS - 1) % NS);
+      }
+      ++issued;
+    }
+    const float* us = sm + st * SC::STAGE;
+    const float* vbase = us + SC::SU + lk * 4;
+    // operand fragments of step (cc, q); the next step's are loaded before
+    // this step's FMAs are issued
+    auto load_frag = [&](int cc, int q, float (&a)[MT], unsigned long long (&b2)[MK / 2]) {
+      const float* up = us + (f0 + q) * Cfg::UPL + cc * TB + lt * MT;
+      const float* vp = vbase + (f0 + q) * Cfg::VPL + cc * KB;
 #pragma unroll
-    for (int cc = 0; cc < CC; ++cc) {
+      for (int i = 0; i < MT; i += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(up + i);
+        a[i] = v.x;
+        a[i + 1] = v.y;
+        a[i + 2] = v.z;
+        a[i + 3] = v.w;
+      }
 #pragma unroll
-      for (int q = 0; q < FPL; ++q) {
-        const float* up = us + (f0 + q) * Cfg::UPL + cc * TB + lt * MT;
-        const float* vp = vbase + (f0 + q) * Cfg::VPL + cc * KB;
-        float a[MT], b[MK];
+      for (int s4 = 0; s4 < MK / 4; ++s4) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(vp + s4 * 4 * LK);
+        b2[2 * s4] = v.x;
+        b2[2 * s4 + 1] = v.y;
+      }
+    };
+    float a[2][MT];
+    unsigned long long b2[2][MK / 2];
+    load_frag(0, 0, a[0], b2[0]);
 #pragma unroll
-        for (int i = 0; i < MT; i += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(up + i);
-          a[i] = v.x;
-          a[i + 1] = v.y;
-          a[i + 2] = v.z;
-          a[i + 3] = v.w;
-        }
+    for (int step = 0; step < CC * FPL; ++step) {
+      const int cur = step & 1;
+      if (step + 1 < CC * FPL)
+        load_frag((step + 1) / FPL, (step + 1) % FPL, a[cur ^ 1], b2[cur ^ 1]);
+      const int q = step % FPL;
 #pragma unroll
-        for (int s4 = 0; s4 < MK / 4; ++s4) {
-          const float4 v = *reinterpret_cast<const float4*>(vp + s4 * 4 * LK);
-          b[4 * s4] = v.x;
-          b[4 * s4 + 1] = v.y;
-          b[4 * s4 + 2] = v.z;
-          b[4 * s4 + 3] = v.w;
-        }
+      for (int i = 0; i < MT; ++i) {
+        const unsigned long long ai = pack_dup(a[cur][i]);
 #pragma unroll
-        for (int i = 0; i < MT; ++i)
-#pragma unroll
-          for (int j = 0; j < MK; ++j) acc[q][i][j] = fmaf(a[i], b[j], acc[q][i][j]);
+        for (int j = 0; j < MK / 2; ++j) acc[q][i][j] = fma2(ai, b2[cur][j], acc[q][i][j]);
       }
     }
-    __syncthreads();
   }
+  __syncthreads();  // every thread done with the stages the epilogue reuses
 
-  // epilogue: accumulators to Es[f][k][t], then A^T M A per (t, k)
+  // epilogue: accumulators to Es[f][t][k], then A^T M A per (t, k)
   float* Es = sm;
   // Es[f][t][k] with rows of KB + 4 floats: the float4 stores of a warp
   // spread evenly over the banks, and the epilogue's reads (k fastest) are
@@ -542,113 +724,167 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
 #pragma unroll
       for (int s4 = 0; s4 < MK / 4; ++s4) {
         float* dst = Es + ((size_t)(f0 + q) * TB + lt * MT + i) * Cfg::EKB + s4 * 4 * LK + lk * 4;
-        *reinterpret_cast<float4*>(dst) =
-            make_float4(acc[q][i][4 * s4], acc[q][i][4 * s4 + 1], acc[q][i][4 * s4 + 2],
-                        acc[q][i][4 * s4 + 3]);
+        const float2 lo = unpack2(acc[q][i][2 * s4]), hi = unpack2(acc[q][i][2 * s4 + 1]);
+        *reinterpret_cast<float4*>(dst) = make_float4(lo.x, lo.y, hi.x, hi.y);
       }
   __syncthreads();
-  const int tpi = g.th * g.tw;
+  // A^T M A per (t, k), the same order as the fused kernel's epilogue; the
+  // pairs (j, j + 1) of Z = A^T M and (b, b + 1) of Y = Z A run as one
+  // fma.rn.f32x2 each (two IEEE fused multiply-adds, the same bits).
+  const int64_t plane = (int64_t)g.Ho * g.Wo;
   for (int p = tid; p < TB * KB; p += NT) {
     const int kl = p % KB, t = p / KB;
-    const int64_t tg = t0 + t;
+    const int rows = s_rows[t], cols = s_cols[t];
+    if (rows == 0) continue;
     const int k = k0 + kl;
-    if (tg >= g.T || k >= g.K) continue;
-    float Mv[F];
+    unsigned long long Mp[F / 2];  // (M[i][j], M[i][j + 1]), j even
 #pragma unroll
-    for (int q = 0; q < F; ++q) Mv[q] = Es[((size_t)q * TB + t) * Cfg::EKB + kl];
+    for (int q = 0; q < F; q += 2)
+      Mp[q / 2] = pack2(Es[((size_t)q * TB + t) * Cfg::EKB + kl],
+                        Es[((size_t)(q + 1) * TB + t) * Cfg::EKB + kl]);
     float Z[MM * A];
 #pragma unroll
     for (int a = 0; a < MM; ++a)
 #pragma unroll
-      for (int j = 0; j < A; ++j) {
-        float z = 0.0f;
+      for (int j = 0; j < A; j += 2) {
+        unsigned long long z = 0ull;
 #pragma unroll
-        for (int i = 0; i < A; ++i) z = fmaf(Mx.AT[a * A + i], Mv[i * A + j], z);
-        Z[a * A + j] = z;
+        for (int i = 0; i < A; ++i) z = fma2(pack_dup(Mx.AT[a * A + i]), Mp[(i * A + j) / 2], z);
+        const float2 zz = unpack2(z);
+        Z[a * A + j] = zz.x;
+        Z[a * A + j + 1] = zz.y;
       }
-    const int n = (int)(tg / tpi);
-    const int rem = (int)(tg - (int64_t)n * tpi);
-    const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
-    float* yk = y + ((int64_t)n * g.K + k) * g.Ho * g.Wo;
+    float* yt = y + s_ybase[t] + (int64_t)k * plane;
 #pragma unroll
     for (int a = 0; a < MM; ++a) {
-      const int pr = ti * MM + a;
       float yr[MM];
 #pragma unroll
-      for (int b = 0; b < MM; ++b) {
-        float v = 0.0f;
+      for (int b = 0; b < MM; b += 2) {
+        unsigned long long v = 0ull;
 #pragma unroll
-        for (int j = 0; j < A; ++j) v = fmaf(Z[a * A + j], Mx.AT[b * A + j], v);
-        yr[b] = v;
+        for (int j = 0; j < A; ++j)
+          v = fma2(pack_dup(Z[a * A + j]), pack2(Mx.AT[b * A + j], Mx.AT[(b + 1) * A + j]), v);
+        const float2 vv = unpack2(v);
+        yr[b] = vv.x;
+        yr[b + 1] = vv.y;
       }
-      if (pr >= g.Ho) continue;
-      float* yrow = yk + (int64_t)pr * g.Wo + tj * MM;
+      if (a >= rows) continue;
+      float* yrow = yt + (int64_t)a * g.Wo;
 #pragma unroll
       for (int b = 0; b < MM; ++b)
-        if (tj * MM + b < g.Wo) yrow[b] = yr[b];
+        if (b < cols) yrow[b] = yr[b];
     }
   }
 }
 
-template <FUSED_TPARAMS>
-static int launch_split(const float* x, const float* V, float* U, float* y, const LayerGeom& g,
-                        const LayerMats& M, cudaStream_t st) {
+// Blocked workspace of a tile shape: Vb, then Ub (256-byte aligned).
+static size_t split_ws_bytes(const SplitGeom& sg) {
+  const size_t v = ((size_t)sg.vb_floats() * 4 + 255) & ~(size_t)255;
+  return v + (size_t)sg.ub_floats() * 4 + 256;
+}
+
+template <SPLIT_TPARAMS>
+static size_t split_ws_for(const LayerGeom& g) {
   using Cfg = FusedCfg<FUSED_TARGS>;
-  using SC = SplitCfg<FUSED_TARGS>;
+  if (g.K % Cfg::KB != 0) return 0;
+  return split_ws_bytes(split_geom(g, Cfg::TB, Cfg::KB, CC));
+}
+
+template <SPLIT_TPARAMS>
+static int launch_split(const float* x, const float* w, float* y, const LayerGeom& g,
+                        const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st) {
+  using Cfg = FusedCfg<FUSED_TARGS>;
+  using SC = SplitCfg<SPLIT_TARGS>;
   if (g.K % Cfg::KB != 0) return kFallback;
-  const int64_t Tp = (g.T + 3) & ~(int64_t)3;
+  const SplitGeom sg = split_geom(g, Cfg::TB, Cfg::KB, CC);
+  if (ws_bytes < split_ws_bytes(sg)) return kFallback;
+  float* Vb = (float*)ws;
+  float* Ub = (float*)((char*)ws + (((size_t)sg.vb_floats() * 4 + 255) & ~(size_t)255));
+  int* err = nullptr;
+  {
+    int rc = wait_error_flag(&err);
+    if (rc != WINO_OK) return rc;
+  }
   static bool attr_set[16] = {false};
   int dev = 0;
   WINO_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 16 && !attr_set[dev]) {
-    WINO_CUDA_TRY(cudaFuncSetAttribute(k_gemm_otx<FUSED_TARGS>,
+    WINO_CUDA_TRY(cudaFuncSetAttribute(k_gemm_otx<SPLIT_TARGS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SC::SMEM));
     attr_set[dev] = true;
   }
-  const int64_t nblk = (int64_t)(g.K / Cfg::KB) * ((g.T + Cfg::TB - 1) / Cfg::TB);
-  const int64_t nin = (int64_t)g.C * Tp;
-  if (nblk > 0x7fffffffLL || (nin + 255) / 256 > 0x7fffffffLL) return kFallback;
+  const int64_t nblk = (int64_t)sg.nkb * sg.ntb;
+  const int64_t nfl = (int64_t)sg.nch * CC * g.K;
+  static_assert(CC * Cfg::TB <= 256, "one input-transform thread per (channel, tile) of a chunk");
+  if (nblk > 0x7fffffffLL || sg.nch > 65535 || (nfl + 255) / 256 > 0x7fffffffLL) return kFallback;
+  {
+    ProfScope ps(kKFilter, st);
+    k_filter_transform_blk<<<(unsigned)((nfl + 255) / 256), 256, 0, st>>>(w, Vb, g.C, g.K, M, sg);
+  }
   {
     ProfScope ps(kKInput, st);
-    k_input_transform_r3<MM><<<(unsigned)((nin + 255) / 256), 256, 0, st>>>(x, U, g, M, Tp);
+    const size_t csm = (size_t)Cfg::F * sg.UPL * sizeof(float);
+    k_input_transform_blk<MM><<<dim3((unsigned)sg.ntb, (unsigned)sg.nch), CC * Cfg::TB, csm, st>>>(
+        x, Ub, g, M, sg);
   }
   {
     ProfScope ps(kKFused, st);
-    k_gemm_otx<FUSED_TARGS><<<(unsigned)nblk, Cfg::NT, SC::SMEM, st>>>(U, V, y, g, M, Tp);
+    k_gemm_otx<SPLIT_TARGS><<<(unsigned)nblk, Cfg::NT, SC::SMEM, st>>>(Ub, Vb, y, g, M, sg, err);
   }
-  note_launches(2);
+  note_launches(3);
   WINO_CUDA_TRY(cudaGetLastError());
   return WINO_OK;
 }
 
+// Tile shapes of the split variant per m, as
+// (MM, LX, LT, LK, FPL, MT, MK, CC, NS) -> TB = LT MT tiles x KB = LK MK
+// output channels per CTA, CC channels per chunk, NS stages.  The layer
+// autotuner times each.
+#define SPLIT_M2_0 2, 2, 4, 4, 1, 8, 16, 8, 2
+#define SPLIT_M4_0 4, 1, 4, 8, 3, 4, 8, 8, 2
+#define SPLIT_M4_1 4, 1, 8, 4, 3, 4, 8, 8, 2
+#define SPLIT_M4_2 4, 1, 8, 4, 3, 4, 8, 4, 4
+#define SPLIT_M6_0 6, 8, 1, 4, 1, 8, 16, 4, 2
+#define SPLIT_M6_1 6, 8, 2, 2, 1, 8, 16, 4, 3
+#define SPLIT_M6_2 6, 8, 2, 2, 1, 8, 16, 2, 4
+
+int split_configs(int m) { return m == 2 ? 1 : 3; }
+
 size_t split_workspace_bytes(const LayerGeom& g) {
-  const int64_t Tp = (g.T + 3) & ~(int64_t)3;
-  return (size_t)g.F * g.C * g.K * sizeof(float) + (size_t)g.F * g.C * Tp * sizeof(float) + 256;
+  size_t b = 0;
+  auto mx = [&](size_t v) { b = v > b ? v : b; };
+  if (g.F == 16) mx(split_ws_for<SPLIT_M2_0>(g));
+  if (g.F == 36) {
+    mx(split_ws_for<SPLIT_M4_0>(g));
+    mx(split_ws_for<SPLIT_M4_1>(g));
+    mx(split_ws_for<SPLIT_M4_2>(g));
+  }
+  if (g.F == 64) {
+    mx(split_ws_for<SPLIT_M6_0>(g));
+    mx(split_ws_for<SPLIT_M6_1>(g));
+    mx(split_ws_for<SPLIT_M6_2>(g));
+  }
+  return b;
 }
 
-// Two-kernel variant (needs V and U in the workspace).
+// Two-kernel variant (blocked U and V in the workspace); `cfg` picks the
+// tile shape (0 .. split_configs(m) - 1).
 int layer_forward_split(const float* x, const float* w, float* y, const LayerGeom& g,
-                        const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (g.dim != 2 || M.r != 3 || (M.m != 2 && M.m != 4 && M.m != 6) || g.K % 64 != 0)
+                        const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st,
+                        int cfg) {
+  if (g.dim != 2 || M.r != 3 || (M.m != 2 && M.m != 4 && M.m != 6) || g.K % 32 != 0)
     return kFallback;
-  if (ws_bytes < split_workspace_bytes(g)) return kFallback;
-  float* V = (float*)ws;
-  float* U = V + (((size_t)g.F * g.C * g.K + 63) & ~(size_t)63);
-  {
-    const int64_t n = (int64_t)g.C * g.K;
-    ProfScope ps(kKFilter, st);
-    k_filter_transform<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, V, g.dim, g.C, g.K, M);
-    note_launches(1);
+  if (cfg < 0 || cfg >= split_configs(M.m)) return kFallback;
+  if (M.m == 2) return launch_split<SPLIT_M2_0>(x, w, y, g, M, ws, ws_bytes, st);
+  if (M.m == 4) {
+    if (cfg == 0) return launch_split<SPLIT_M4_0>(x, w, y, g, M, ws, ws_bytes, st);
+    if (cfg == 1) return launch_split<SPLIT_M4_1>(x, w, y, g, M, ws, ws_bytes, st);
+    return launch_split<SPLIT_M4_2>(x, w, y, g, M, ws, ws_bytes, st);
   }
-  switch (M.m) {
-    case 2:
-      return launch_split<2, 2, 4, 4, 1, 8, 16, 8>(x, V, U, y, g, M, st);
-    case 4:
-      return launch_split<4, 1, 4, 8, 3, 4, 8, 8>(x, V, U, y, g, M, st);
-    default:
-      return launch_split<6, 8, 1, 4, 1, 8, 16, 4>(x, V, U, y, g, M, st);
-  }
+  if (cfg == 0) return launch_split<SPLIT_M6_0>(x, w, y, g, M, ws, ws_bytes, st);
+  if (cfg == 1) return launch_split<SPLIT_M6_1>(x, w, y, g, M, ws, ws_bytes, st);
+  return launch_split<SPLIT_M6_2>(x, w, y, g, M, ws, ws_bytes, st);
 }
 
 }  // namespace wino

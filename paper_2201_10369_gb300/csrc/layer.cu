@@ -36,34 +36,11 @@ __global__ void k_filter_transform(const float* __restrict__ w, float* __restric
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)C * K) return;
   const int k = (int)(idx % K), c = (int)(idx / K);
-  const int A = M.alpha, r = M.r;
-  const int taps = (dim == 1) ? r : r * r;
-  const float* g = w + ((int64_t)k * C + c) * taps;
-  float gl[kMaxR * kMaxR];
-  for (int i = 0; i < taps; ++i) gl[i] = g[i];
+  const int taps = (dim == 1) ? M.r : M.r * M.r;
   const int64_t plane = (int64_t)C * K;
   float* out = V + (int64_t)c * K + k;
-  if (dim == 1) {
-    for (int i = 0; i < A; ++i) {
-      float acc = 0.0f;
-      for (int q = 0; q < r; ++q) acc = fmaf(M.G[i * r + q], gl[q], acc);
-      out[i * plane] = acc;
-    }
-    return;
-  }
-  float Wk[kMaxAlpha * kMaxR];
-  for (int i = 0; i < A; ++i)
-    for (int q = 0; q < r; ++q) {
-      float acc = 0.0f;
-      for (int l = 0; l < r; ++l) acc = fmaf(M.G[i * r + l], gl[l * r + q], acc);
-      Wk[i * r + q] = acc;
-    }
-  for (int i = 0; i < A; ++i)
-    for (int j = 0; j < A; ++j) {
-      float acc = 0.0f;
-      for (int q = 0; q < r; ++q) acc = fmaf(Wk[i * r + q], M.G[j * r + q], acc);
-      out[(int64_t)(i * A + j) * plane] = acc;
-    }
+  filter_transform_one(w + ((int64_t)k * C + c) * taps, dim, M,
+                       [&](int f, float v) { out[(int64_t)f * plane] = v; });
 }
 
 // ---------------------------------------------------------------------------
@@ -266,6 +243,8 @@ int layer_forward_fused(const float* x, const float* w, float* y, const LayerGeo
 size_t fused_workspace_bytes(const LayerGeom& g);
 size_t tc_workspace_bytes(const LayerGeom& g, int dtype);
 
+size_t split_workspace_bytes(const LayerGeom& g);
+
 size_t layer_workspace_bytes(const LayerGeom& g, int dtype) {
   const size_t F = (size_t)g.F;
   const size_t v = F * g.C * g.K * sizeof(float);
@@ -273,7 +252,8 @@ size_t layer_workspace_bytes(const LayerGeom& g, int dtype) {
   const size_t mm = F * g.K * (size_t)g.T * sizeof(float);
   size_t general = v + u + mm + 1024;
   if (dtype != 0) return tc_workspace_bytes(g, dtype);
-  return general;
+  const size_t split = split_workspace_bytes(g);
+  return split > general ? split : general;
 }
 
 int layer_forward_general_f32(const float* x, const float* w, float* y, const LayerGeom& g,
@@ -313,20 +293,28 @@ int layer_forward_general_f32(const float* x, const float* w, float* y, const La
 }
 
 int layer_forward_split(const float* x, const float* w, float* y, const LayerGeom& g,
-                        const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st);
+                        const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st, int cfg);
+int split_configs(int m);
 
 // ---------------------------------------------------------------------------
 // Variant choice for the FP32 layer (autotuner): the fully fused kernel
-// (fused.cu), the split transform + GEMM/output kernels (fused.cu) and the
-// general pipeline above compute the same bits; which is fastest depends
-// on the shape.  The first call for a shape times the fused and split
-// variants on the caller's stream (twice each, keeping the second) and
-// caches the faster one for the process.  Timing synchronises the stream,
-// so it is skipped while the stream is being captured into a graph (the
-// split variant is used then) and when WINO_AUTOTUNE=0.
-// WINO_LAYER_VARIANT=fused|split|general forces a variant.
+// (fused.cu), the split transform + GEMM/output kernels (fused.cu) in each
+// of its tile shapes, and the general pipeline above compute the same bits;
+// which is fastest depends on the shape.  The first call for a shape times
+// the fused variant and every split tile shape on the caller's stream
+// (twice each, keeping the second) and caches the fastest for the process.
+// Timing synchronises the stream, so it is skipped while the stream is being
+// captured into a graph (split tile shape 0 is used then) and when
+// WINO_AUTOTUNE=0.  WINO_LAYER_VARIANT=fused|split|split1|split2|general
+// forces a variant.
 // ---------------------------------------------------------------------------
-enum LayerVariant { kVarUnknown = 0, kVarFused = 1, kVarSplit = 2, kVarGeneral = 3 };
+enum LayerVariant {
+  kVarUnknown = 0,
+  kVarFused = 1,
+  kVarSplit = 2,  // split tile shape 0
+  kVarGeneral = 3,
+  kVarSplitN = 16  // kVarSplitN + c: split tile shape c >= 1
+};
 
 static std::mutex g_var_mu;
 static std::map<std::string, int> g_var_cache;
@@ -343,6 +331,8 @@ static int forced_variant() {
   if (!v) return kVarUnknown;
   if (!strcmp(v, "fused")) return kVarFused;
   if (!strcmp(v, "split")) return kVarSplit;
+  if (!strcmp(v, "split1")) return kVarSplitN + 1;
+  if (!strcmp(v, "split2")) return kVarSplitN + 2;
   if (!strcmp(v, "general")) return kVarGeneral;
   return kVarUnknown;
 }
@@ -350,7 +340,9 @@ static int forced_variant() {
 static int run_variant(int var, const float* x, const float* w, float* y, const LayerGeom& g,
                        const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (var == kVarFused) return layer_forward_fused(x, w, y, g, M, ws, ws_bytes, st);
-  if (var == kVarSplit) return layer_forward_split(x, w, y, g, M, ws, ws_bytes, st);
+  if (var == kVarSplit) return layer_forward_split(x, w, y, g, M, ws, ws_bytes, st, 0);
+  if (var > kVarSplitN)
+    return layer_forward_split(x, w, y, g, M, ws, ws_bytes, st, var - kVarSplitN);
   return layer_forward_general_f32(x, w, y, g, M, ws, st);
 }
 
@@ -362,8 +354,12 @@ static int tune_variant(const float* x, const float* w, float* y, const LayerGeo
   WINO_CUDA_TRY(cudaEventCreate(&b));
   float best = 1e30f;
   int best_var = kVarGeneral;
-  const int cands[2] = {kVarSplit, kVarFused};
-  for (int var : cands) {
+  int cands[8], nc = 0;
+  cands[nc++] = kVarSplit;
+  for (int c = 1; c < split_configs(M.m) && nc < 7; ++c) cands[nc++] = kVarSplitN + c;
+  cands[nc++] = kVarFused;
+  for (int ci = 0; ci < nc; ++ci) {
+    const int var = cands[ci];
     float ms = 1e30f;
     bool ok = true;
     for (int rep = 0; rep < 2 && ok; ++rep) {
@@ -418,7 +414,7 @@ int layer_forward_f32(const float* x, const float* w, float* y, const LayerGeom&
   }
   int rc = run_variant(var, x, w, y, g, M, ws, ws_bytes, st);
   if (rc == kFallback && var != kVarGeneral) {
-    rc = layer_forward_split(x, w, y, g, M, ws, ws_bytes, st);
+    rc = layer_forward_split(x, w, y, g, M, ws, ws_bytes, st, 0);
     if (rc == kFallback) rc = layer_forward_fused(x, w, y, g, M, ws, ws_bytes, st);
   }
   if (rc == kFallback) rc = layer_forward_general_f32(x, w, y, g, M, ws, st);

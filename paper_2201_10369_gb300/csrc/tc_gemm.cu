@@ -357,7 +357,7 @@ struct TcGemmArgs {
   const uint16_t* V[3];  // [F][K][Cp]
   const float* sV;
   float* M;  // [F][K][T]
-  int* err;  // set to 1 when a bounded wait gives up
+  int* err;  // the device's wait-error flag: set to 1 when a bounded wait gives up
   TcScales S;
   int64_t T, Tp;
   int K, Cp, NB, ncols, mode;
@@ -517,7 +517,7 @@ static size_t tc_smem_bytes(int NB, int parts) {
 
 // Workspace layout of the precision form (bytes), all 1024-aligned.
 struct TcLayout {
-  size_t V32, vmax, sV, err, V[3], U[3], M, total;
+  size_t V32, vmax, sV, V[3], U[3], M, total;
 };
 
 static TcLayout tc_layout(const LayerGeom& g, int dtype) {
@@ -533,8 +533,6 @@ static TcLayout tc_layout(const LayerGeom& g, int dtype) {
   o = al(o + (size_t)g.F * 4);
   L.sV = o;
   o = al(o + (size_t)g.F * 4);
-  L.err = o;
-  o = al(o + 64);
   for (int pp = 0; pp < 3; ++pp) {
     L.V[pp] = o;
     o = al(o + (pp < parts ? (size_t)g.F * g.K * Cp * 2 : 0));
@@ -580,7 +578,11 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
   float* V32 = (float*)(b + L.V32);
   unsigned* vmax = (unsigned*)(b + L.vmax);
   float* sV = (float*)(b + L.sV);
-  int* err = (int*)(b + L.err);
+  int* err = nullptr;
+  {
+    int rc = wait_error_flag(&err);
+    if (rc != WINO_OK) return rc;
+  }
   uint16_t *Vp[3], *Up[3];
   for (int pp = 0; pp < 3; ++pp) {
     Vp[pp] = (uint16_t*)(b + L.V[pp]);
@@ -608,7 +610,6 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     }
   }
   WINO_CUDA_TRY(cudaMemsetAsync(vmax, 0, (size_t)g.F * 4, st));
-  WINO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));
   {
     ProfScope ps(kKTcTransform, st);
     const int64_t n = (int64_t)g.C * g.K;
@@ -689,16 +690,6 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     note_launches(1);
   }
   WINO_CUDA_TRY(cudaGetLastError());
-  return WINO_OK;
-}
-
-// Reads (and clears) the error flag of the last precision-form layer run in
-// workspace `ws`: 1 when a bounded wait on the tensor cores gave up.
-int tc_error_flag(void* ws, const LayerGeom& g, int dtype, cudaStream_t st, int* flag) {
-  const TcLayout L = tc_layout(g, dtype);
-  int* err = (int*)((char*)ws + L.err);
-  WINO_CUDA_TRY(cudaMemcpyAsync(flag, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  WINO_CUDA_TRY(cudaStreamSynchronize(st));
   return WINO_OK;
 }
 
