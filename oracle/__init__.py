@@ -82,6 +82,9 @@ def lib():
             L.orc_error_sweep.restype = ctypes.c_int
             L.orc_direct_error.argtypes = [ctypes.c_int] * 4 + [ctypes.c_uint64]
             L.orc_direct_error.restype = ctypes.c_double
+            L.orc_pointset_error.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_int, ctypes.c_int,
+                                                                  ctypes.c_uint64, dp]
+            L.orc_pointset_error.restype = ctypes.c_int
             L.orc_round_bf16.argtypes = [ctypes.c_float]
             L.orc_round_bf16.restype = ctypes.c_float
             L.orc_round_fp16.argtypes = [ctypes.c_float]
@@ -244,6 +247,17 @@ def error_sweep(c_grid, sizes, masks, trials: int, seed: int, c_stride: int = 1,
 
 def direct_error(dim: int, m: int, r: int, trials: int, seed: int) -> float:
     return float(lib().orc_direct_error(dim, m, r, trials, seed))
+
+
+def pointset_error(dim: int, m: int, r: int, point_sets, trials: int, seed: int):
+    """The sweep metric of explicit point sets (each m + r - 1 values with one
+    +inf, any order) on the sweep's trials of size (dim, m, r)."""
+    pts = np.ascontiguousarray(point_sets, dtype=np.float64)
+    assert pts.ndim == 2 and pts.shape[1] == m + r - 1
+    err = np.full(pts.shape[0], np.nan)
+    rc = lib().orc_pointset_error(dim, m, r, _dp(pts), pts.shape[0], trials, seed, _dp(err))
+    assert rc == 0
+    return err
 
 
 def round_bf16(v: float) -> float:

@@ -679,6 +679,20 @@ int orc_error_sweep(const double* c_grid, int n_c, const orc_size* sizes,
   return rc;
 }
 
+int orc_pointset_error(int dim, int m, int r, const double* points, int n_sets, int trials,
+                       uint64_t seed, double* err_out) {
+  const int A = m + r - 1;
+  if (dim < 1 || dim > 2 || A < 2 || A > ORC_MAX_ALPHA || n_sets < 0 || trials < 1) return -1;
+  orc_size s = {dim, m, r, 1.0};
+  size_data sd;
+  memset(&sd, 0, sizeof(sd));
+  int rc = build_size_data(&s, trials, seed, &sd);
+  for (int q = 0; q < n_sets && rc == 0; ++q)
+    err_out[q] = eval_instance(&s, &sd, points + (size_t)q * A, trials);
+  free(sd.g); free(sd.d); free(sd.y);
+  return rc;
+}
+
 double orc_direct_error(int dim, int m, int r, int trials, uint64_t seed) {
   orc_size s = {dim, m, r, 1.0};
   size_data sd;

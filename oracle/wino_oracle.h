@@ -103,6 +103,14 @@ int orc_error_sweep(const double* c_grid, int n_c, const orc_size* sizes,
                     int trials, uint64_t seed, double* err_out,
                     int c_stride, int n_threads);
 
+/* The same metric for explicit point sets (the comparison sets of Tables
+ * 7-8, Chebyshev nodes): err_out[q] for points[q * alpha .. + alpha)
+ * (alpha = m + r - 1 values, one +INFINITY, any order), on the trials the
+ * sweep draws for size (dim, m, r).  +INF for coinciding points, NaN for an
+ * invalid set.  Returns 0, -1 on bad arguments.                           */
+int orc_pointset_error(int dim, int m, int r, const double* points, int n_sets, int trials,
+                       uint64_t seed, double* err_out);
+
 /* The same metric for FP32 direct correlation (the "n = 0" row).         */
 double orc_direct_error(int dim, int m, int r, int trials, uint64_t seed);
 

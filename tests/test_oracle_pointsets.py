@@ -1,0 +1,78 @@
+"""Oracle pins for explicit point sets: the comparison sets of Barabasz et al.
+against the errors Tables 7-8 print for them, the Chebyshev nodes of Sec. 2
+against their closed form, and the point-set metric against the mask sweep
+where a set has both forms."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from test_oracle_sweep import _mean_abs_y
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_pointsets.txt")
+
+
+def _rows():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = [s.strip() for s in line.split("|")]
+            pts = [float(Fraction(v)) for v in p[3].split(",")] + [math.inf]
+            rows.append(dict(label=p[0], dim=int(p[1]), m=int(p[2]), points=pts,
+                             paper=float(p[4]), cite=p[5]))
+    return rows
+
+
+def chebyshev_points(n):
+    """Sec. 2: x_k = cos((2k - 1) pi / (2 n)), k = 1..n, as the n finite points
+    (reading: with infinity the set has n + 1 points)."""
+    k = np.arange(1, n + 1)
+    return list(np.cos((2 * k - 1) / (2 * n) * np.pi))
+
+
+@pytest.mark.parametrize("row", _rows(), ids=lambda r: r["label"])
+def test_barabasz_sets_match_printed_errors(orc, row):
+    """Our error for the paper's comparison sets, in the per-element absolute
+    reading, within [0.75, 1.05] of the printed value (Huffman order there)."""
+    trials, seed = 5000, 0
+    rel = orc.pointset_error(row["dim"], row["m"], 3, [row["points"]], trials, seed)[0]
+    ours = rel * _mean_abs_y(orc, row["dim"], row["m"], trials, seed)
+    assert 0.75 <= ours / row["paper"] <= 1.05, (row["cite"], ours, row["paper"])
+
+
+def test_chebyshev_closed_form():
+    assert np.allclose(chebyshev_points(1), [0.0], atol=1e-15)
+    assert np.allclose(chebyshev_points(3), [math.sqrt(3) / 2, 0.0, -math.sqrt(3) / 2], atol=1e-15)
+    p = chebyshev_points(7)
+    assert np.allclose(p, -np.array(p[::-1]), atol=1e-15)  # symmetric about 0
+    assert all(-1 < v < 1 for v in p)
+
+
+def test_chebyshev_worse_for_larger_sets(orc):
+    """Table 9: for n >= 6 points the Chebyshev nodes give a larger error than
+    the Barabasz sets (every column); the synthetic sweep agrees in 1D and 2D."""
+    rows = {(r["dim"], r["m"]): r for r in _rows()}
+    for dim in (1, 2):
+        for m in (4, 6, 8):
+            ch = chebyshev_points(m + 1) + [math.inf]
+            e = orc.pointset_error(dim, m, 3, [rows[(dim, m)]["points"], ch], 1000, 0)
+            assert e[1] > e[0], (dim, m, e)
+
+
+def test_pointset_equals_mask_sweep(orc):
+    """P8 is the full c-group with c = 2, d = 1 (mask 0x6f): the point-set
+    metric and the mask sweep evaluate the same matrices on the same trials."""
+    p8 = [0, -1, 1, 0.5, -0.5, 2, -2, math.inf]
+    for dim in (1, 2):
+        a = orc.pointset_error(dim, 6, 3, [p8], 300, 4)[0]
+        b = orc.error_sweep([2.0], [(dim, 6, 3, 1.0)], [0x6F], 300, 4)[0, 0, 0]
+        assert a == b
+
+
+def test_pointset_degenerate(orc):
+    e = orc.pointset_error(1, 2, 3, [[0, 1, 1, math.inf], [0, 1, -1, 2.0]], 50, 0)
+    assert math.isinf(e[0]) and math.isnan(e[1])
