@@ -403,6 +403,7 @@ def run_ours(args, rank, world, local_rank):
             if r:
                 roofs[k] = r
     dom = max(roofs, key=lambda k: prof[k][0])
+    comparison = paper_comparison(wino, inputs, ex, cg, masks, sizes)
     plan_info = plan.info()
     plan.close()
     guided.close()
@@ -457,6 +458,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk,
+        "paper_comparison": comparison,
     }
     if world == 1 and not args.no_cpu_baseline:
         v, dt, nth = oracle_layer_sample(layers)
@@ -469,6 +471,33 @@ def run_ours(args, rank, world, local_rank):
                       "sample": "every 4th c of the 4096-value grid, all sizes and subsets, "
                                 "1000 trials (%d instances, %.1f s)" % (sw_n, sw_dt)}}
     print(json.dumps(line), flush=True)
+
+
+def paper_comparison(wino, inputs, ex, cg, masks, sizes):
+    """Tables 7-8 from this run (untimed): per size, the relative error of
+    Barabasz's set, of the paper's proposed set and of the best set the
+    exhaustive sweep found (same trials), and the improvements over
+    Barabasz's set beside the paper's."""
+    out = {}
+    for s, (dim, m, r, d) in enumerate(sizes):
+        n = m + 2
+        key = (dim, n)
+        if key not in inputs.COMPARISON_SETS:
+            continue
+        inf = math.inf
+        pn, prop = wino.wino_pointset_error((dim, m, r), [inputs.COMPARISON_SETS[key] + [inf],
+                                                          inputs.PROPOSED_SETS[key] + [inf]],
+                                            inputs.SWEEP_TRIALS, seed=0)
+        e = np.where(np.isfinite(ex[s]), ex[s], np.nan)
+        q, k = np.unravel_index(np.nanargmin(e), e.shape)
+        best = float(e[q, k])
+        out["%dd_n%d" % (dim, n)] = {
+            "barabasz": float(pn), "paper_set": float(prop), "sweep_best": best,
+            "sweep_best_mask": "%#04x" % int(masks[q]), "sweep_best_c": float(cg[k]),
+            "d": d, "improvement_pct_paper_set": 100.0 * (pn - prop) / pn,
+            "improvement_pct_sweep_best": 100.0 * (pn - best) / pn,
+            "improvement_pct_printed": inputs.PAPER_IMPROVEMENT_PCT[key]}
+    return out
 
 
 def fp32_peak_tflops():

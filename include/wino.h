@@ -172,6 +172,20 @@ int wino_error_sweep(const double* c_grid, int n_c,
                      int trials, unsigned long long seed,
                      double* err_out, void* cuda_stream);
 
+/* The sweep's metric for explicit point sets (the comparison sets of
+ * Tables 7-8, Chebyshev nodes): for each set q, points[q * alpha ..
+ * + alpha) (alpha = m + r - 1 values holding one +INFINITY, any order;
+ * sorted like wino_make_matrices), err_out[q] = the error of wino_error_sweep
+ * on the same trials of size (dim, m, r), in the same summation order (a set
+ * that is also a mask instance gets the same bits).  +INFINITY when two
+ * points coincide.  Sizes as compiled for the sweep (1D r = 3 m = 2..8, 1D
+ * r = 5 m = 2..6, 2D r = 3 m = 2..6), else WINO_EUNSUPPORTED; WINO_EINVAL
+ * for a set without exactly one +INFINITY.  points, err_out: host arrays.
+ * Synchronises `cuda_stream`.                                              */
+int wino_pointset_error(int dim, int m, int r, const double* points, int n_sets,
+                        int trials, unsigned long long seed, double* err_out,
+                        void* cuda_stream);
+
 /* The FP64 transform matrices the sweep builds on the device for the
  * instances (size, mask, c_k), k < n_c -- the same construction as
  * wino_make_matrices (Sec. 4.1-4.2), run by the sweep's own device code.

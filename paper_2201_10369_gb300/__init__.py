@@ -109,6 +109,8 @@ def _declare(L):
     L.wino_kernel_launches.argtypes = []
     L.wino_last_error.restype = ctypes.c_char_p
     L.wino_device_ok.restype = _i
+    L.wino_pointset_error.argtypes = [_i, _i, _i, _DP, _i, _i, ctypes.c_ulonglong, _DP, _vp]
+    L.wino_pointset_error.restype = _i
     L.wino_wait_error.argtypes = [ctypes.POINTER(ctypes.c_int)]
     L.wino_wait_error.restype = _i
     L.wino_shutdown.restype = None
@@ -654,6 +656,19 @@ def guided_sweep(model, sizes, masks, c_grid, trials: int, seed: int = 0, top: i
         return gs.run()
     finally:
         gs.close()
+
+
+def wino_pointset_error(size, point_sets, trials: int, seed: int = 0, stream=None) -> np.ndarray:
+    """The sweep metric of explicit point sets on the sweep's trials of size
+    (dim, m, r[, d]): each set m + r - 1 values with one +inf, any order."""
+    dim, m, r = size[0], size[1], size[2]
+    pts = np.ascontiguousarray(point_sets, dtype=np.float64)
+    if pts.ndim != 2 or pts.shape[1] != m + r - 1:
+        raise ValueError("each point set needs m + r - 1 values")
+    err = np.empty(pts.shape[0])
+    _check(load().wino_pointset_error(dim, m, r, pts.ctypes.data_as(_DP), pts.shape[0], trials,
+                                      seed, err.ctypes.data_as(_DP), _stream(stream)))
+    return err
 
 
 def grid_instances(sizes, masks, c_grid):

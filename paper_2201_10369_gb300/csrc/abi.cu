@@ -9,6 +9,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/wino.h"
 #include "common.cuh"
@@ -122,7 +123,8 @@ static int check_device() {
 }
 
 // Validates a point set (alpha values, exactly one +inf) and writes the
-// sorted finite points.  Returns WINO_OK / WINO_EINVAL.
+// alpha - 1 sorted finite points to fin (never more).  Returns WINO_OK /
+// WINO_EINVAL.
 static int canonical_points(const double* points, int alpha, double* fin) {
   if (!points) {
     set_error("points is NULL");
@@ -138,6 +140,10 @@ static int canonical_points(const double* points, int alpha, double* fin) {
     if (isinf(p)) {
       ++n_inf;
     } else {
+      if (nf == alpha - 1) {
+        set_error("exactly one point must be +INFINITY");
+        return WINO_EINVAL;
+      }
       fin[nf++] = p;
     }
   }
@@ -351,6 +357,27 @@ int wino_error_sweep(const double* c_grid, int n_c, const wino_size* sizes, int 
   if (st != WINO_OK) return st;
   return error_sweep(c_grid, n_c, reinterpret_cast<const SweepSize*>(sizes), n_sizes, subsets,
                      n_subsets, trials, seed, err_out, (cudaStream_t)cuda_stream);
+}
+
+int wino_pointset_error(int dim, int m, int r, const double* points, int n_sets, int trials,
+                        unsigned long long seed, double* err_out, void* cuda_stream) {
+  const int alpha = m + r - 1;
+  if (!points || !err_out || n_sets < 1 || trials < 1 || trials > (1 << 20) ||
+      (dim != 1 && dim != 2) || m < 1 || r < 1 || alpha < 3 || alpha > 10) {
+    set_error("invalid point-set sweep arguments");
+    return WINO_EINVAL;
+  }
+  std::vector<double> sorted((size_t)n_sets * (alpha - 1));
+  for (int q = 0; q < n_sets; ++q) {
+    double fin[kMaxAlpha];
+    int st = canonical_points(points + (size_t)q * alpha, alpha, fin);
+    if (st != WINO_OK) return st;
+    for (int i = 0; i < alpha - 1; ++i) sorted[(size_t)q * (alpha - 1) + i] = fin[i];
+  }
+  int st = check_device();
+  if (st != WINO_OK) return st;
+  return pointset_error(dim, m, r, sorted.data(), n_sets, trials, seed, err_out,
+                        (cudaStream_t)cuda_stream);
 }
 
 int wino_instance_matrices(const double* c_grid, int n_c, wino_size size, unsigned mask,

@@ -327,6 +327,78 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   return WINO_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Explicit point sets (the comparison sets of Tables 7-8, Chebyshev nodes):
+// one lane per set, the sweep's trials and summation order.
+// ---------------------------------------------------------------------------
+template <int DIM, int M, int R>
+__global__ void __launch_bounds__(128) k_pointset_eval(const float* __restrict__ rec, int trials,
+                                                       const double* __restrict__ pts, int n_sets,
+                                                       const double* __restrict__ ysum,
+                                                       double* __restrict__ err) {
+  constexpr int A = M + R - 1;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = s < n_sets;
+  const int ss = active ? s : 0;
+  double a[A - 1];
+#pragma unroll
+  for (int i = 0; i < A - 1; ++i) a[i] = pts[(int64_t)ss * (A - 1) + i];
+  Mats<M, R> Mx;
+  const bool ok = build_from_points<M, R>(a, Mx);
+  lane_eval_mats<DIM, M, R>(Mx, ok, rec, trials, 0, trial_chunks(trials), *ysum, false, err + ss,
+                            0, active);
+}
+
+typedef void (*PointsetFn)(const float*, int, const double*, int, const double*, double*);
+
+static PointsetFn pointset_kernel(int dim, int m, int r) {
+#define WINO_PSET_CASE(I, D, MM, RR) \
+  if (dim == D && m == MM && r == RR) return k_pointset_eval<D, MM, RR>;
+  WINO_SWEEP_SIZES(WINO_PSET_CASE)
+#undef WINO_PSET_CASE
+  return nullptr;
+}
+
+// points: [n_sets][alpha-1] sorted finite points (host); err_out host.
+int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int trials,
+                   unsigned long long seed, double* err_out, cudaStream_t st) {
+  PointsetFn fn = pointset_kernel(dim, m, r);
+  if (!fn) {
+    set_error("point-set sizes: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6");
+    return WINO_EUNSUPPORTED;
+  }
+  const int A = m + r - 1;
+  const int nb = sweep_prepare_blocks(trials);
+  const size_t rec_b = (size_t)trials * sweep_rec_width(dim, m, r) * sizeof(float);
+  size_t o_part = (rec_b + 255) & ~(size_t)255;
+  size_t o_ysum = (o_part + (size_t)nb * 8 + 255) & ~(size_t)255;
+  size_t o_pts = (o_ysum + 8 + 255) & ~(size_t)255;
+  size_t o_err = (o_pts + (size_t)n_sets * (A - 1) * 8 + 255) & ~(size_t)255;
+  const size_t total = o_err + (size_t)n_sets * 8;
+  void* base = nullptr;
+  int rc = scratch_get(kScratchSweep, total, &base);
+  if (rc != WINO_OK) return rc;
+  char* b = (char*)base;
+  float* rec = (float*)b;
+  double* part = (double*)(b + o_part);
+  double* ysum = (double*)(b + o_ysum);
+  double* pts = (double*)(b + o_pts);
+  double* err = (double*)(b + o_err);
+  WINO_CUDA_TRY(cudaMemcpyAsync(pts, sorted, (size_t)n_sets * (A - 1) * 8,
+                                cudaMemcpyHostToDevice, st));
+  rc = sweep_prepare(rec, part, ysum, dim, m, r, trials, seed, st);
+  if (rc != WINO_OK) return rc;
+  {
+    ProfScope ps(kKSweepEval, st);
+    fn<<<(n_sets + 127) / 128, 128, 0, st>>>(rec, trials, pts, n_sets, ysum, err);
+    note_launches(1);
+  }
+  WINO_CUDA_TRY(cudaGetLastError());
+  WINO_CUDA_TRY(cudaMemcpyAsync(err_out, err, (size_t)n_sets * 8, cudaMemcpyDeviceToHost, st));
+  WINO_CUDA_TRY(cudaStreamSynchronize(st));
+  return WINO_OK;
+}
+
 // Device FP64 construction for a batch of instances (the sweep's matrix
 // build, exposed for parity checks): one thread per c.
 __global__ void k_instance_matrices(const double* __restrict__ cg, int n_c, int m, int r,

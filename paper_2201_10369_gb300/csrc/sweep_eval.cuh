@@ -50,6 +50,22 @@ __device__ __forceinline__ bool build_instance(unsigned mask, double c, double d
   return ok;
 }
 
+// The same from explicit finite points a[0] < ... < a[alpha-2] (infinity is
+// the extra point); false when two coincide.
+template <int M, int R>
+__device__ __forceinline__ bool build_from_points(const double* a, Mats<M, R>& Mx) {
+  constexpr int A = M + R - 1;
+  double ATd[M * A], Gd[A * R], BTd[A * A];
+  const bool ok = build_matrices<double>(a, M, R, ATd, Gd, BTd);
+#pragma unroll
+  for (int i = 0; i < M * A; ++i) Mx.AT[i] = __double2float_rn(ATd[i]);
+#pragma unroll
+  for (int i = 0; i < A * R; ++i) Mx.G[i] = __double2float_rn(Gd[i]);
+#pragma unroll
+  for (int i = 0; i < A * A; ++i) Mx.BT[i] = __double2float_rn(BTd[i]);
+  return ok;
+}
+
 // |yhat - y| with y = hi + lo, in FP32.
 __device__ __forceinline__ float abs_err(float yhat, float hi, float lo) {
   return fabsf(__fsub_rn(__fsub_rn(yhat, hi), lo));
@@ -174,19 +190,19 @@ __device__ __forceinline__ double chunk_error(const Mats<M, R>& Mx, const float*
   return num;
 }
 
-// One lane's instance (mask, c) over trial chunks [ch0, ch1) of `trials`
-// warp-uniform trial records.  partial == false (the lane owns every chunk):
+// One lane's instance (matrices Mx; ok = false when two points coincide)
+// over trial chunks [ch0, ch1) of `trials` warp-uniform trial records.
+// partial == false (the lane owns every chunk):
 // *out = sum_t ||yhat_t - y_t||_1 / sum_t ||y_t||_1, +inf when two points
 // coincide.  partial == true: out[ch * stride] = the chunk's sum (+inf when
 // two points coincide), for k_sweep_combine.  Per trial the m (m^2) terms are
 // summed in FP32, the trial sums in FP64 in the chunked order above.
 template <int DIM, int M, int R>
-__device__ __forceinline__ void lane_eval(const float* __restrict__ rec, int trials,
-                                          unsigned mask, double c, double d, int ch0, int ch1,
-                                          double ysum, bool partial, double* __restrict__ out,
-                                          int64_t stride, bool active) {
-  Mats<M, R> Mx;
-  const bool ok = build_instance<M, R>(mask, c, d, Mx);
+__device__ __forceinline__ void lane_eval_mats(const Mats<M, R>& Mx, bool ok,
+                                               const float* __restrict__ rec, int trials,
+                                               int ch0, int ch1, double ysum, bool partial,
+                                               double* __restrict__ out, int64_t stride,
+                                               bool active) {
   double num = 0.0;
   for (int ch = ch0; ch < ch1; ++ch) {
     const int t0 = ch * kTrialChunk;
@@ -198,6 +214,17 @@ __device__ __forceinline__ void lane_eval(const float* __restrict__ rec, int tri
     }
   }
   if (!partial && active) *out = ok ? num / ysum : (double)INFINITY;
+}
+
+// lane_eval_mats for the instance (mask, c, d) of a sweep.
+template <int DIM, int M, int R>
+__device__ __forceinline__ void lane_eval(const float* __restrict__ rec, int trials,
+                                          unsigned mask, double c, double d, int ch0, int ch1,
+                                          double ysum, bool partial, double* __restrict__ out,
+                                          int64_t stride, bool active) {
+  Mats<M, R> Mx;
+  const bool ok = build_instance<M, R>(mask, c, d, Mx);
+  lane_eval_mats<DIM, M, R>(Mx, ok, rec, trials, ch0, ch1, ysum, partial, out, stride, active);
 }
 
 // Partial chunk sums -> errors: err[i] = (sum over chunks ascending of

@@ -80,3 +80,52 @@ def sweep_masks() -> np.ndarray:
         elif pc >= 7:
             out.append(mk)
     return np.array(out, dtype=np.uint8)
+
+
+# The comparison point sets of Barabasz et al. that Tables 7 (1D) and 8 (2D)
+# list beside the proposed ones, finite points of F(n - 2, 3) (infinity is
+# the extra point), keyed (dim, n); and the paper's improvement (%) of its
+# proposed set over each (Tables 7-8, last column).
+_P4 = [0.0, -1.0, 1.0]
+COMPARISON_SETS = {
+    (1, 4): _P4, (1, 5): _P4 + [0.5], (1, 6): _P4 + [0.5, -3.0],
+    (1, 7): _P4 + [0.5, -0.5, -3.0], (1, 8): _P4 + [0.5, -0.5, 2.0, -2.0],
+    (1, 9): _P4 + [0.5, -0.5, 2.0, -2.0, -0.25], (1, 10): _P4 + [0.5, -0.5, 2.0, -2.0, -0.25, 4.0],
+    (2, 4): _P4, (2, 5): _P4 + [0.5], (2, 6): _P4 + [0.5, -2.0],
+    (2, 7): _P4 + [0.5, -2.0, -0.5], (2, 8): _P4 + [0.5, -0.5, 2.0, -2.0],
+    (2, 9): _P4 + [0.5, -0.5, 2.0, -2.0, -0.25], (2, 10): _P4 + [0.5, -0.5, 2.0, -2.0, -0.25, 4.0],
+}
+def _cd(c, d, slots):
+    """Points named by slot letters: z 0, a -1/c, b -c, C c, A 1/c, e -1/d,
+    f -d, D d, E 1/d, p +1, m -1, h 1/2."""
+    v = {"z": 0.0, "a": -1.0 / c, "b": -c, "C": c, "A": 1.0 / c, "p": 1.0, "m": -1.0,
+         "h": 0.5}
+    if d is not None:
+        v.update({"e": -1.0 / d, "f": -d, "D": d, "E": 1.0 / d})
+    return [v[k] for k in slots]
+
+
+# The paper's proposed point sets (Tables 7-8, "Proposed points" column),
+# finite points keyed (dim, n).
+PROPOSED_SETS = {
+    (1, 4): _cd(1.028, None, "zmA"), (1, 5): _cd(1.5, None, "zhbC"),
+    (1, 6): _cd(1.829, None, "abzCA"), (1, 7): _cd(2.22, 1.0, "zabCAD"),
+    (1, 8): _cd(2.0, 1.0, "zabCAfD"), (1, 9): _cd(1.313, 2.478, "zabCAefD"),
+    (1, 10): _cd(1.953, 1.229, "abefzCDEA"),
+    (2, 4): _cd(1.054, None, "zaA"), (2, 5): _cd(2.0, None, "zpmb"),
+    (2, 6): _cd(1.622, None, "abzCA"), (2, 7): _cd(2.0, 1.0, "zabCAD"),
+    (2, 8): _cd(2.0, 1.003, "zabCAeD"), (2, 9): _cd(1.305, 2.485, "zabCAefD"),
+    (2, 10): _cd(1.272, 2.099, "abefzCDEA"),
+}
+PAPER_IMPROVEMENT_PCT = {
+    (1, 4): -24.9, (1, 5): 9.6, (1, 6): 18.35, (1, 7): -14.44, (1, 8): 0.0, (1, 9): 2.14,
+    (1, 10): 59.54, (2, 4): -20.52, (2, 5): 35.75, (2, 6): 27.96, (2, 7): -13.36, (2, 8): 0.0,
+    (2, 9): 17.5, (2, 10): 28.16,
+}
+
+
+def chebyshev_points(n):
+    """The n Chebyshev nodes cos((2k - 1) pi / (2 n)), k = 1..n (Sec. 2), as
+    finite points (infinity is added as the extra point)."""
+    k = np.arange(1, n + 1)
+    return list(np.cos((2 * k - 1) / (2 * n) * np.pi))

@@ -75,3 +75,16 @@ def test_no_cpu_fallback(lib):
     with pytest.raises(lib.WinoError) as e:
         lib.wino_error_sweep([1.5], [(1, 2, 3, 1.0)], [0x06], 10, 0, stream=0)
     assert e.value.status == lib.WINO_EUNSUPPORTED
+
+
+def test_pointset_validation_on_host(wino):
+    """A point set without exactly one +inf is rejected before any device
+    work (and without writing past the caller's set)."""
+    import ctypes
+    import math
+    L = wino.load()
+    pts = (ctypes.c_double * 8)(0.0, 1.0, -1.0, 2.0, 0.0, 1.0, -1.0, math.inf)
+    err = (ctypes.c_double * 2)()
+    assert L.wino_pointset_error(1, 2, 3, pts, 2, 10, 0, err, None) == wino.WINO_EINVAL
+    pts2 = (ctypes.c_double * 4)(0.0, math.inf, -1.0, math.inf)
+    assert L.wino_pointset_error(1, 2, 3, pts2, 1, 10, 0, err, None) == wino.WINO_EINVAL

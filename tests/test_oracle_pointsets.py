@@ -27,11 +27,20 @@ def _rows():
     return rows
 
 
-def chebyshev_points(n):
-    """Sec. 2: x_k = cos((2k - 1) pi / (2 n)), k = 1..n, as the n finite points
-    (reading: with infinity the set has n + 1 points)."""
-    k = np.arange(1, n + 1)
-    return list(np.cos((2 * k - 1) / (2 * n) * np.pi))
+from paper_2201_10369_gb300.inputs import (COMPARISON_SETS, PAPER_IMPROVEMENT_PCT,  # noqa: E402
+                                           PROPOSED_SETS, chebyshev_points)
+
+# Rows of Tables 7-8 whose printed improvement our plain-order FP32 does not
+# reproduce: 1D n=10 and 2D n=5 print proposed-set errors 2.5x and 1.5x below
+# what we measure for those sets (paper_errors.txt, "loose"); 1D n=5 measures
+# -2% against the printed +9.6%.
+SIGN_EXCEPTIONS = {(1, 5), (1, 10), (2, 5)}
+
+
+def test_input_sets_match_golden():
+    """The comparison sets the bench and GPU tests use are the golden file's."""
+    for r in _rows():
+        assert COMPARISON_SETS[(r["dim"], r["m"] + 2)] + [math.inf] == r["points"], r["label"]
 
 
 @pytest.mark.parametrize("row", _rows(), ids=lambda r: r["label"])
@@ -76,3 +85,21 @@ def test_pointset_equals_mask_sweep(orc):
 def test_pointset_degenerate(orc):
     e = orc.pointset_error(1, 2, 3, [[0, 1, 1, math.inf], [0, 1, -1, 2.0]], 50, 0)
     assert math.isinf(e[0]) and math.isnan(e[1])
+
+
+@pytest.mark.slow
+def test_paper_comparison_signs(orc):
+    """Tables 7-8: the paper's proposed set of each size against Barabasz's
+    set of that size.  Where the paper reports a change of more than 5%, our
+    error reproduces its sign (8 such rows; SIGN_EXCEPTIONS lists the three
+    it does not), e.g. 2D F(4x4) c = 1.622: about +30% (paper +28%)."""
+    checked = 0
+    for (dim, n), paper in PAPER_IMPROVEMENT_PCT.items():
+        if abs(paper) <= 5.0 or (dim, n) in SIGN_EXCEPTIONS:
+            continue
+        e = orc.pointset_error(dim, n - 2, 3, [COMPARISON_SETS[(dim, n)] + [math.inf],
+                                                 PROPOSED_SETS[(dim, n)] + [math.inf]], 2000, 0)
+        ours = 100.0 * (e[0] - e[1]) / e[0]
+        assert np.sign(ours) == np.sign(paper), (dim, n, ours, paper)
+        checked += 1
+    assert checked == 8
