@@ -497,7 +497,24 @@ def paper_comparison(wino, inputs, ex, cg, masks, sizes):
             "d": d, "improvement_pct_paper_set": 100.0 * (pn - prop) / pn,
             "improvement_pct_sweep_best": 100.0 * (pn - best) / pn,
             "improvement_pct_printed": inputs.PAPER_IMPROVEMENT_PCT[key]}
+    # two-parameter (c, d) search of the paper's subset for the sizes whose
+    # proposed set has a d: 128 d x 1024 c, log-spaced in [1.001, 4] x [0.25, 4]
+    dg, cgg = np.geomspace(1.001, 4.0, 128), np.geomspace(0.25, 4.0, 1024)
+    for dim, n, mask in CD_SEARCH:
+        row = out.get("%dd_n%d" % (dim, n))
+        if row is None:
+            continue
+        err = wino.cd_sweep(dim, n - 2, cgg, dg, [mask], inputs.SWEEP_TRIALS)[:, 0, :]
+        e = np.where(np.isfinite(err), err, np.nan)
+        i, k = np.unravel_index(np.nanargmin(e), e.shape)
+        row["cd_search"] = {"mask": "%#04x" % mask, "c": float(cgg[k]), "d": float(dg[i]),
+                            "err": float(e[i, k]),
+                            "improvement_pct": 100.0 * (row["barabasz"] - e[i, k]) / row["barabasz"]}
     return out
+
+
+# sizes (dim, n) whose proposed set in Tables 7-8 uses the d-group, with its subset
+CD_SEARCH = [(1, 9, 0x7F), (1, 10, 0xFF), (2, 7, 0x4F), (2, 8, 0x5F)]
 
 
 def fp32_peak_tflops():

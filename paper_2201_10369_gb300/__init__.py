@@ -671,6 +671,39 @@ def wino_pointset_error(size, point_sets, trials: int, seed: int = 0, stream=Non
     return err
 
 
+def cd_sweep(dim: int, m: int, c_grid, d_grid, masks, trials: int, seed: int = 0, r: int = 3,
+             mode: int = WINO_SWEEP_PERSISTENT) -> np.ndarray:
+    """The two-parameter sweep (Sec. 4: the c-group {-1/c, -c, c, 1/c} with a
+    subset of the d-group {-1/d, -d, d, 1/d} for larger sizes): the errors of
+    every valid mask at every (d, c), err[n_d][n_masks][n_c], NaN where a
+    mask is invalid for that d.  Runs as planned persistent launches of at
+    most 64 d values each (one plan size per d); the same trials as
+    wino_error_sweep for size (dim, m, r)."""
+    cg = np.ascontiguousarray(c_grid, dtype=np.float64)
+    dg = [float(d) for d in d_grid]
+    masks = [int(mk) for mk in masks]
+    err = np.full((len(dg), len(masks), cg.size), np.nan)
+    for d0 in range(0, len(dg), 64):
+        sizes = [(dim, m, r, d) for d in dg[d0:d0 + 64]]
+        si, mi, ks = [], [], []
+        for s, size in enumerate(sizes):
+            for mk in valid_masks(size, masks):
+                si.append(np.full(cg.size, s, np.int32))
+                mi.append(np.full(cg.size, mk, np.uint8))
+                ks.append((s, masks.index(mk)))
+        if not ks:
+            continue
+        inst = instance_array(np.concatenate(si), np.concatenate(mi), np.tile(cg, len(ks)))
+        plan = SweepPlan(sizes, inst, trials, seed=seed, mode=mode)
+        try:
+            e = plan.run().reshape(len(ks), cg.size)
+        finally:
+            plan.close()
+        for row, (s, q) in enumerate(ks):
+            err[d0 + s, q] = e[row]
+    return err
+
+
 def grid_instances(sizes, masks, c_grid):
     """All (size, mask, c) of a full grid, in [size][mask][c] order."""
     return [(s, int(mk), float(c)) for s in range(len(sizes)) for mk in masks for c in c_grid]

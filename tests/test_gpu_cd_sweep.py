@@ -1,0 +1,44 @@
+"""GPU checks of the two-parameter sweep (Sec. 4: all four c points plus a
+subset of {-1/d, -d, d, 1/d} for the larger sizes): parity with the oracle
+on a small (c, d) grid, and, for each size whose proposed set of Tables 7-8
+has a d, a grid search that finds a point at least as good as the paper's
+printed (c, d)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2201_10369_gb300.inputs import PROPOSED_SETS
+
+pytestmark = pytest.mark.gpu
+
+INF = math.inf
+
+
+def test_cd_sweep_vs_oracle(wino, orc):
+    dg = [1.5, 2.478, 3.1]
+    cg = [0.4, 0.77, 1.313, 1.9, 2.6, 3.3]
+    masks = [m for m in range(256) if bin(m).count("1") == 7]
+    got = wino.cd_sweep(1, 7, cg, dg, masks, 300, seed=6)
+    for i, d in enumerate(dg):
+        want = orc.error_sweep(cg, [(1, 7, 3, d)], masks, 300, 6)[0]
+        fin = np.isfinite(want)
+        assert np.array_equal(np.isfinite(got[i]), fin)
+        assert np.all(np.abs(got[i][fin] - want[fin]) <= 1e-6 * want[fin])
+
+
+@pytest.mark.parametrize("dim,n,mask,c,d", [
+    (1, 9, 0x7F, 1.313, 2.478),    # Table 7, n=9: {0,-1/c,-c,c,1/c,-1/d,-d,d}
+    (1, 10, 0xFF, 1.953, 1.229),   # Table 7, n=10: all eight points
+    (2, 8, 0x5F, 2.0, 1.003),      # Table 8, n=8: {0,-1/c,-c,c,1/c,-1/d,d}
+])
+def test_cd_search_reaches_paper_point(wino, dim, n, mask, c, d):
+    """A 64 x 512 (d, c) grid over the paper's subset finds an error no more
+    than 2% above the paper's printed point, on the same trials."""
+    m = n - 2
+    paper = wino.wino_pointset_error((dim, m, 3), [PROPOSED_SETS[(dim, n)] + [INF]], 1000)[0]
+    dg = np.geomspace(max(0.5 * d, 1.0 + 1e-3), 2.0 * d, 64)
+    cg = np.geomspace(0.5 * c, 2.0 * c, 512)
+    err = wino.cd_sweep(dim, m, cg, dg, [mask], 1000)[:, 0, :]
+    best = np.nanmin(np.where(np.isinf(err), np.nan, err))
+    assert best <= 1.02 * paper, (best, paper)
