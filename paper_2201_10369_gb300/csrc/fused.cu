@@ -564,7 +564,9 @@ struct SplitCfg {
   static constexpr int SV = Base::F * Base::VPL;  // V chunk (floats)
   static constexpr int STAGE = SU + SV;
   static constexpr int MAIN_FL = NS * STAGE;
-  static constexpr int SMEM_FL = MAIN_FL > Base::EPI_FL ? MAIN_FL : Base::EPI_FL;
+  static constexpr int ETB = Base::TB + 4;                  // epilogue row: TB tiles (padded)
+  static constexpr int EPI_FL = Base::F * Base::KB * ETB;   // Es[f][k][t]
+  static constexpr int SMEM_FL = MAIN_FL > EPI_FL ? MAIN_FL : EPI_FL;
   static constexpr size_t SMEM = (size_t)SMEM_FL * sizeof(float);
   static_assert(NS >= 2, "at least double buffering");
   static_assert((SU * 4) % 16 == 0 && (SV * 4) % 16 == 0, "bulk copies move 16-byte multiples");
@@ -712,20 +714,30 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
   }
   __syncthreads();  // every thread done with the stages the epilogue reuses
 
-  // epilogue: accumulators to Es[f][t][k], then A^T M A per (t, k)
+  // epilogue: accumulators to Es[f][k][t] (rows of TB + 4 floats, tiles
+  // contiguous), then A^T M A per (t, k) with consecutive lanes on
+  // consecutive tiles of one output channel, so that a warp's output rows
+  // land in adjacent 16-byte segments of y.
+  constexpr int ETB = SC::ETB;
   float* Es = sm;
-  // Es[f][t][k] with rows of KB + 4 floats: the float4 stores of a warp
-  // spread evenly over the banks, and the epilogue's reads (k fastest) are
-  // conflict-free.
 #pragma unroll
   for (int q = 0; q < FPL; ++q)
 #pragma unroll
-    for (int i = 0; i < MT; ++i)
+    for (int s4 = 0; s4 < MK / 4; ++s4)
 #pragma unroll
-      for (int s4 = 0; s4 < MK / 4; ++s4) {
-        float* dst = Es + ((size_t)(f0 + q) * TB + lt * MT + i) * Cfg::EKB + s4 * 4 * LK + lk * 4;
-        const float2 lo = unpack2(acc[q][i][2 * s4]), hi = unpack2(acc[q][i][2 * s4 + 1]);
-        *reinterpret_cast<float4*>(dst) = make_float4(lo.x, lo.y, hi.x, hi.y);
+      for (int jj = 0; jj < 4; ++jj) {
+        const int kl = s4 * 4 * LK + lk * 4 + jj;
+        float* dst = Es + ((size_t)(f0 + q) * KB + kl) * ETB + lt * MT;
+#pragma unroll
+        for (int i = 0; i < MT; i += 4) {
+          float v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 pr = unpack2(acc[q][i + u][2 * s4 + jj / 2]);
+            v[u] = (jj & 1) ? pr.y : pr.x;
+          }
+          *reinterpret_cast<float4*>(dst + i) = make_float4(v[0], v[1], v[2], v[3]);
+        }
       }
   __syncthreads();
   // A^T M A per (t, k), the same order as the fused kernel's epilogue; the
@@ -733,15 +745,15 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
   // fma.rn.f32x2 each (two IEEE fused multiply-adds, the same bits).
   const int64_t plane = (int64_t)g.Ho * g.Wo;
   for (int p = tid; p < TB * KB; p += NT) {
-    const int kl = p % KB, t = p / KB;
+    const int t = p % TB, kl = p / TB;
     const int rows = s_rows[t], cols = s_cols[t];
     if (rows == 0) continue;
     const int k = k0 + kl;
     unsigned long long Mp[F / 2];  // (M[i][j], M[i][j + 1]), j even
 #pragma unroll
     for (int q = 0; q < F; q += 2)
-      Mp[q / 2] = pack2(Es[((size_t)q * TB + t) * Cfg::EKB + kl],
-                        Es[((size_t)(q + 1) * TB + t) * Cfg::EKB + kl]);
+      Mp[q / 2] = pack2(Es[((size_t)q * KB + kl) * ETB + t],
+                        Es[((size_t)(q + 1) * KB + kl) * ETB + t]);
     float Z[MM * A];
 #pragma unroll
     for (int a = 0; a < MM; ++a)
@@ -770,9 +782,19 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
       }
       if (a >= rows) continue;
       float* yrow = yt + (int64_t)a * g.Wo;
+      if (MM % 4 == 0 && cols == MM && (((uintptr_t)yrow) & 15) == 0) {
 #pragma unroll
-      for (int b = 0; b < MM; ++b)
-        if (b < cols) yrow[b] = yr[b];
+        for (int b = 0; b < MM; b += 4)
+          *reinterpret_cast<float4*>(yrow + b) = make_float4(yr[b], yr[b + 1], yr[b + 2], yr[b + 3]);
+      } else if (MM % 2 == 0 && cols == MM && (((uintptr_t)yrow) & 7) == 0) {
+#pragma unroll
+        for (int b = 0; b < MM; b += 2)
+          *reinterpret_cast<float2*>(yrow + b) = make_float2(yr[b], yr[b + 1]);
+      } else {
+#pragma unroll
+        for (int b = 0; b < MM; ++b)
+          if (b < cols) yrow[b] = yr[b];
+      }
     }
   }
 }
