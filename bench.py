@@ -569,9 +569,10 @@ def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
 # proportion to the bytes the launch must move).
 NCU_TRAFFIC = {
     # k_gemm_otx F(4x4) tile shape 1, C = K = 64, 224x224, N = 8: U read + y written
-    "fused_layer": (311.44e6, 36 * 25088 * 64 * 4 + 8 * 64 * 224 * 224 * 4),
-    # k_tc_gemm BF16, same layer: U + V read (16-bit), M written (FP32)
-    "tc_gemm": (289.35e6, 36 * (2 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
+    "fused_layer": (314.06e6, 36 * 25088 * 64 * 4 + 8 * 64 * 224 * 224 * 4),
+    # k_tc_gemm split-BF16x6, same layer: three 16-bit parts of U and V read,
+    # M written (FP32)
+    "tc_gemm": (542.59e6, 36 * (2 * 3 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
 }
 
 
@@ -639,12 +640,13 @@ def profile_case(name):
         base, shapes = name[:-4], inputs.VGG16_LAYERS
     elif name[-3:-1] == "_l":  # one VGG16 stage at the bench's N=32
         base, shapes, nimg = name[:-3], [inputs.VGG16_LAYERS[int(name[-1])]], 32
-    if base in ("f4x4", "f6x6", "f4x4_bf16", "f4x4_split"):
+    if base in ("f4x4", "f6x6", "f4x4_bf16", "f4x4_split", "f4x4_x6"):
         # one layer (64 ch, 224x224, N=8) unless a suffix says otherwise
         xs = [inputs.vgg_layer_device(C, H, N=nimg, seed=i) for i, (C, H) in enumerate(shapes)]
         ys = [torch.empty_like(x) for x, _ in xs]
         m, pts = (4, PTS4) if base.startswith("f4x4") else (6, PTS6)
-        dt = {"f4x4_bf16": "bf16", "f4x4_split": "split_bf16x3"}.get(base, "f32")
+        dt = {"f4x4_bf16": "bf16", "f4x4_split": "split_bf16x3",
+              "f4x4_x6": "split_bf16x6"}.get(base, "f32")
         for _ in range(4):
             for (x, w), y in zip(xs, ys):
                 wino.wino_conv2d(x, w, y, pts, m, 3, 1, dt)
@@ -667,7 +669,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     help="run one small workload a few times for an ncu capture: "
-                         "f4x4 | f6x6 | f4x4_bf16 | f4x4_split (VGG 64ch 224x224, N=8; "
+                         "f4x4 | f6x6 | f4x4_bf16 | f4x4_split | f4x4_x6 (VGG 64ch 224x224, N=8; "
                          "suffix _vgg: the five VGG16 stages, N=8; suffix _l0.._l4: that "
                          "VGG16 stage at N=32) | sweep (2D F(4x4), all masks, 4096 c)")
     args = ap.parse_args()

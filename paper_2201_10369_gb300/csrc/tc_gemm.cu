@@ -46,8 +46,6 @@
 
 namespace wino {
 
-__global__ void k_filter_transform(const float* __restrict__ w, float* __restrict__ V, int dim,
-                                   int C, int K, const LayerMats M);
 __global__ void k_output_transform(const float* __restrict__ Mi, float* __restrict__ y,
                                    const LayerGeom g, const LayerMats M);
 
@@ -101,72 +99,141 @@ struct TcScales {
 // ---------------------------------------------------------------------------
 // Operand preparation.
 // ---------------------------------------------------------------------------
-// max |V| of each frequency plane: block (x, f) reduces a grid-stride slice
-// of plane f (warp shuffles, then shared memory) and issues ONE atomicMax on
-// the bit pattern (non-negative floats order like their bits), so a plane of
-// C K values costs gridDim.x atomics, not C K.
-constexpr int kVmaxThreads = 256;
-__global__ void __launch_bounds__(kVmaxThreads) k_vmax(const float* __restrict__ V, int64_t plane,
-                                                       unsigned* __restrict__ vmax_bits) {
-  const int f = blockIdx.y;
-  const float* p = V + (int64_t)f * plane;
-  float mx = 0.0f;
-  for (int64_t i = (int64_t)blockIdx.x * kVmaxThreads + threadIdx.x; i < plane;
-       i += (int64_t)gridDim.x * kVmaxThreads)
-    mx = fmaxf(mx, fabsf(p[i]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  __shared__ float wm[kVmaxThreads / 32];
-  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+// V = G g G^T of one (c, k) kernel with compile-time sizes, in the FP32
+// layer's order (W = G g, l ascending; then V = W G^T, q ascending; every sum
+// from zero with fmaf), so the values equal the FP32 filter transform's.
+template <int MM>
+__device__ __forceinline__ void filter_fixed(const float* __restrict__ g9, const LayerMats& M,
+                                             float (&v)[(MM + 2) * (MM + 2)]) {
+  constexpr int A = MM + 2, R = 3;
+  float gl[R * R];
+#pragma unroll
+  for (int i = 0; i < R * R; ++i) gl[i] = g9[i];
+  float Wk[A][R];
+#pragma unroll
+  for (int i = 0; i < A; ++i)
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int l = 0; l < R; ++l) acc = fmaf(M.G[i * R + l], gl[l * R + q], acc);
+      Wk[i][q] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < A; ++i)
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < R; ++q) acc = fmaf(Wk[i][q], M.G[j * R + q], acc);
+      v[i * A + j] = acc;
+    }
+}
+
+// max |V[f]| over every (c, k): a grid-stride loop over kernels (channels
+// fastest, so neighbouring threads read neighbouring weights), per-thread
+// maxima, then per block one warp-shuffle and shared-memory reduction and
+// ONE atomicMax per frequency on the bit pattern (non-negative floats order
+// like their bits).
+constexpr int kFvThreads = 256;
+template <int MM>
+__global__ void __launch_bounds__(kFvThreads) k_filter_vmax(const float* __restrict__ w, int C,
+                                                           int K, const LayerMats M,
+                                                           unsigned* __restrict__ vmax_bits) {
+  constexpr int F = (MM + 2) * (MM + 2);
+  float mx[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) mx[f] = 0.0f;
+  const int64_t n = (int64_t)C * K;
+  for (int64_t idx = (int64_t)blockIdx.x * kFvThreads + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * kFvThreads) {
+    const int c = (int)(idx % C), k = (int)(idx / C);
+    float v[F];
+    filter_fixed<MM>(w + ((int64_t)k * C + c) * 9, M, v);
+#pragma unroll
+    for (int f = 0; f < F; ++f) mx[f] = fmaxf(mx[f], fabsf(v[f]));
+  }
+  __shared__ float wm[kFvThreads / 32][F];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    float m = mx[f];
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) wm[warp][f] = m;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < kVmaxThreads / 32; ++w) mx = fmaxf(mx, wm[w]);
-    atomicMax(vmax_bits + f, __float_as_uint(mx));
+  if (threadIdx.x < F) {
+    float m = wm[0][threadIdx.x];
+    for (int q = 1; q < kFvThreads / 32; ++q) m = fmaxf(m, wm[q][threadIdx.x]);
+    atomicMax(vmax_bits + threadIdx.x, __float_as_uint(m));
   }
 }
 
-// V32[f][c][k] -> parts V0/V1/V2 [f][k][c] (c padded to Cp with zeros), scaled.
-__global__ void k_quant_v(const float* __restrict__ V, int C, int K, int Cp, int F,
-                          const unsigned* __restrict__ vmax_bits, float* __restrict__ sV,
-                          uint16_t* __restrict__ V0, uint16_t* __restrict__ V1,
-                          uint16_t* __restrict__ V2, int mode) {
+// Filter transform recomputed, scaled by sV[f] = 2^(1 - e) for max |V[f]| =
+// m 2^e, m in [0.5, 1), and split into the operand parts V0/V1/V2
+// [f][k][Cp] (K-major B operand; channels c >= C zero).  One thread per
+// (k, c), channels fastest (coalesced 16-bit stores).  Block 0 also records
+// sV for the epilogue.
+template <int MM>
+__global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ w, int C, int K,
+                                                      int Cp, const LayerMats M,
+                                                      const unsigned* __restrict__ vmax_bits,
+                                                      float* __restrict__ sV,
+                                                      uint16_t* __restrict__ V0,
+                                                      uint16_t* __restrict__ V1,
+                                                      uint16_t* __restrict__ V2, int mode) {
+  constexpr int F = (MM + 2) * (MM + 2);
+  __shared__ float ss[F];
+  if (threadIdx.x < F) {
+    ss[threadIdx.x] = pow2_normaliser(__uint_as_float(vmax_bits[threadIdx.x]));
+    if (blockIdx.x == 0) sV[threadIdx.x] = ss[threadIdx.x];
+  }
+  __syncthreads();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)F * K * Cp;
-  if (idx >= total) return;
-  const int c = (int)(idx % Cp);
-  const int k = (int)((idx / Cp) % K);
-  const int f = (int)(idx / ((int64_t)Cp * K));
-  const float s = pow2_normaliser(__uint_as_float(vmax_bits[f]));
-  if (c == 0 && k == 0) sV[f] = s;
-  float v = 0.0f;
-  if (c < C) v = V[((int64_t)f * C + c) * K + k] * s;
-  uint16_t q[3];
-  split_parts(v, mode, q);
-  V0[idx] = q[0];
-  if (mode == 3 || mode == 4) V1[idx] = q[1];
-  if (mode == 4) V2[idx] = q[2];
+  if (idx >= (int64_t)K * Cp) return;
+  const int c = (int)(idx % Cp), k = (int)(idx / Cp);
+  float v[F];
+  if (c < C) {
+    filter_fixed<MM>(w + ((int64_t)k * C + c) * 9, M, v);
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) v[f] = 0.0f;
+  }
+  const int parts = tc_parts(mode);
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    uint16_t q[3];
+    split_parts(v[f] * ss[f], mode, q);
+    const int64_t o = ((int64_t)f * K + k) * Cp + c;
+    V0[o] = q[0];
+    if (parts > 1) V1[o] = q[1];
+    if (parts > 2) V2[o] = q[2];
+  }
 }
 
 // Input transform (FP32, the FP32 layer's order) -> operand parts
 // U0/U1/U2 [f][t][c], scaled; rows t >= T and columns c >= C are zero.
-// One block = 16 tiles x 16 channels; a thread transforms one (tile,
-// channel) with tiles fastest (neighbouring patches share input rows), the
-// 16-bit results meet in shared memory and leave as 32-byte rows of 16
-// channels.
-constexpr int kQT = 16, kQC = 16;
+// One block = kQT = 4 tiles x 64 channels; a thread transforms two adjacent
+// channels of one tile (tiles fastest: neighbouring patches share input
+// rows).  The 16-bit results are staged in shared memory as 32-bit channel
+// pairs -- rows of 32 pairs padded to kQRow = 40 words, so the 32 stores of
+// a warp (4 tiles x 8 pairs) hit 32 distinct banks -- and leave as whole
+// 128-byte rows of 64 channels (one cache line per (f, tile) and part).
+constexpr int kQT = 4, kQC = 64, kQP = kQC / 2, kQRow = kQP + 8;
+constexpr int kQuantThreads = kQT * kQP;
 // largest staging: three parts of F = 64 frequencies (m = 6)
-constexpr int kQuantSmemMax = 3 * 64 * kQT * kQC * 2;
-template <int MM>
-__global__ void __launch_bounds__(kQT* kQC) k_quant_input_tiled(
-    const float* __restrict__ x, const LayerGeom g, const LayerMats Mx, const TcScales S, int Cp,
-    int64_t Tp, uint16_t* __restrict__ U0, uint16_t* __restrict__ U1, uint16_t* __restrict__ U2,
-    int mode) {
-  constexpr int A = MM + 2, F = A * A;
-  extern __shared__ __align__(16) uint16_t qs[];  // [parts][F][kQT][kQC]
-  const int tl = threadIdx.x % kQT, cl = threadIdx.x / kQT;
-  const int64_t t = (int64_t)blockIdx.x * kQT + tl;
-  const int c = blockIdx.y * kQC + cl;
-  const bool live = t < g.T && c < g.C;
+constexpr int kQuantSmemMax = 3 * 64 * kQT * kQRow * 4;
+
+// B^T d B of the tile patch of channel c (zeros when the tile or the channel
+// is out of range), rows i in [I0, I1) of the result only: frequency f =
+// i alpha + j at out(f, v).  Each value is computed exactly as by the whole
+// transform (the row restriction only skips rows).
+template <int MM, int I0, int I1, class Out>
+__device__ __forceinline__ void quant_patch(const float* __restrict__ x, const LayerGeom& g,
+                                            const LayerMats& Mx, int64_t t, int c, Out out) {
+  constexpr int A = MM + 2;
   float d[A][A];
+  const bool live = t < g.T && c < g.C;
   if (live) {
     const int tpi = g.th * g.tw;
     const int n = (int)(t / tpi);
@@ -189,47 +256,94 @@ __global__ void __launch_bounds__(kQT* kQC) k_quant_input_tiled(
 #pragma unroll
       for (int j = 0; j < A; ++j) d[i][j] = 0.0f;
   }
-  float tm[A][A];
+  float tm[I1 - I0][A];
 #pragma unroll
-  for (int i = 0; i < A; ++i)
+  for (int i = I0; i < I1; ++i)
 #pragma unroll
     for (int l = 0; l < A; ++l) {
       float acc = 0.0f;
 #pragma unroll
       for (int q = 0; q < A; ++q) acc = fmaf(Mx.BT[i * A + q], d[q][l], acc);
-      tm[i][l] = acc;
+      tm[i - I0][l] = acc;
     }
-  const int parts = tc_parts(mode);
-  constexpr int kPart = F * kQT * kQC;  // one part's staging, in 16-bit values
 #pragma unroll
-  for (int i = 0; i < A; ++i)
+  for (int i = I0; i < I1; ++i)
 #pragma unroll
     for (int j = 0; j < A; ++j) {
       float acc = 0.0f;
 #pragma unroll
-      for (int l = 0; l < A; ++l) acc = fmaf(tm[i][l], Mx.BT[j * A + l], acc);
-      const int f = i * A + j;
-      const float v = live ? acc * S.sU[f] : 0.0f;
-      uint16_t q[3];
-      split_parts(v, mode, q);
-      const int o = (f * kQT + tl) * kQC + cl;
-      qs[o] = q[0];
-      if (parts > 1) qs[kPart + o] = q[1];
-      if (parts > 2) qs[2 * kPart + o] = q[2];
+      for (int l = 0; l < A; ++l) acc = fmaf(tm[i - I0][l], Mx.BT[j * A + l], acc);
+      out(i * A + j, live ? acc : 0.0f);
     }
+}
+
+// Rows [I0, I1) of two adjacent channels' transforms, scaled, split and
+// staged as 32-bit channel pairs (channel c in the low half).
+template <int MM, int I0, int I1>
+__device__ __forceinline__ void quant_pair_rows(const float* __restrict__ x, const LayerGeom& g,
+                                                const LayerMats& Mx, const TcScales& S,
+                                                int64_t t, int c, int tl, int cp, int mode,
+                                                int parts, uint32_t* qs, int kPart) {
+  constexpr int A = MM + 2, NR = (I1 - I0) * A;
+  float ua[NR];
+  quant_patch<MM, I0, I1>(x, g, Mx, t, c, [&](int f, float v) { ua[f - I0 * A] = v; });
+  quant_patch<MM, I0, I1>(x, g, Mx, t, c + 1, [&](int f, float v) {
+    uint16_t qa[3], qb[3];
+    split_parts(ua[f - I0 * A] * S.sU[f], mode, qa);
+    split_parts(v * S.sU[f], mode, qb);
+    const int o = (f * kQT + tl) * kQRow + cp;
+    qs[o] = (uint32_t)qa[0] | ((uint32_t)qb[0] << 16);
+    if (parts > 1) qs[kPart + o] = (uint32_t)qa[1] | ((uint32_t)qb[1] << 16);
+    if (parts > 2) qs[2 * kPart + o] = (uint32_t)qa[2] | ((uint32_t)qb[2] << 16);
+  });
+}
+
+template <int MM>
+__global__ void __launch_bounds__(kQuantThreads) k_quant_input_tiled(
+    const float* __restrict__ x, const LayerGeom g, const LayerMats Mx, const TcScales S, int Cp,
+    int64_t Tp, uint16_t* __restrict__ U0, uint16_t* __restrict__ U1, uint16_t* __restrict__ U2,
+    int mode) {
+  constexpr int A = MM + 2, F = A * A;
+  extern __shared__ __align__(16) uint32_t qs[];  // [parts][F][kQT][kQRow] channel pairs
+  constexpr int kPart = F * kQT * kQRow;          // one part's staging, in words
+  const int tl = threadIdx.x % kQT, cp = threadIdx.x / kQT;
+  const int64_t t = (int64_t)blockIdx.x * kQT + tl;
+  const int c = blockIdx.y * kQC + 2 * cp;
+  const int parts = tc_parts(mode);
+  if constexpr (A <= 6) {
+    // both channels' values of a frequency meet in registers: one 32-bit
+    // store per (f, part)
+    quant_pair_rows<MM, 0, A>(x, g, Mx, S, t, c, tl, cp, mode, parts, qs, kPart);
+  } else {
+    // alpha = 8: holding one channel's 64 values while transforming the
+    // other costs too many registers (and transforming in row halves costs
+    // a second pass over the patches), so each channel goes straight to its
+    // 16-bit half of the same words
+    uint16_t* qh = reinterpret_cast<uint16_t*>(qs);
+    for (int h = 0; h < 2; ++h)
+      quant_patch<MM, 0, A>(x, g, Mx, t, c + h, [&](int f, float v) {
+        uint16_t q[3];
+        split_parts(v * S.sU[f], mode, q);
+        const int o = 2 * ((f * kQT + tl) * kQRow + cp) + h;
+        qh[o] = q[0];
+        if (parts > 1) qh[2 * kPart + o] = q[1];
+        if (parts > 2) qh[4 * kPart + o] = q[2];
+      });
+  }
   __syncthreads();
-  // rows (f, tile) of 16 channels = 32 bytes = two 16-byte stores per part
+  // rows (f, tile) of 64 channels = 8 x 16-byte stores, consecutive threads
+  // on consecutive segments of a row
   const int64_t plane = Tp * Cp;
   const int64_t tb = (int64_t)blockIdx.x * kQT;
   const int c0 = blockIdx.y * kQC;
   uint16_t* const dsts[3] = {U0, U1, U2};
-  for (int e = threadIdx.x; e < F * kQT * 2; e += kQT * kQC) {
-    const int half = e & 1, row = e >> 1;  // row = f * kQT + tl
+  for (int e = threadIdx.x; e < F * kQT * 8; e += kQuantThreads) {
+    const int seg = e % 8, row = e / 8;  // row = f * kQT + tile
     const int f = row / kQT, tr = row % kQT;
-    const int64_t dst = f * plane + (tb + tr) * Cp + c0 + half * 8;
+    const int64_t dst = f * plane + (tb + tr) * Cp + c0 + seg * 8;
     for (int pp = 0; pp < parts; ++pp)
       *reinterpret_cast<uint4*>(dsts[pp] + dst) =
-          *reinterpret_cast<const uint4*>(qs + pp * kPart + row * kQC + half * 8);
+          *reinterpret_cast<const uint4*>(qs + pp * kPart + row * kQRow + seg * 4);
   }
 }
 
@@ -265,16 +379,34 @@ __global__ void __launch_bounds__(256) k_output_transform_r3(const float* __rest
   const int rem = (int)(t - (int64_t)n * tpi);
   const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
   float* yk = y + ((int64_t)n * g.K + k) * g.Ho * g.Wo;
+  const int cols = min(MM, g.Wo - tj * MM);
 #pragma unroll
   for (int a = 0; a < MM; ++a) {
     const int p = ti * MM + a;
+    float yr[MM];
 #pragma unroll
     for (int b = 0; b < MM; ++b) {
       float acc = 0.0f;
 #pragma unroll
       for (int j = 0; j < A; ++j) acc = fmaf(Z[a][j], Mx.AT[b * A + j], acc);
-      const int q = tj * MM + b;
-      if (p < g.Ho && q < g.Wo) yk[(int64_t)p * g.Wo + q] = acc;
+      yr[b] = acc;
+    }
+    if (p >= g.Ho) continue;
+    float* yrow = yk + (int64_t)p * g.Wo + tj * MM;
+    // whole rows as vector stores when aligned (adjacent lanes hold adjacent
+    // tiles, so a warp writes one contiguous run)
+    if (MM % 4 == 0 && cols == MM && (((uintptr_t)yrow) & 15) == 0) {
+#pragma unroll
+      for (int b = 0; b < MM; b += 4)
+        *reinterpret_cast<float4*>(yrow + b) = make_float4(yr[b], yr[b + 1], yr[b + 2], yr[b + 3]);
+    } else if (MM % 2 == 0 && cols == MM && (((uintptr_t)yrow) & 7) == 0) {
+#pragma unroll
+      for (int b = 0; b < MM; b += 2)
+        *reinterpret_cast<float2*>(yrow + b) = make_float2(yr[b], yr[b + 1]);
+    } else {
+#pragma unroll
+      for (int b = 0; b < MM; ++b)
+        if (b < cols) yrow[b] = yr[b];
     }
   }
 }
@@ -517,7 +649,7 @@ static size_t tc_smem_bytes(int NB, int parts) {
 
 // Workspace layout of the precision form (bytes), all 1024-aligned.
 struct TcLayout {
-  size_t V32, vmax, sV, V[3], U[3], M, total;
+  size_t vmax, sV, V[3], U[3], M, total;
 };
 
 static TcLayout tc_layout(const LayerGeom& g, int dtype) {
@@ -527,8 +659,6 @@ static TcLayout tc_layout(const LayerGeom& g, int dtype) {
   const int parts = tc_parts(dtype);
   TcLayout L;
   size_t o = 0;
-  L.V32 = o;
-  o = al(o + (size_t)g.F * g.C * g.K * 4);
   L.vmax = o;
   o = al(o + (size_t)g.F * 4);
   L.sV = o;
@@ -549,10 +679,14 @@ static TcLayout tc_layout(const LayerGeom& g, int dtype) {
 
 size_t tc_workspace_bytes(const LayerGeom& g, int dtype) { return tc_layout(g, dtype).total; }
 
-static int tc_nb(int K) {
+// Output channels per CTA (MMA N): the largest of 256..16 dividing K; at most
+// 128 for the three-part form, whose 256-wide tiles would need 148 KB of
+// shared memory and so leave one CTA per SM, with nothing to overlap its
+// single-stage load / MMA loop.
+static int tc_nb(int K, int parts) {
   const int cands[5] = {256, 128, 64, 32, 16};
   for (int nb : cands)
-    if (K % nb == 0) return nb;
+    if (K % nb == 0 && !(parts == 3 && nb > 128)) return nb;
   return 0;
 }
 
@@ -562,7 +696,7 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     set_error("tensor-core forms support 2D F(m x m, 3 x 3), m in {2, 4, 6}");
     return WINO_EUNSUPPORTED;
   }
-  const int NB = tc_nb(g.K);
+  const int NB = tc_nb(g.K, tc_parts(dtype));
   if (NB == 0) {
     set_error("tensor-core forms need K a multiple of 16");
     return WINO_EUNSUPPORTED;
@@ -575,7 +709,6 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
   const int mode = dtype;  // 1 bf16, 2 fp16, 3 split bf16 x3, 4 split bf16 x6
   const int parts = tc_parts(mode);
   char* b = (char*)ws;
-  float* V32 = (float*)(b + L.V32);
   unsigned* vmax = (unsigned*)(b + L.vmax);
   float* sV = (float*)(b + L.sV);
   int* err = nullptr;
@@ -612,17 +745,25 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
   WINO_CUDA_TRY(cudaMemsetAsync(vmax, 0, (size_t)g.F * 4, st));
   {
     ProfScope ps(kKTcTransform, st);
-    const int64_t n = (int64_t)g.C * g.K;
-    k_filter_transform<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, V32, g.dim, g.C, g.K, M);
-    const int64_t plane = (int64_t)g.C * g.K;
-    const unsigned bx = (unsigned)std::min<int64_t>(256, (plane + 8 * kVmaxThreads - 1) /
-                                                            (8 * kVmaxThreads));
-    k_vmax<<<dim3(bx, (unsigned)g.F), kVmaxThreads, 0, st>>>(V32, plane, vmax);
-    const int64_t nq = (int64_t)g.F * g.K * Cp;
-    k_quant_v<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(V32, g.C, g.K, Cp, g.F, vmax, sV,
-                                                            Vp[0], Vp[1], Vp[2], mode);
+    // per-frequency maxima of V (each block reduces up to 8 kernels per
+    // thread), then V recomputed, scaled and split
+    const int64_t nck = (int64_t)g.C * g.K;
+    const unsigned bf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(
+                                                           (nck + 8 * kFvThreads - 1) /
+                                                           (8 * kFvThreads), 1 << 16));
+    const unsigned bq = (unsigned)(((int64_t)g.K * Cp + 255) / 256);
+    if (M.m == 2) {
+      k_filter_vmax<2><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
+      k_filter_quant<2><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode);
+    } else if (M.m == 4) {
+      k_filter_vmax<4><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
+      k_filter_quant<4><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode);
+    } else {
+      k_filter_vmax<6><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
+      k_filter_quant<6><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode);
+    }
     const dim3 gq((unsigned)(Tp / kQT), (unsigned)(Cp / kQC));
-    const size_t qsm = (size_t)parts * g.F * kQT * kQC * sizeof(uint16_t);
+    const size_t qsm = (size_t)parts * g.F * kQT * kQRow * sizeof(uint32_t);
     static bool qattr[16] = {false};
     int qdev = 0;
     WINO_CUDA_TRY(cudaGetDevice(&qdev));
@@ -636,15 +777,15 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
       qattr[qdev] = true;
     }
     if (M.m == 2)
-      k_quant_input_tiled<2><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+      k_quant_input_tiled<2><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
                                                          mode);
     else if (M.m == 4)
-      k_quant_input_tiled<4><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+      k_quant_input_tiled<4><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
                                                          mode);
     else
-      k_quant_input_tiled<6><<<gq, kQT * kQC, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+      k_quant_input_tiled<6><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
                                                          mode);
-    note_launches(4);
+    note_launches(3);
   }
   TcGemmArgs P;
   for (int pp = 0; pp < 3; ++pp) {
