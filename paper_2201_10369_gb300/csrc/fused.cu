@@ -100,7 +100,7 @@ struct FusedCfg {
   static constexpr int SMEM_FL = MAIN_FL > EPI_FL ? MAIN_FL : EPI_FL;
   static constexpr size_t SMEM = (size_t)SMEM_FL * sizeof(float);
   static_assert(LX * LT * LK == 32, "a warp is 32 lanes");
-  static_assert(F % (LX * FPL) == 0 && NW % 4 == 0, "whole warps, 4 per SM sub-partition");
+  static_assert(F % (LX * FPL) == 0, "whole warps");
   static_assert(MT % 4 == 0 && MK % 4 == 0, "float4 operand loads");
 };
 
@@ -556,8 +556,8 @@ __global__ void __launch_bounds__(256) k_filter_transform_blk(const float* __res
                        [&](int f, float v) { out[(int64_t)f * sg.VPL] = v; });
 }
 
-// NS stages of (U chunk, V chunk) in shared memory.
-template <FUSED_TPARAMS, int NS>
+// NS stages of (U chunk, V chunk) in shared memory; MINB CTAs per SM.
+template <FUSED_TPARAMS, int NS, int MINB>
 struct SplitCfg {
   using Base = FusedCfg<FUSED_TARGS>;
   static constexpr int SU = Base::F * Base::UPL;  // U chunk (floats)
@@ -572,11 +572,11 @@ struct SplitCfg {
   static_assert((SU * 4) % 16 == 0 && (SV * 4) % 16 == 0, "bulk copies move 16-byte multiples");
 };
 
-#define SPLIT_TPARAMS FUSED_TPARAMS, int NS
-#define SPLIT_TARGS FUSED_TARGS, NS
+#define SPLIT_TPARAMS FUSED_TPARAMS, int NS, int MINB
+#define SPLIT_TARGS FUSED_TARGS, NS, MINB
 
 template <SPLIT_TPARAMS>
-__global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, 1)
+__global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, MINB)
     k_gemm_otx(const float* __restrict__ Ub, const float* __restrict__ Vb, float* __restrict__ y,
                const LayerGeom g, const LayerMats Mx, const SplitGeom sg, int* err) {
   using Cfg = FusedCfg<FUSED_TARGS>;
@@ -860,16 +860,18 @@ static int launch_split(const float* x, const float* w, float* y, const LayerGeo
 }
 
 // Tile shapes of the split variant per m, as
-// (MM, LX, LT, LK, FPL, MT, MK, CC, NS) -> TB = LT MT tiles x KB = LK MK
-// output channels per CTA, CC channels per chunk, NS stages.  The layer
-// autotuner times each.
-#define SPLIT_M2_0 2, 2, 4, 4, 1, 8, 16, 8, 2
-#define SPLIT_M4_0 4, 1, 4, 8, 3, 4, 8, 8, 2
-#define SPLIT_M4_1 4, 1, 8, 4, 3, 4, 8, 8, 2
-#define SPLIT_M4_2 4, 1, 8, 4, 3, 4, 8, 4, 4
-#define SPLIT_M6_0 6, 8, 1, 4, 1, 8, 16, 4, 2
-#define SPLIT_M6_1 6, 8, 2, 2, 1, 8, 16, 4, 3
-#define SPLIT_M6_2 6, 8, 2, 2, 1, 8, 16, 2, 4
+// (MM, LX, LT, LK, FPL, MT, MK, CC, NS, MINB) -> TB = LT MT tiles x KB =
+// LK MK output channels per CTA, CC channels per chunk, NS stages, MINB CTAs
+// per SM for the register budget.  The layer autotuner times each.  (A
+// 32 x 16 tile with an 8 x 8 microtile per thread and two CTAs per SM was
+// measured slower: its register cap forces spills.)
+#define SPLIT_M2_0 2, 2, 4, 4, 1, 8, 16, 8, 2, 1
+#define SPLIT_M4_0 4, 1, 4, 8, 3, 4, 8, 8, 2, 1
+#define SPLIT_M4_1 4, 1, 8, 4, 3, 4, 8, 8, 2, 1
+#define SPLIT_M4_2 4, 1, 8, 4, 3, 4, 8, 4, 4, 1
+#define SPLIT_M6_0 6, 8, 1, 4, 1, 8, 16, 4, 2, 1
+#define SPLIT_M6_1 6, 8, 2, 2, 1, 8, 16, 4, 3, 1
+#define SPLIT_M6_2 6, 8, 2, 2, 1, 8, 16, 2, 4, 1
 
 int split_configs(int m) { return m == 2 ? 1 : 3; }
 
