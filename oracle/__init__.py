@@ -85,6 +85,11 @@ def lib():
             L.orc_pointset_error.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_int, ctypes.c_int,
                                                                   ctypes.c_uint64, dp]
             L.orc_pointset_error.restype = ctypes.c_int
+            L.orc_tile2d_kron.argtypes = [dp, ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int]
+            L.orc_tile2d_kron.restype = ctypes.c_int
+            L.orc_pointset_error_kron.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_uint64, ctypes.c_int, dp]
+            L.orc_pointset_error_kron.restype = ctypes.c_int
             L.orc_round_bf16.argtypes = [ctypes.c_float]
             L.orc_round_bf16.restype = ctypes.c_float
             L.orc_round_fp16.argtypes = [ctypes.c_float]
@@ -242,6 +247,31 @@ def error_sweep(c_grid, sizes, masks, trials: int, seed: int, c_stride: int = 1,
     lib().orc_error_sweep(_dp(cg), cg.size, sz, len(sizes),
                           mk.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), mk.size, trials,
                           seed, _dp(err), c_stride, n_threads)
+    return err
+
+
+def tile2d_kron(points, m: int, r: int, g, d, pairwise: bool = False):
+    """One 2D tile in the Kronecker-product form (Sec. 7): y [m][m]."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float32).ravel()
+    d = np.ascontiguousarray(d, dtype=np.float32).ravel()
+    y = np.zeros(m * m, np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    rc = lib().orc_tile2d_kron(_dp(pts), m, r, g.ctypes.data_as(fp), d.ctypes.data_as(fp),
+                               y.ctypes.data_as(fp), int(pairwise))
+    assert rc == 0, rc
+    return y.reshape(m, m)
+
+
+def pointset_error_kron(m: int, r: int, point_sets, trials: int, seed: int,
+                        pairwise: bool = False):
+    """The sweep metric of the Kronecker-product 2D form for explicit sets."""
+    pts = np.ascontiguousarray(point_sets, dtype=np.float64)
+    assert pts.ndim == 2 and pts.shape[1] == m + r - 1
+    err = np.full(pts.shape[0], np.nan)
+    rc = lib().orc_pointset_error_kron(m, r, _dp(pts), pts.shape[0], trials, seed, int(pairwise),
+                                       _dp(err))
+    assert rc == 0
     return err
 
 

@@ -693,6 +693,121 @@ int orc_pointset_error(int dim, int m, int r, const double* points, int n_sets, 
   return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Kronecker-product form of the 2D tile (Sec. 7): with row-major vec,       */
+/*   vec(G g G^T) = (G (x) G) vec(g),  vec(B^T d B) = (B^T (x) B^T) vec(d),   */
+/*   vec(A^T M A) = (A^T (x) A^T) vec(M).                                     */
+/* Reading: the Kronecker entries are products of the FP64 matrix entries,  */
+/* rounded once to FP32 ("multiply the transform matrices together before   */
+/* the vector multiplication"); each product row is summed in FP32 with     */
+/* fmaf, column index ascending, or (pairwise) as rounded products summed   */
+/* pairwise: sum(x[0..n)) = sum(x[0..h)) + sum(x[h..n)), h = ceil(n / 2).   */
+/* ------------------------------------------------------------------------ */
+
+static float pairwise_sum(const float* x, int n) {
+  if (n == 1) return x[0];
+  const int h = (n + 1) / 2;
+  return pairwise_sum(x, h) + pairwise_sum(x + h, n - h);
+}
+
+/* y[rows] = K[rows][cols] x[cols] in FP32, one of the two summation orders */
+static void kron_matvec(const float* K, int rows, int cols, const float* x, float* y,
+                        int pairwise) {
+  float prod[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int i = 0; i < rows; ++i) {
+    const float* k = K + (size_t)i * cols;
+    if (pairwise) {
+      for (int c = 0; c < cols; ++c) prod[c] = k[c] * x[c];
+      y[i] = pairwise_sum(prod, cols);
+    } else {
+      float acc = 0.0f;
+      for (int c = 0; c < cols; ++c) acc = fmaf(k[c], x[c], acc);
+      y[i] = acc;
+    }
+  }
+}
+
+/* The three Kronecker matrices of a point set, FP32. */
+typedef struct {
+  int m, r, A;
+  float KG[ORC_MAX_ALPHA * ORC_MAX_ALPHA * 25];                       /* [A^2][r^2] */
+  float KB[ORC_MAX_ALPHA * ORC_MAX_ALPHA * ORC_MAX_ALPHA * ORC_MAX_ALPHA]; /* [A^2][A^2] */
+  float KA[ORC_MAX_ALPHA * ORC_MAX_ALPHA * ORC_MAX_ALPHA * ORC_MAX_ALPHA]; /* [m^2][A^2] */
+} kron_mats;
+
+static int build_kron(const double* points, int m, int r, kron_mats* K) {
+  const int A = m + r - 1;
+  if (r > 5 || A > ORC_MAX_ALPHA) return -1;
+  double ATd[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Gd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  double BTd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  int st = orc_make_matrices(points, m, r, ATd, Gd, BTd);
+  if (st < 0) return st;
+  K->m = m; K->r = r; K->A = A;
+  for (int i = 0; i < A; ++i)
+    for (int j = 0; j < A; ++j)
+      for (int k = 0; k < r; ++k)
+        for (int l = 0; l < r; ++l)
+          K->KG[(i * A + j) * r * r + k * r + l] = (float)(Gd[i * r + k] * Gd[j * r + l]);
+  for (int i = 0; i < A; ++i)
+    for (int j = 0; j < A; ++j)
+      for (int k = 0; k < A; ++k)
+        for (int l = 0; l < A; ++l)
+          K->KB[(i * A + j) * A * A + k * A + l] = (float)(BTd[i * A + k] * BTd[j * A + l]);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b)
+      for (int i = 0; i < A; ++i)
+        for (int j = 0; j < A; ++j)
+          K->KA[(a * m + b) * A * A + i * A + j] = (float)(ATd[a * A + i] * ATd[b * A + j]);
+  return 0;
+}
+
+static void kron_tile(const kron_mats* K, const float* g, const float* d, float* y, int pairwise) {
+  const int A2 = K->A * K->A;
+  float u[ORC_MAX_ALPHA * ORC_MAX_ALPHA], v[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float p[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  kron_matvec(K->KG, A2, K->r * K->r, g, u, pairwise);
+  kron_matvec(K->KB, A2, A2, d, v, pairwise);
+  for (int i = 0; i < A2; ++i) p[i] = u[i] * v[i];
+  kron_matvec(K->KA, K->m * K->m, A2, p, y, pairwise);
+}
+
+int orc_tile2d_kron(const double* points, int m, int r, const float* g, const float* d,
+                    float* y, int pairwise) {
+  kron_mats* K = (kron_mats*)malloc(sizeof(kron_mats));
+  if (!K) return -1;
+  int st = build_kron(points, m, r, K);
+  if (st == 0) kron_tile(K, g, d, y, pairwise);
+  free(K);
+  return st;
+}
+
+int orc_pointset_error_kron(int m, int r, const double* points, int n_sets, int trials,
+                            uint64_t seed, int pairwise, double* err_out) {
+  const int A = m + r - 1;
+  if (A < 2 || A > ORC_MAX_ALPHA || r > 5 || n_sets < 0 || trials < 1) return -1;
+  orc_size s = {2, m, r, 1.0};
+  size_data sd;
+  memset(&sd, 0, sizeof(sd));
+  int rc = build_size_data(&s, trials, seed, &sd);
+  kron_mats* K = (kron_mats*)malloc(sizeof(kron_mats));
+  if (!K) rc = -1;
+  for (int q = 0; q < n_sets && rc == 0; ++q) {
+    int st = build_kron(points + (size_t)q * A, m, r, K);
+    if (st == -2) { err_out[q] = INFINITY; continue; }
+    if (st < 0) { err_out[q] = NAN; continue; }
+    double num = 0.0;
+    float yh[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+    for (int t = 0; t < trials; ++t) {
+      kron_tile(K, sd.g + (size_t)t * sd.nin_g, sd.d + (size_t)t * sd.nin_d, yh, pairwise);
+      for (int j = 0; j < sd.nout; ++j) num += fabs((double)yh[j] - sd.y[(size_t)t * sd.nout + j]);
+    }
+    err_out[q] = num / sd.ysum;
+  }
+  free(K);
+  free(sd.g); free(sd.d); free(sd.y);
+  return rc;
+}
+
 double orc_direct_error(int dim, int m, int r, int trials, uint64_t seed) {
   orc_size s = {dim, m, r, 1.0};
   size_data sd;

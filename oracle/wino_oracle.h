@@ -111,6 +111,20 @@ int orc_error_sweep(const double* c_grid, int n_c, const orc_size* sizes,
 int orc_pointset_error(int dim, int m, int r, const double* points, int n_sets, int trials,
                        uint64_t seed, double* err_out);
 
+/* Kronecker-product form of the 2D Winograd tile (Sec. 7):
+ *   u = (G (x) G) vec(g), v = (B^T (x) B^T) vec(d), y = (A^T (x) A^T)(u .* v),
+ * row-major vec; Kronecker entries = FP64 products of the FP64 matrix entries
+ * rounded once to FP32; each row summed with fmaf (column ascending), or
+ * with pairwise = 1 as rounded products summed pairwise (split at ceil(n/2)).
+ * orc_tile2d_kron: one tile (g r x r, d alpha x alpha, y m x m, row-major);
+ * returns 0 or -1 / -2 like orc_make_matrices.  orc_pointset_error_kron: the
+ * sweep metric on the sweep's 2D trials of size (m, r), like
+ * orc_pointset_error.                                                      */
+int orc_tile2d_kron(const double* points, int m, int r, const float* g, const float* d,
+                    float* y, int pairwise);
+int orc_pointset_error_kron(int m, int r, const double* points, int n_sets, int trials,
+                            uint64_t seed, int pairwise, double* err_out);
+
 /* The same metric for FP32 direct correlation (the "n = 0" row).         */
 double orc_direct_error(int dim, int m, int r, int trials, uint64_t seed);
 

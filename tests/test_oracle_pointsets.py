@@ -103,3 +103,39 @@ def test_paper_comparison_signs(orc):
         assert np.sign(ours) == np.sign(paper), (dim, n, ours, paper)
         checked += 1
     assert checked == 8
+
+
+@pytest.mark.parametrize("pairwise", [False, True])
+def test_kron_tile_exact_on_integers(orc, pairwise):
+    """Exact regime of the Kronecker-product form (Sec. 7): P4's matrices and
+    their Kronecker products are exact in FP32, so on small integer inputs
+    the tile equals the direct correlation -- a transposed Kronecker matrix or
+    a swapped factor order (d read as d^T) fails here."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        g = rng.integers(-9, 10, (3, 3)).astype(np.float32)
+        d = rng.integers(-9, 10, (4, 4)).astype(np.float32)
+        y = orc.tile2d_kron([0.0, -1.0, 1.0, math.inf], 2, 3, g, d, pairwise)
+        want = np.array([[np.sum(d[a:a + 3, b:b + 3] * g) for b in range(2)] for a in range(2)])
+        assert np.array_equal(y, want.astype(np.float32))
+
+
+def test_kron_and_nested_agree_to_first_order(orc):
+    """Off the exact regime the two forms differ only by rounding: on the
+    sweep's trials their errors agree to first order (within 2x)."""
+    sets = [COMPARISON_SETS[(2, 6)] + [math.inf]]
+    a = orc.pointset_error(2, 4, 3, sets, 300, 0)[0]
+    b = orc.pointset_error_kron(4, 3, sets, 300, 0)[0]
+    assert 0.5 < b / a < 2.0
+
+
+def test_kron_error_larger_than_nested(orc):
+    """Sec. 7: the Kronecker-product transforms give a larger FP error than the
+    nested matrix products, and pairwise summation does not remove the gap
+    (2D, n = 5..8, Barabasz's and the proposed sets)."""
+    for n in range(5, 9):
+        sets = [COMPARISON_SETS[(2, n)] + [math.inf], PROPOSED_SETS[(2, n)] + [math.inf]]
+        nested = orc.pointset_error(2, n - 2, 3, sets, 1000, 0)
+        kron = orc.pointset_error_kron(n - 2, 3, sets, 1000, 0)
+        pw = orc.pointset_error_kron(n - 2, 3, sets, 1000, 0, pairwise=True)
+        assert np.all(kron > nested) and np.all(pw > nested), (n, nested, kron, pw)
