@@ -186,6 +186,18 @@ int wino_pointset_error(int dim, int m, int r, const double* points, int n_sets,
                         int trials, unsigned long long seed, double* err_out,
                         void* cuda_stream);
 
+/* The same metric for the Kronecker-product form of the 2D tile (Sec. 7):
+ *   u = (G (x) G) vec(g), v = (B^T (x) B^T) vec(d), y = (A^T (x) A^T)(u .* v)
+ * (row-major vec), Kronecker entries = FP64 products of the FP64 matrix
+ * entries rounded once to FP32, each row summed with fmaf (column ascending)
+ * or, pairwise != 0, as rounded products summed pairwise (a sum of n terms
+ * splits at ceil(n / 2)).  2D F(m x m, 3 x 3), m = 2..6, on the sweep's 2D
+ * trials of that size; points and err_out as for wino_pointset_error; trial
+ * errors summed in FP64 in a fixed order.  Synchronises `cuda_stream`.     */
+int wino_pointset_error_kron(int m, int r, const double* points, int n_sets,
+                             int trials, unsigned long long seed, int pairwise,
+                             double* err_out, void* cuda_stream);
+
 /* The FP64 transform matrices the sweep builds on the device for the
  * instances (size, mask, c_k), k < n_c -- the same construction as
  * wino_make_matrices (Sec. 4.1-4.2), run by the sweep's own device code.

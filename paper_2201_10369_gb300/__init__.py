@@ -111,6 +111,9 @@ def _declare(L):
     L.wino_device_ok.restype = _i
     L.wino_pointset_error.argtypes = [_i, _i, _i, _DP, _i, _i, ctypes.c_ulonglong, _DP, _vp]
     L.wino_pointset_error.restype = _i
+    L.wino_pointset_error_kron.argtypes = [_i, _i, _DP, _i, _i, ctypes.c_ulonglong, _i, _DP,
+                                           _vp]
+    L.wino_pointset_error_kron.restype = _i
     L.wino_wait_error.argtypes = [ctypes.POINTER(ctypes.c_int)]
     L.wino_wait_error.restype = _i
     L.wino_shutdown.restype = None
@@ -701,6 +704,20 @@ def cd_sweep(dim: int, m: int, c_grid, d_grid, masks, trials: int, seed: int = 0
             plan.close()
         for row, (s, q) in enumerate(ks):
             err[d0 + s, q] = e[row]
+    return err
+
+
+def wino_pointset_error_kron(m: int, point_sets, trials: int, seed: int = 0,
+                             pairwise: bool = False, r: int = 3, stream=None) -> np.ndarray:
+    """The sweep metric of the Kronecker-product form of the 2D tile (Sec. 7)
+    for explicit point sets, on the sweep's 2D trials of size (m, r)."""
+    pts = np.ascontiguousarray(point_sets, dtype=np.float64)
+    if pts.ndim != 2 or pts.shape[1] != m + r - 1:
+        raise ValueError("each point set needs m + r - 1 values")
+    err = np.empty(pts.shape[0])
+    _check(load().wino_pointset_error_kron(m, r, pts.ctypes.data_as(_DP), pts.shape[0], trials,
+                                           seed, int(pairwise), err.ctypes.data_as(_DP),
+                                           _stream(stream)))
     return err
 
 

@@ -380,6 +380,28 @@ int wino_pointset_error(int dim, int m, int r, const double* points, int n_sets,
                         (cudaStream_t)cuda_stream);
 }
 
+int wino_pointset_error_kron(int m, int r, const double* points, int n_sets, int trials,
+                             unsigned long long seed, int pairwise, double* err_out,
+                             void* cuda_stream) {
+  const int alpha = m + r - 1;
+  if (!points || !err_out || n_sets < 1 || n_sets > (1 << 20) || trials < 1 ||
+      trials > (1 << 20) || m < 1 || r < 1 || alpha < 3 || alpha > 10) {
+    set_error("invalid Kronecker point-set arguments");
+    return WINO_EINVAL;
+  }
+  std::vector<double> sorted((size_t)n_sets * (alpha - 1));
+  for (int q = 0; q < n_sets; ++q) {
+    double fin[kMaxAlpha];
+    int st = canonical_points(points + (size_t)q * alpha, alpha, fin);
+    if (st != WINO_OK) return st;
+    for (int i = 0; i < alpha - 1; ++i) sorted[(size_t)q * (alpha - 1) + i] = fin[i];
+  }
+  int st = check_device();
+  if (st != WINO_OK) return st;
+  return pointset_error_kron(m, r, sorted.data(), n_sets, trials, seed, pairwise, err_out,
+                             (cudaStream_t)cuda_stream);
+}
+
 int wino_instance_matrices(const double* c_grid, int n_c, wino_size size, unsigned mask,
                            double* AT, double* G, double* BT, unsigned char* singular,
                            void* cuda_stream) {

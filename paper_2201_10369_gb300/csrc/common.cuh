@@ -126,6 +126,8 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
                 double* err_out, cudaStream_t st);
 int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int trials,
                    unsigned long long seed, double* err_out, cudaStream_t st);
+int pointset_error_kron(int m, int r, const double* sorted, int n_sets, int trials,
+                        unsigned long long seed, int pairwise, double* err_out, cudaStream_t st);
 int instance_matrices(const double* c_grid, int n_c, const SweepSize& s, unsigned mask,
                       double* AT, double* G, double* BT, unsigned char* singular,
                       cudaStream_t st);

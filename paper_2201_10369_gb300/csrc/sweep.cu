@@ -399,6 +399,167 @@ int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int 
   return WINO_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Kronecker-product form of the 2D tile (Sec. 7): with row-major vec,
+// vec(G g G^T) = (G (x) G) vec(g), vec(B^T d B) = (B^T (x) B^T) vec(d),
+// vec(A^T M A) = (A^T (x) A^T) vec(M).  Kronecker entries: FP64 products of
+// the FP64 matrix entries, rounded once to FP32.  Each row is summed with
+// fmaf, column ascending, or (pairwise) as rounded products summed pairwise,
+// sum(x[0..n)) = sum(x[0..h)) + sum(x[h..n)), h = ceil(n / 2).
+// One block per point set (its Kronecker matrices in shared memory); threads
+// take trials t = tid, tid + blockDim, ...; per-thread FP64 sums of the
+// per-trial FP32 errors, added in thread order.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ float pairwise_sum(const float* x) {
+  if constexpr (N == 1) {
+    return x[0];
+  } else {
+    constexpr int H = (N + 1) / 2;
+    return __fadd_rn(pairwise_sum<H>(x), pairwise_sum<N - H>(x + H));
+  }
+}
+
+// One row of a Kronecker matrix times x: fmaf, column ascending, or (PW)
+// rounded products summed pairwise.
+template <int COLS, bool PW>
+__device__ __forceinline__ float kron_row(const float* __restrict__ k,
+                                          const float (&x)[COLS]) {
+  if constexpr (PW) {
+    float pr[COLS];
+#pragma unroll
+    for (int c = 0; c < COLS; ++c) pr[c] = __fmul_rn(k[c], x[c]);
+    return pairwise_sum<COLS>(pr);
+  } else {
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < COLS; ++c) acc = fmaf(k[c], x[c], acc);
+    return acc;
+  }
+}
+
+constexpr int kKronThreads = 64;
+
+template <int M, bool PW>
+__global__ void __launch_bounds__(kKronThreads) k_pointset_kron(const float* __restrict__ rec,
+                                                                int trials,
+                                                                const double* __restrict__ pts,
+                                                                const double* __restrict__ ysum,
+                                                                double* __restrict__ err) {
+  constexpr int R = 3, A = M + R - 1, A2 = A * A, R2 = R * R, M2 = M * M;
+  constexpr int PP = A2 + 1;  // a thread's row of Hadamard products (padded)
+  using S = SweepShape<2, M, R>;
+  __shared__ float KG[A2 * R2], KB[A2 * A2], KA[M2 * A2];
+  __shared__ float sp[kKronThreads * PP];
+  __shared__ double ATd[M * A], Gd[A * R], BTd[A * A];
+  __shared__ double part[kKronThreads];
+  __shared__ int s_ok;
+  const int set = blockIdx.x, tid = threadIdx.x;
+  if (tid == 0) {
+    double a[A - 1];
+    for (int i = 0; i < A - 1; ++i) a[i] = pts[(int64_t)set * (A - 1) + i];
+    s_ok = build_matrices<double>(a, M, R, ATd, Gd, BTd) ? 1 : 0;
+  }
+  __syncthreads();
+  for (int e = tid; e < A2 * R2; e += kKronThreads) {
+    const int i = e / (A * R2), j = (e / R2) % A, k = (e % R2) / R, l = e % R;
+    KG[e] = __double2float_rn(__dmul_rn(Gd[i * R + k], Gd[j * R + l]));
+  }
+  for (int e = tid; e < A2 * A2; e += kKronThreads) {
+    const int i = e / (A * A2), j = (e / A2) % A, k = (e % A2) / A, l = e % A;
+    KB[e] = __double2float_rn(__dmul_rn(BTd[i * A + k], BTd[j * A + l]));
+  }
+  for (int e = tid; e < M2 * A2; e += kKronThreads) {
+    const int a = e / (M * A2), b = (e / A2) % M, i = (e % A2) / A, j = e % A;
+    KA[e] = __double2float_rn(__dmul_rn(ATd[a * A + i], ATd[b * A + j]));
+  }
+  __syncthreads();
+  float* my = sp + tid * PP;
+  double num = 0.0;
+  for (int t = tid; t < trials; t += kKronThreads) {
+    const float* rc = rec + (int64_t)t * S::REC;  // [g | d | hi(y) | lo(y)]
+    float g[R2], d[A2];
+#pragma unroll
+    for (int i = 0; i < R2; ++i) g[i] = rc[i];
+#pragma unroll
+    for (int i = 0; i < A2; ++i) d[i] = rc[R2 + i];
+#pragma unroll 1
+    for (int i = 0; i < A2; ++i)
+      my[i] = __fmul_rn(kron_row<R2, PW>(KG + i * R2, g), kron_row<A2, PW>(KB + i * A2, d));
+    float pv[A2];
+#pragma unroll
+    for (int i = 0; i < A2; ++i) pv[i] = my[i];
+    float e = 0.0f;
+#pragma unroll 1
+    for (int j = 0; j < M2; ++j) {
+      const float yj = kron_row<A2, PW>(KA + j * A2, pv);
+      e = __fadd_rn(e, abs_err(yj, rc[R2 + A2 + j], rc[R2 + A2 + M2 + j]));
+    }
+    num += (double)e;
+  }
+  part[tid] = num;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < kKronThreads; ++q) tot += part[q];
+    err[set] = s_ok ? tot / *ysum : (double)INFINITY;
+  }
+}
+
+typedef void (*KronFn)(const float*, int, const double*, const double*, double*);
+
+static KronFn kron_kernel(int m, bool pw) {
+  switch (m) {
+    case 2: return pw ? k_pointset_kron<2, true> : k_pointset_kron<2, false>;
+    case 3: return pw ? k_pointset_kron<3, true> : k_pointset_kron<3, false>;
+    case 4: return pw ? k_pointset_kron<4, true> : k_pointset_kron<4, false>;
+    case 5: return pw ? k_pointset_kron<5, true> : k_pointset_kron<5, false>;
+    case 6: return pw ? k_pointset_kron<6, true> : k_pointset_kron<6, false>;
+    default: return nullptr;
+  }
+}
+
+// points: [n_sets][alpha-1] sorted finite points (host); err_out host.
+int pointset_error_kron(int m, int r, const double* sorted, int n_sets, int trials,
+                        unsigned long long seed, int pairwise, double* err_out,
+                        cudaStream_t st) {
+  KronFn fn = r == 3 ? kron_kernel(m, pairwise != 0) : nullptr;
+  if (!fn) {
+    set_error("Kronecker-product form: 2D F(m x m, 3 x 3), m = 2..6");
+    return WINO_EUNSUPPORTED;
+  }
+  const int A = m + r - 1;
+  const int nb = sweep_prepare_blocks(trials);
+  const size_t rec_b = (size_t)trials * sweep_rec_width(2, m, r) * sizeof(float);
+  size_t o_part = (rec_b + 255) & ~(size_t)255;
+  size_t o_ysum = (o_part + (size_t)nb * 8 + 255) & ~(size_t)255;
+  size_t o_pts = (o_ysum + 8 + 255) & ~(size_t)255;
+  size_t o_err = (o_pts + (size_t)n_sets * (A - 1) * 8 + 255) & ~(size_t)255;
+  const size_t total = o_err + (size_t)n_sets * 8;
+  void* base = nullptr;
+  int rc = scratch_get(kScratchSweep, total, &base);
+  if (rc != WINO_OK) return rc;
+  char* b = (char*)base;
+  float* rec = (float*)b;
+  double* part = (double*)(b + o_part);
+  double* ysum = (double*)(b + o_ysum);
+  double* pts = (double*)(b + o_pts);
+  double* err = (double*)(b + o_err);
+  WINO_CUDA_TRY(cudaMemcpyAsync(pts, sorted, (size_t)n_sets * (A - 1) * 8,
+                                cudaMemcpyHostToDevice, st));
+  rc = sweep_prepare(rec, part, ysum, 2, m, r, trials, seed, st);
+  if (rc != WINO_OK) return rc;
+  {
+    ProfScope ps(kKSweepEval, st);
+    fn<<<n_sets, kKronThreads, 0, st>>>(rec, trials, pts, ysum, err);
+    note_launches(1);
+  }
+  WINO_CUDA_TRY(cudaGetLastError());
+  WINO_CUDA_TRY(cudaMemcpyAsync(err_out, err, (size_t)n_sets * 8, cudaMemcpyDeviceToHost, st));
+  WINO_CUDA_TRY(cudaStreamSynchronize(st));
+  return WINO_OK;
+}
+
 // Device FP64 construction for a batch of instances (the sweep's matrix
 // build, exposed for parity checks): one thread per c.
 __global__ void k_instance_matrices(const double* __restrict__ cg, int n_c, int m, int r,

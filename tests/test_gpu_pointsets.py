@@ -71,3 +71,25 @@ def test_paper_comparison(wino):
         ex = wino.wino_error_sweep(cg, [sizes[(dim, m)]], masks, 1000, seed=0)[0]
         best = np.nanmin(np.where(np.isinf(ex), np.nan, ex))
         assert best <= pn, (dim, n, best, pn)
+
+
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8])
+@pytest.mark.parametrize("pairwise", [False, True])
+def test_kron_form_vs_oracle(wino, orc, n, pairwise):
+    """The Kronecker-product 2D form (Sec. 7) on the GPU against the oracle."""
+    m = n - 2
+    sets = [COMPARISON_SETS[(2, n)] + [INF], PROPOSED_SETS[(2, n)] + [INF]]
+    got = wino.wino_pointset_error_kron(m, sets, 1000, seed=2, pairwise=pairwise)
+    want = orc.pointset_error_kron(m, 3, sets, 1000, 2, pairwise)
+    assert np.all(np.abs(got - want) <= REL * want), (got, want)
+
+
+def test_kron_form_larger_error_on_gpu(wino):
+    """Sec. 7's finding on the GPU: the Kronecker-product form and its pairwise
+    variant give larger errors than the nested form (2D n = 5..8)."""
+    for n in range(5, 9):
+        sets = [COMPARISON_SETS[(2, n)] + [INF], PROPOSED_SETS[(2, n)] + [INF]]
+        nested = wino.wino_pointset_error((2, n - 2, 3), sets, 1000)
+        kron = wino.wino_pointset_error_kron(n - 2, sets, 1000)
+        pw = wino.wino_pointset_error_kron(n - 2, sets, 1000, pairwise=True)
+        assert np.all(kron > nested) and np.all(pw > nested), (n, nested, kron, pw)
