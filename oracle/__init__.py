@@ -90,6 +90,17 @@ def lib():
             L.orc_pointset_error_kron.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_uint64, ctypes.c_int, dp]
             L.orc_pointset_error_kron.restype = ctypes.c_int
+            ip = ctypes.POINTER(ctypes.c_int)
+            L.orc_huffman_merges.argtypes = [dp, ctypes.c_int, ip, ip]
+            L.orc_huffman_merges.restype = ctypes.c_int
+            L.orc_huffman_dot_f32.argtypes = [fp, fp, ctypes.c_int]
+            L.orc_huffman_dot_f32.restype = ctypes.c_float
+            L.orc_tile_order.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, fp, fp, fp,
+                                         ctypes.c_int]
+            L.orc_tile_order.restype = ctypes.c_int
+            L.orc_pointset_error_order.argtypes = [ctypes.c_int] * 3 + [
+                dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, dp]
+            L.orc_pointset_error_order.restype = ctypes.c_int
             L.orc_round_bf16.argtypes = [ctypes.c_float]
             L.orc_round_bf16.restype = ctypes.c_float
             L.orc_round_fp16.argtypes = [ctypes.c_float]
@@ -271,6 +282,52 @@ def pointset_error_kron(m: int, r: int, point_sets, trials: int, seed: int,
     err = np.full(pts.shape[0], np.nan)
     rc = lib().orc_pointset_error_kron(m, r, _dp(pts), pts.shape[0], trials, seed, int(pairwise),
                                        _dp(err))
+    assert rc == 0
+    return err
+
+
+ORDERS = {"fma": 0, "huffman": 1, "huffman_mixed": 2}
+
+
+def huffman_merges(w):
+    """Huffman tree over the leaves with w[k] > 0: list of (first, second)
+    node ids per merge (leaf k = id k, merge s creates id len(w) + s)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    f = np.zeros(len(w), np.int32)
+    s = np.zeros(len(w), np.int32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    n = lib().orc_huffman_merges(_dp(w), len(w), f.ctypes.data_as(ip), s.ctypes.data_as(ip))
+    assert n >= 0
+    return [(int(f[i]), int(s[i])) for i in range(n)]
+
+
+def huffman_dot_f32(c, x) -> np.float32:
+    """sum c[k] x[k] in FP32 along the Huffman tree of |c|."""
+    c = np.ascontiguousarray(c, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    assert c.shape == x.shape and c.ndim == 1
+    return np.float32(lib().orc_huffman_dot_f32(_fp(c), _fp(x), len(c)))
+
+
+def tile_order(dim: int, points, m: int, r: int, g, d, order: str):
+    """One tile in a summation-order variant ('huffman', 'huffman_mixed')."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float32).ravel()
+    d = np.ascontiguousarray(d, dtype=np.float32).ravel()
+    y = np.zeros(m if dim == 1 else m * m, np.float32)
+    rc = lib().orc_tile_order(dim, _dp(pts), m, r, _fp(g), _fp(d), _fp(y), ORDERS[order])
+    assert rc == 0, rc
+    return y if dim == 1 else y.reshape(m, m)
+
+
+def pointset_error_order(dim: int, m: int, r: int, point_sets, trials: int, seed: int,
+                         order: str):
+    """The sweep metric for explicit sets in one of the summation orders."""
+    pts = np.ascontiguousarray(point_sets, dtype=np.float64)
+    assert pts.ndim == 2 and pts.shape[1] == m + r - 1
+    err = np.full(pts.shape[0], np.nan)
+    rc = lib().orc_pointset_error_order(dim, m, r, _dp(pts), pts.shape[0], trials, seed,
+                                        ORDERS[order], _dp(err))
     assert rc == 0
     return err
 

@@ -808,6 +808,241 @@ int orc_pointset_error_kron(int m, int r, const double* points, int n_sets, int 
   return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Summation-order variants of the single tile (Sec. 5): the Huffman        */
+/* evaluation order of Barabasz et al. that the paper's error tables use,   */
+/* alone in FP32, and with the transforms in FP64 and the Hadamard product  */
+/* in FP32 ("mixed precision").  The paper names both and defines neither;  */
+/* the reading taken here:                                                  */
+/*  - every output of a transform is one dot product sum_k c_k x_k, c a row */
+/*    of G, B^T or A^T (a 2D transform is two such passes, in the order of  */
+/*    orc_tile2d_f32);                                                      */
+/*  - terms with c_k == 0 are left out; the others are the rounded products */
+/*    c_k * x_k (no fused multiply-add);                                    */
+/*  - the terms are added along a Huffman tree with leaf weights |c_k| (the */
+/*    FP32 entry): the two live nodes of least weight are replaced by their */
+/*    sum, whose weight is the FP64 sum of theirs, until one node is left;  */
+/*    ties go to the node created first (leaves in column order, then the   */
+/*    merged nodes in order of creation);                                   */
+/*  - ORC_ORDER_HUFFMAN: products and sums in FP32.                         */
+/*    ORC_ORDER_HUFFMAN_MIXED: products and sums in FP64 on the FP64 matrix */
+/*    entries and the widened inputs, with the same trees; U and V rounded  */
+/*    to FP32, P = U .* V in FP32, the output transform in FP64 on P, and Y */
+/*    rounded to FP32 once at the end.                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Merge list of the Huffman tree over the leaves k < n with w[k] > 0: merge
+ * s joins node ids first[s] and second[s] (leaf k has id k, merge s creates
+ * id n + s).  Returns the number of merges (-1 when no weight is positive)
+ * and the root's id in *root. */
+static int huffman_merges(const double* w, int n, int* first, int* second, int* root) {
+  double wt[2 * ORC_MAX_ALPHA];
+  int live[2 * ORC_MAX_ALPHA];
+  int n_live = 0, nodes = n, s = 0, last = -1;
+  for (int k = 0; k < n; ++k) {
+    wt[k] = w[k];
+    live[k] = w[k] > 0.0;
+    if (live[k]) { ++n_live; last = k; }
+  }
+  if (n_live == 0) return -1;
+  while (n_live > 1) {
+    int f = -1, g = -1;
+    for (int id = 0; id < nodes; ++id) /* least weight, earliest id on ties */
+      if (live[id] && (f < 0 || wt[id] < wt[f])) f = id;
+    for (int id = 0; id < nodes; ++id) /* the same among the rest */
+      if (live[id] && id != f && (g < 0 || wt[id] < wt[g])) g = id;
+    first[s] = f;
+    second[s] = g;
+    wt[nodes] = wt[f] + wt[g];
+    live[nodes] = 1;
+    live[f] = live[g] = 0;
+    ++nodes;
+    ++s;
+    --n_live;
+  }
+  *root = s == 0 ? last : nodes - 1;
+  return s;
+}
+
+int orc_huffman_merges(const double* w, int n, int* first, int* second) {
+  int root;
+  if (n < 1 || n > ORC_MAX_ALPHA) return -1;
+  return huffman_merges(w, n, first, second, &root);
+}
+
+/* sum_k c[k] x[k] in FP32 along the Huffman tree of |c| */
+static float huff_dot_f32(const float* c, const float* x, int n) {
+  double w[ORC_MAX_ALPHA];
+  int f[ORC_MAX_ALPHA], g[ORC_MAX_ALPHA], root;
+  for (int k = 0; k < n; ++k) w[k] = fabs((double)c[k]);
+  const int ns = huffman_merges(w, n, f, g, &root);
+  if (ns < 0) return 0.0f;
+  float v[2 * ORC_MAX_ALPHA];
+  for (int k = 0; k < n; ++k) v[k] = c[k] * x[k];
+  for (int s = 0; s < ns; ++s) v[n + s] = v[f[s]] + v[g[s]];
+  return v[root];
+}
+
+/* the same in FP64 (coefficients FP64, tree of the |FP32-rounded| entries) */
+static double huff_dot_f64(const double* c, const double* x, int n) {
+  double w[ORC_MAX_ALPHA];
+  int f[ORC_MAX_ALPHA], g[ORC_MAX_ALPHA], root;
+  for (int k = 0; k < n; ++k) w[k] = fabs((double)(float)c[k]);
+  const int ns = huffman_merges(w, n, f, g, &root);
+  if (ns < 0) return 0.0;
+  double v[2 * ORC_MAX_ALPHA];
+  for (int k = 0; k < n; ++k) v[k] = c[k] * x[k];
+  for (int s = 0; s < ns; ++s) v[n + s] = v[f[s]] + v[g[s]];
+  return v[root];
+}
+
+float orc_huffman_dot_f32(const float* c, const float* x, int n) {
+  if (n < 1 || n > ORC_MAX_ALPHA) return NAN;
+  return huff_dot_f32(c, x, n);
+}
+
+typedef struct {
+  int m, r, A;
+  double ATd[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Gd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  double BTd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float AT[ORC_MAX_ALPHA * ORC_MAX_ALPHA], G[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float BT[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+} ord_mats;
+
+static int build_ord(const double* points, int m, int r, ord_mats* M) {
+  const int st = orc_make_matrices(points, m, r, M->ATd, M->Gd, M->BTd);
+  if (st < 0) return st;
+  M->m = m; M->r = r; M->A = st;
+  for (int i = 0; i < m * st; ++i) M->AT[i] = (float)M->ATd[i];
+  for (int i = 0; i < st * r; ++i) M->G[i] = (float)M->Gd[i];
+  for (int i = 0; i < st * st; ++i) M->BT[i] = (float)M->BTd[i];
+  return 0;
+}
+
+/* One tile in ORC_ORDER_HUFFMAN (mixed = 0) or ORC_ORDER_HUFFMAN_MIXED. */
+static void tile_order(const ord_mats* M, int dim, const float* g, const float* d, float* y,
+                       int mixed) {
+  const int m = M->m, r = M->r, A = M->A;
+  float xs[ORC_MAX_ALPHA];
+  double xd[ORC_MAX_ALPHA];
+  if (dim == 1) {
+    float p[ORC_MAX_ALPHA];
+    for (int i = 0; i < A; ++i) {
+      float u, v;
+      if (mixed) {
+        for (int k = 0; k < r; ++k) xd[k] = g[k];
+        u = (float)huff_dot_f64(&M->Gd[i * r], xd, r);
+        for (int l = 0; l < A; ++l) xd[l] = d[l];
+        v = (float)huff_dot_f64(&M->BTd[i * A], xd, A);
+      } else {
+        u = huff_dot_f32(&M->G[i * r], g, r);
+        v = huff_dot_f32(&M->BT[i * A], d, A);
+      }
+      p[i] = u * v;
+    }
+    for (int j = 0; j < m; ++j) {
+      if (mixed) {
+        for (int i = 0; i < A; ++i) xd[i] = p[i];
+        y[j] = (float)huff_dot_f64(&M->ATd[j * A], xd, A);
+      } else {
+        y[j] = huff_dot_f32(&M->AT[j * A], p, A);
+      }
+    }
+    return;
+  }
+  /* 2D: W = G g, U = W G^T, T = B^T d, V = T B, P = U .* V, Z = A^T P,
+   * Y = Z A; each entry one Huffman dot product over a matrix row. */
+  float Wf[ORC_MAX_ALPHA * 5], U[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float Tf[ORC_MAX_ALPHA * ORC_MAX_ALPHA], V[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  float P[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Zf[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  double Wd[ORC_MAX_ALPHA * 5], Td[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  double Zd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int i = 0; i < A; ++i) /* W[i][k] = sum_l G[i][l] g[l][k] */
+    for (int k = 0; k < r; ++k) {
+      if (mixed) {
+        for (int l = 0; l < r; ++l) xd[l] = g[l * r + k];
+        Wd[i * r + k] = huff_dot_f64(&M->Gd[i * r], xd, r);
+      } else {
+        for (int l = 0; l < r; ++l) xs[l] = g[l * r + k];
+        Wf[i * r + k] = huff_dot_f32(&M->G[i * r], xs, r);
+      }
+    }
+  for (int i = 0; i < A; ++i) /* U[i][j] = sum_k W[i][k] G[j][k] */
+    for (int j = 0; j < A; ++j)
+      U[i * A + j] = mixed ? (float)huff_dot_f64(&M->Gd[j * r], &Wd[i * r], r)
+                           : huff_dot_f32(&M->G[j * r], &Wf[i * r], r);
+  for (int i = 0; i < A; ++i) /* T[i][l] = sum_k BT[i][k] d[k][l] */
+    for (int l = 0; l < A; ++l) {
+      if (mixed) {
+        for (int k = 0; k < A; ++k) xd[k] = d[k * A + l];
+        Td[i * A + l] = huff_dot_f64(&M->BTd[i * A], xd, A);
+      } else {
+        for (int k = 0; k < A; ++k) xs[k] = d[k * A + l];
+        Tf[i * A + l] = huff_dot_f32(&M->BT[i * A], xs, A);
+      }
+    }
+  for (int i = 0; i < A; ++i) /* V[i][j] = sum_l T[i][l] BT[j][l] */
+    for (int j = 0; j < A; ++j)
+      V[i * A + j] = mixed ? (float)huff_dot_f64(&M->BTd[j * A], &Td[i * A], A)
+                           : huff_dot_f32(&M->BT[j * A], &Tf[i * A], A);
+  for (int i = 0; i < A * A; ++i) P[i] = U[i] * V[i]; /* Hadamard, FP32 */
+  for (int a = 0; a < m; ++a) /* Z[a][j] = sum_i AT[a][i] P[i][j] */
+    for (int j = 0; j < A; ++j) {
+      if (mixed) {
+        for (int i = 0; i < A; ++i) xd[i] = P[i * A + j];
+        Zd[a * A + j] = huff_dot_f64(&M->ATd[a * A], xd, A);
+      } else {
+        for (int i = 0; i < A; ++i) xs[i] = P[i * A + j];
+        Zf[a * A + j] = huff_dot_f32(&M->AT[a * A], xs, A);
+      }
+    }
+  for (int a = 0; a < m; ++a) /* Y[a][b] = sum_j Z[a][j] AT[b][j] */
+    for (int b = 0; b < m; ++b)
+      y[a * m + b] = mixed ? (float)huff_dot_f64(&M->ATd[b * A], &Zd[a * A], A)
+                           : huff_dot_f32(&M->AT[b * A], &Zf[a * A], A);
+}
+
+int orc_tile_order(int dim, const double* points, int m, int r, const float* g,
+                   const float* d, float* y, int order) {
+  if (dim < 1 || dim > 2 || r > 5 || order < ORC_ORDER_HUFFMAN || order > ORC_ORDER_HUFFMAN_MIXED)
+    return -1;
+  ord_mats M;
+  const int st = build_ord(points, m, r, &M);
+  if (st < 0) return st;
+  tile_order(&M, dim, g, d, y, order == ORC_ORDER_HUFFMAN_MIXED);
+  return 0;
+}
+
+int orc_pointset_error_order(int dim, int m, int r, const double* points, int n_sets,
+                             int trials, uint64_t seed, int order, double* err_out) {
+  if (order == ORC_ORDER_FMA)
+    return orc_pointset_error(dim, m, r, points, n_sets, trials, seed, err_out);
+  const int A = m + r - 1;
+  if (dim < 1 || dim > 2 || A < 2 || A > ORC_MAX_ALPHA || r > 5 || n_sets < 0 || trials < 1 ||
+      order < ORC_ORDER_HUFFMAN || order > ORC_ORDER_HUFFMAN_MIXED)
+    return -1;
+  orc_size s = {dim, m, r, 1.0};
+  size_data sd;
+  memset(&sd, 0, sizeof(sd));
+  int rc = build_size_data(&s, trials, seed, &sd);
+  for (int q = 0; q < n_sets && rc == 0; ++q) {
+    ord_mats M;
+    const int st = build_ord(points + (size_t)q * A, m, r, &M);
+    if (st == -2) { err_out[q] = INFINITY; continue; }
+    if (st < 0) { err_out[q] = NAN; continue; }
+    double num = 0.0;
+    float yh[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+    for (int t = 0; t < trials; ++t) {
+      tile_order(&M, dim, sd.g + (size_t)t * sd.nin_g, sd.d + (size_t)t * sd.nin_d, yh,
+                 order == ORC_ORDER_HUFFMAN_MIXED);
+      for (int j = 0; j < sd.nout; ++j) num += fabs((double)yh[j] - sd.y[(size_t)t * sd.nout + j]);
+    }
+    err_out[q] = num / sd.ysum;
+  }
+  free(sd.g); free(sd.d); free(sd.y);
+  return rc;
+}
+
 double orc_direct_error(int dim, int m, int r, int trials, uint64_t seed) {
   orc_size s = {dim, m, r, 1.0};
   size_data sd;

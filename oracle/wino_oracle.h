@@ -125,6 +125,39 @@ int orc_tile2d_kron(const double* points, int m, int r, const float* g, const fl
 int orc_pointset_error_kron(int m, int r, const double* points, int n_sets, int trials,
                             uint64_t seed, int pairwise, double* err_out);
 
+/* Summation-order variants (Sec. 5; the order the paper's tables use, from
+ * Barabasz et al., which the paper does not define -- the reading is stated
+ * at the definitions in the .c file):
+ *   ORC_ORDER_FMA            the order of orc_tile1d_f32 / orc_tile2d_f32;
+ *   ORC_ORDER_HUFFMAN        every transform dot product summed in FP32
+ *                            along the Huffman tree of its |coefficients|;
+ *   ORC_ORDER_HUFFMAN_MIXED  the same trees, transforms in FP64, Hadamard
+ *                            product in FP32.
+ * orc_huffman_merges: the tree over the leaves k with w[k] > 0 as a merge
+ * list (leaf k = id k, merge s creates id n + s); returns the merge count or
+ * -1.  Pinned by: optimal weighted path length against brute force, the
+ * tie rule on equal weights.
+ * orc_huffman_dot_f32: sum c[k] x[k] along that tree, FP32.  Pinned by: a
+ * worked example whose FP32 result differs from every sequential order,
+ * and sequential ascending-magnitude summation when every weight exceeds
+ * the sum of the smaller ones.
+ * orc_tile_order: one tile (layout of orc_tile2d_kron; 1D: g r, d alpha,
+ * y m) in ORC_ORDER_HUFFMAN or ORC_ORDER_HUFFMAN_MIXED; returns 0 or -1 /
+ * -2 like orc_make_matrices.  Pinned by: exact correlation on inputs where
+ * no operation rounds (both orders); MIXED equals the rational transforms
+ * of the FP64 matrices rounded to FP32 at U, V, P and Y.
+ * orc_pointset_error_order: the sweep metric of orc_pointset_error in one of
+ * the three orders.                                                        */
+#define ORC_ORDER_FMA 0
+#define ORC_ORDER_HUFFMAN 1
+#define ORC_ORDER_HUFFMAN_MIXED 2
+int orc_huffman_merges(const double* w, int n, int* first, int* second);
+float orc_huffman_dot_f32(const float* c, const float* x, int n);
+int orc_tile_order(int dim, const double* points, int m, int r, const float* g,
+                   const float* d, float* y, int order);
+int orc_pointset_error_order(int dim, int m, int r, const double* points, int n_sets,
+                             int trials, uint64_t seed, int order, double* err_out);
+
 /* The same metric for FP32 direct correlation (the "n = 0" row).         */
 double orc_direct_error(int dim, int m, int r, int trials, uint64_t seed);
 
