@@ -186,6 +186,47 @@ int wino_pointset_error(int dim, int m, int r, const double* points, int n_sets,
                         int trials, unsigned long long seed, double* err_out,
                         void* cuda_stream);
 
+/* Summation-order variants of the sweep (Sec. 5: the paper's tables use the
+ * Huffman evaluation order of Barabasz et al., and its curves also show that
+ * order with the transforms in FP64).  The paper defines neither; the reading
+ * implemented:
+ *   WINO_ORDER_FMA           the order of wino_error_sweep (fmaf, inner
+ *                            index ascending);
+ *   WINO_ORDER_HUFFMAN       every output of a transform (one dot product
+ *                            over a row of G, B^T or A^T; a 2D transform is
+ *                            two passes, left factor first) is the sum of
+ *                            its non-zero terms, each a rounded FP32
+ *                            product, added along the Huffman tree of the
+ *                            terms' |FP32 coefficients|: the two live nodes
+ *                            of least weight are replaced by their sum, of
+ *                            weight the FP64 sum of theirs; ties go to the
+ *                            node created first (leaves in column order,
+ *                            then merged nodes in creation order);
+ *   WINO_ORDER_HUFFMAN_MIXED the same trees with the FP64 matrices, FP64
+ *                            products and sums, the FP32 inputs widened; U
+ *                            and V rounded to FP32, the Hadamard product in
+ *                            FP32, the output transform in FP64 and Y
+ *                            rounded to FP32 once.
+ * Per-trial and per-chunk summation of the errors as in wino_error_sweep.  */
+typedef enum {
+  WINO_ORDER_FMA = 0,
+  WINO_ORDER_HUFFMAN = 1,
+  WINO_ORDER_HUFFMAN_MIXED = 2
+} wino_order;
+
+/* wino_error_sweep in one of the summation orders; order WINO_ORDER_FMA is
+ * wino_error_sweep itself.  Other order values: WINO_EINVAL.             */
+int wino_error_sweep_order(const double* c_grid, int n_c,
+                           const wino_size* sizes, int n_sizes,
+                           const unsigned char* subsets, int n_subsets,
+                           int trials, unsigned long long seed, int order,
+                           double* err_out, void* cuda_stream);
+
+/* wino_pointset_error in one of the summation orders.                     */
+int wino_pointset_error_order(int dim, int m, int r, const double* points,
+                              int n_sets, int trials, unsigned long long seed,
+                              int order, double* err_out, void* cuda_stream);
+
 /* The same metric for the Kronecker-product form of the 2D tile (Sec. 7):
  *   u = (G (x) G) vec(g), v = (B^T (x) B^T) vec(d), y = (A^T (x) A^T)(u .* v)
  * (row-major vec), Kronecker entries = FP64 products of the FP64 matrix
@@ -352,8 +393,8 @@ void wino_mlp_destroy(void* mlp);
  * graph capture).  wino_profile_read sums, then forgets, the recorded
  * launches of one kernel ("filter_transform", "input_transform",
  * "wino_gemm", "output_transform", "fused_layer", "tc_gemm", "tc_transform",
- * "sweep_eval", "sweep_prepare", "direct_f64", "error_stats", "mlp"); it
- * waits for the recorded events.                                           */
+ * "sweep_eval", "sweep_prepare", "direct_f64", "error_stats", "mlp",
+ * "sweep_order"); it waits for the recorded events.                       */
 int wino_profile_enable(int on);
 int wino_profile_read(const char* kernel, double* total_ms, int* launches);
 

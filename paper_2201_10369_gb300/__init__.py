@@ -44,6 +44,9 @@ class WinoInstance(ctypes.Structure):
 
 
 WINO_SWEEP_AUTO, WINO_SWEEP_PERSISTENT, WINO_SWEEP_PERSISTENT3, WINO_SWEEP_PER_SIZE = 0, 1, 2, 3
+WINO_ORDER_FMA, WINO_ORDER_HUFFMAN, WINO_ORDER_HUFFMAN_MIXED = 0, 1, 2
+ORDERS = {"fma": WINO_ORDER_FMA, "huffman": WINO_ORDER_HUFFMAN,
+          "huffman_mixed": WINO_ORDER_HUFFMAN_MIXED}
 
 _lib = None
 _lock = threading.Lock()
@@ -111,6 +114,13 @@ def _declare(L):
     L.wino_device_ok.restype = _i
     L.wino_pointset_error.argtypes = [_i, _i, _i, _DP, _i, _i, ctypes.c_ulonglong, _DP, _vp]
     L.wino_pointset_error.restype = _i
+    L.wino_pointset_error_order.argtypes = [_i, _i, _i, _DP, _i, _i, ctypes.c_ulonglong, _i, _DP,
+                                            _vp]
+    L.wino_pointset_error_order.restype = _i
+    L.wino_error_sweep_order.argtypes = [_DP, _i, ctypes.POINTER(WinoSize), _i,
+                                         ctypes.POINTER(ctypes.c_ubyte), _i, _i,
+                                         ctypes.c_ulonglong, _i, _DP, _vp]
+    L.wino_error_sweep_order.restype = _i
     L.wino_pointset_error_kron.argtypes = [_i, _i, _DP, _i, _i, ctypes.c_ulonglong, _i, _DP,
                                            _vp]
     L.wino_pointset_error_kron.restype = _i
@@ -282,17 +292,24 @@ def wino_error_stats(yhat, y64, stream=None):
     return tuple(float(v) for v in out)
 
 
-def wino_error_sweep(c_grid, sizes, subsets, trials: int, seed: int = 0, stream=None):
-    """err[n_sizes][n_subsets][n_c] (host FP64); sizes = [(dim, m, r, d)]."""
+def wino_error_sweep(c_grid, sizes, subsets, trials: int, seed: int = 0, stream=None,
+                     order: str = "fma"):
+    """err[n_sizes][n_subsets][n_c] (host FP64); sizes = [(dim, m, r, d)].
+    ``order``: 'fma' (wino_error_sweep), 'huffman' or 'huffman_mixed'
+    (wino_error_sweep_order)."""
     L = load()
     cg = np.ascontiguousarray(c_grid, dtype=np.float64)
     sz = (WinoSize * len(sizes))(*[WinoSize(int(a), int(b), int(c), float(d))
                                    for a, b, c, d in sizes])
     mk = np.ascontiguousarray(subsets, dtype=np.uint8)
     err = np.empty((len(sizes), mk.size, cg.size))
-    _check(L.wino_error_sweep(cg.ctypes.data_as(_DP), cg.size, sz, len(sizes),
-                              mk.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), mk.size, trials,
-                              seed, err.ctypes.data_as(_DP), _stream(stream)))
+    args = (cg.ctypes.data_as(_DP), cg.size, sz, len(sizes),
+            mk.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), mk.size, trials, seed)
+    if order == "fma":
+        _check(L.wino_error_sweep(*args, err.ctypes.data_as(_DP), _stream(stream)))
+    else:
+        _check(L.wino_error_sweep_order(*args, ORDERS[order], err.ctypes.data_as(_DP),
+                                        _stream(stream)))
     return err
 
 
@@ -661,16 +678,23 @@ def guided_sweep(model, sizes, masks, c_grid, trials: int, seed: int = 0, top: i
         gs.close()
 
 
-def wino_pointset_error(size, point_sets, trials: int, seed: int = 0, stream=None) -> np.ndarray:
+def wino_pointset_error(size, point_sets, trials: int, seed: int = 0, stream=None,
+                        order: str = "fma") -> np.ndarray:
     """The sweep metric of explicit point sets on the sweep's trials of size
-    (dim, m, r[, d]): each set m + r - 1 values with one +inf, any order."""
+    (dim, m, r[, d]): each set m + r - 1 values with one +inf, any order.
+    ``order`` as for wino_error_sweep."""
     dim, m, r = size[0], size[1], size[2]
     pts = np.ascontiguousarray(point_sets, dtype=np.float64)
     if pts.ndim != 2 or pts.shape[1] != m + r - 1:
         raise ValueError("each point set needs m + r - 1 values")
     err = np.empty(pts.shape[0])
-    _check(load().wino_pointset_error(dim, m, r, pts.ctypes.data_as(_DP), pts.shape[0], trials,
-                                      seed, err.ctypes.data_as(_DP), _stream(stream)))
+    L = load()
+    args = (dim, m, r, pts.ctypes.data_as(_DP), pts.shape[0], trials, seed)
+    if order == "fma":
+        _check(L.wino_pointset_error(*args, err.ctypes.data_as(_DP), _stream(stream)))
+    else:
+        _check(L.wino_pointset_error_order(*args, ORDERS[order], err.ctypes.data_as(_DP),
+                                           _stream(stream)))
     return err
 
 

@@ -335,6 +335,18 @@ int wino_error_stats(const void* yhat_f32, const void* y_f64, int64_t n, double*
 int wino_error_sweep(const double* c_grid, int n_c, const wino_size* sizes, int n_sizes,
                      const unsigned char* subsets, int n_subsets, int trials,
                      unsigned long long seed, double* err_out, void* cuda_stream) {
+  return wino_error_sweep_order(c_grid, n_c, sizes, n_sizes, subsets, n_subsets, trials, seed,
+                                WINO_ORDER_FMA, err_out, cuda_stream);
+}
+
+int wino_error_sweep_order(const double* c_grid, int n_c, const wino_size* sizes, int n_sizes,
+                           const unsigned char* subsets, int n_subsets, int trials,
+                           unsigned long long seed, int order, double* err_out,
+                           void* cuda_stream) {
+  if (order < WINO_ORDER_FMA || order > WINO_ORDER_HUFFMAN_MIXED) {
+    set_error("order must be WINO_ORDER_FMA, WINO_ORDER_HUFFMAN or WINO_ORDER_HUFFMAN_MIXED");
+    return WINO_EINVAL;
+  }
   if (!c_grid || !sizes || !subsets || !err_out || n_c < 1 || n_sizes < 1 || n_subsets < 1 ||
       trials < 1 || trials > (1 << 20)) {
     set_error("invalid sweep arguments (counts must be >= 1, trials <= 2^20)");
@@ -356,12 +368,23 @@ int wino_error_sweep(const double* c_grid, int n_c, const wino_size* sizes, int 
   int st = check_device();
   if (st != WINO_OK) return st;
   return error_sweep(c_grid, n_c, reinterpret_cast<const SweepSize*>(sizes), n_sizes, subsets,
-                     n_subsets, trials, seed, err_out, (cudaStream_t)cuda_stream);
+                     n_subsets, trials, seed, order, err_out, (cudaStream_t)cuda_stream);
 }
 
 int wino_pointset_error(int dim, int m, int r, const double* points, int n_sets, int trials,
                         unsigned long long seed, double* err_out, void* cuda_stream) {
+  return wino_pointset_error_order(dim, m, r, points, n_sets, trials, seed, WINO_ORDER_FMA,
+                                   err_out, cuda_stream);
+}
+
+int wino_pointset_error_order(int dim, int m, int r, const double* points, int n_sets,
+                              int trials, unsigned long long seed, int order, double* err_out,
+                              void* cuda_stream) {
   const int alpha = m + r - 1;
+  if (order < WINO_ORDER_FMA || order > WINO_ORDER_HUFFMAN_MIXED) {
+    set_error("order must be WINO_ORDER_FMA, WINO_ORDER_HUFFMAN or WINO_ORDER_HUFFMAN_MIXED");
+    return WINO_EINVAL;
+  }
   if (!points || !err_out || n_sets < 1 || trials < 1 || trials > (1 << 20) ||
       (dim != 1 && dim != 2) || m < 1 || r < 1 || alpha < 3 || alpha > 10) {
     set_error("invalid point-set sweep arguments");
@@ -376,7 +399,7 @@ int wino_pointset_error(int dim, int m, int r, const double* points, int n_sets,
   }
   int st = check_device();
   if (st != WINO_OK) return st;
-  return pointset_error(dim, m, r, sorted.data(), n_sets, trials, seed, err_out,
+  return pointset_error(dim, m, r, sorted.data(), n_sets, trials, seed, order, err_out,
                         (cudaStream_t)cuda_stream);
 }
 

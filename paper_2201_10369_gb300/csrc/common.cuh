@@ -83,7 +83,7 @@ void note_launches(int n);
 // before the launch, destroy right after it.
 enum KernelId {
   kKFilter = 0, kKInput, kKGemm, kKOutput, kKFused, kKTcGemm, kKTcTransform, kKSweepEval,
-  kKSweepPrep, kKDirect, kKStats, kKMlp, kNumKernelIds
+  kKSweepPrep, kKDirect, kKStats, kKMlp, kKSweepOrder, kNumKernelIds
 };
 class ProfScope {
  public:
@@ -123,9 +123,9 @@ struct SweepSize {
 };
 int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_sizes,
                 const unsigned char* subsets, int n_subsets, int trials, unsigned long long seed,
-                double* err_out, cudaStream_t st);
+                int order, double* err_out, cudaStream_t st);
 int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int trials,
-                   unsigned long long seed, double* err_out, cudaStream_t st);
+                   unsigned long long seed, int order, double* err_out, cudaStream_t st);
 int pointset_error_kron(int m, int r, const double* sorted, int n_sets, int trials,
                         unsigned long long seed, int pairwise, double* err_out, cudaStream_t st);
 int instance_matrices(const double* c_grid, int n_c, const SweepSize& s, unsigned mask,

@@ -17,7 +17,7 @@ namespace wino {
 static const char* kKernelNames[kNumKernelIds] = {
     "filter_transform", "input_transform", "wino_gemm",  "output_transform", "fused_layer",
     "tc_gemm",          "tc_transform",    "sweep_eval", "sweep_prepare",    "direct_f64",
-    "error_stats",      "mlp"};
+    "error_stats",      "mlp",             "sweep_order"};
 
 namespace {
 struct Rec {

@@ -128,12 +128,6 @@ int sweep_prepare(float* rec, double* partial, double* ysum, int dim, int m, int
   return WINO_OK;
 }
 
-struct MaskList {
-  unsigned char mask[256];
-  short q[256];  // index of the mask in the caller's subset list
-  int n;
-};
-
 // One warp per (valid mask, block of 32 c values, chunk group); lanes own
 // instances.  split == 1: each lane runs every trial and writes its error to
 // err.  split > 1: the trial chunks are spread over `split` warps of ch_per
@@ -164,9 +158,6 @@ __global__ void __launch_bounds__(128) k_sweep_eval(const float* __restrict__ re
   lane_eval<DIM, M, R>(rec, trials, masks.mask[qv], c, d, ch0, ch1, *ysum, split > 1,
                        split == 1 ? err + o : part + o, n_out, active);
 }
-
-typedef void (*EvalFn)(const float*, int, const double*, int, double, const MaskList,
-                       const double*, double*, int, int, double*, int64_t);
 
 // err[i] = (sum over chunks ascending of part[ch * stride + i]) / ysum of the
 // instance's size.
@@ -234,12 +225,13 @@ static MaskList valid_masks(const SweepSize& s, const unsigned char* subsets, in
 
 int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_sizes,
                 const unsigned char* subsets, int n_subsets, int trials, unsigned long long seed,
-                double* err_out, cudaStream_t st) {
+                int order, double* err_out, cudaStream_t st) {
   std::vector<size_t> rec_off(n_sizes);
   size_t rec_total = 0;
   const int nb_prep = sweep_prepare_blocks(trials);
   for (int s = 0; s < n_sizes; ++s) {
-    if (!eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)) {
+    if (!(order == 0 ? eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)
+                     : order_sweep_kernel(order, sizes[s].dim, sizes[s].m, sizes[s].r))) {
       set_error("sweep size not compiled: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6");
       return WINO_EUNSUPPORTED;
     }
@@ -298,10 +290,11 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
     const int64_t warps = (int64_t)ml[s].n * nblk * (split[s] > 1 ? sp : 1);
     const int warps_per_block = 4;
     const unsigned grid = (unsigned)((warps + warps_per_block - 1) / warps_per_block);
-    EvalFn fn = eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r);
+    EvalFn fn = order == 0 ? eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)
+                           : order_sweep_kernel(order, sizes[s].dim, sizes[s].m, sizes[s].r);
     double* es = err + (size_t)s * n_out;
     {
-      ProfScope ps(kKSweepEval, st);
+      ProfScope ps(order == 0 ? kKSweepEval : kKSweepOrder, st);
       fn<<<grid, 32 * warps_per_block, 0, st>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
                                                  ml[s], ysum + s, es, split[s] > 1 ? sp : 1,
                                                  ch_per, chunk, n_out);
@@ -349,8 +342,6 @@ __global__ void __launch_bounds__(128) k_pointset_eval(const float* __restrict__
                             0, active);
 }
 
-typedef void (*PointsetFn)(const float*, int, const double*, int, const double*, double*);
-
 static PointsetFn pointset_kernel(int dim, int m, int r) {
 #define WINO_PSET_CASE(I, D, MM, RR) \
   if (dim == D && m == MM && r == RR) return k_pointset_eval<D, MM, RR>;
@@ -361,8 +352,8 @@ static PointsetFn pointset_kernel(int dim, int m, int r) {
 
 // points: [n_sets][alpha-1] sorted finite points (host); err_out host.
 int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int trials,
-                   unsigned long long seed, double* err_out, cudaStream_t st) {
-  PointsetFn fn = pointset_kernel(dim, m, r);
+                   unsigned long long seed, int order, double* err_out, cudaStream_t st) {
+  PointsetFn fn = order == 0 ? pointset_kernel(dim, m, r) : order_pointset_kernel(order, dim, m, r);
   if (!fn) {
     set_error("point-set sizes: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6");
     return WINO_EUNSUPPORTED;
@@ -389,7 +380,7 @@ int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int 
   rc = sweep_prepare(rec, part, ysum, dim, m, r, trials, seed, st);
   if (rc != WINO_OK) return rc;
   {
-    ProfScope ps(kKSweepEval, st);
+    ProfScope ps(order == 0 ? kKSweepEval : kKSweepOrder, st);
     fn<<<(n_sets + 127) / 128, 128, 0, st>>>(rec, trials, pts, n_sets, ysum, err);
     note_launches(1);
   }

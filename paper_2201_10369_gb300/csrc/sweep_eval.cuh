@@ -167,46 +167,45 @@ __host__ __device__ constexpr int trial_chunks(int trials) {
   return (trials + kTrialChunk - 1) / kTrialChunk;
 }
 
-// FP64 sum over trials [t0, t1) of the per-trial FP32 L1 error.
-template <int DIM, int M, int R>
-__device__ __forceinline__ double chunk_error(const Mats<M, R>& Mx, const float* __restrict__ rec,
-                                              int t0, int t1) {
-  using S = SweepShape<DIM, M, R>;
+// FP64 sum over trials [t0, t1) of the per-trial FP32 L1 error; `ev(buf)`
+// returns one trial's error from its record (Ev::REC floats).
+template <class Ev>
+__device__ __forceinline__ double chunk_error_ev(const Ev& ev, const float* __restrict__ rec,
+                                                 int t0, int t1) {
+  constexpr int REC = Ev::REC;
   double num = 0.0;
   const float4* r4 = reinterpret_cast<const float4*>(rec);
   for (int t = t0; t < t1; ++t) {
-    float buf[S::REC];
+    float buf[REC];
 #pragma unroll
-    for (int q = 0; q < S::REC / 4; ++q) {
-      const float4 v = __ldg(r4 + (int64_t)t * (S::REC / 4) + q);
+    for (int q = 0; q < REC / 4; ++q) {
+      const float4 v = __ldg(r4 + (int64_t)t * (REC / 4) + q);
       buf[4 * q + 0] = v.x;
       buf[4 * q + 1] = v.y;
       buf[4 * q + 2] = v.z;
       buf[4 * q + 3] = v.w;
     }
-    const float e = (DIM == 1) ? tile_err_1d<M, R>(Mx, buf) : tile_err_2d<M, R>(Mx, buf);
-    num += (double)e;
+    num += (double)ev(buf);
   }
   return num;
 }
 
-// One lane's instance (matrices Mx; ok = false when two points coincide)
+// One lane's instance (evaluator ev; ok = false when two points coincide)
 // over trial chunks [ch0, ch1) of `trials` warp-uniform trial records.
 // partial == false (the lane owns every chunk):
 // *out = sum_t ||yhat_t - y_t||_1 / sum_t ||y_t||_1, +inf when two points
 // coincide.  partial == true: out[ch * stride] = the chunk's sum (+inf when
 // two points coincide), for k_sweep_combine.  Per trial the m (m^2) terms are
 // summed in FP32, the trial sums in FP64 in the chunked order above.
-template <int DIM, int M, int R>
-__device__ __forceinline__ void lane_eval_mats(const Mats<M, R>& Mx, bool ok,
-                                               const float* __restrict__ rec, int trials,
-                                               int ch0, int ch1, double ysum, bool partial,
-                                               double* __restrict__ out, int64_t stride,
-                                               bool active) {
+template <class Ev>
+__device__ __forceinline__ void lane_eval_ev(const Ev& ev, bool ok, const float* __restrict__ rec,
+                                             int trials, int ch0, int ch1, double ysum,
+                                             bool partial, double* __restrict__ out,
+                                             int64_t stride, bool active) {
   double num = 0.0;
   for (int ch = ch0; ch < ch1; ++ch) {
     const int t0 = ch * kTrialChunk;
-    const double s = chunk_error<DIM, M, R>(Mx, rec, t0, min(t0 + kTrialChunk, trials));
+    const double s = chunk_error_ev(ev, rec, t0, min(t0 + kTrialChunk, trials));
     if (partial) {
       if (active) out[(int64_t)ch * stride] = ok ? s : (double)INFINITY;
     } else {
@@ -214,6 +213,26 @@ __device__ __forceinline__ void lane_eval_mats(const Mats<M, R>& Mx, bool ok,
     }
   }
   if (!partial && active) *out = ok ? num / ysum : (double)INFINITY;
+}
+
+// The plain-order tile error of matrices Mx (fmaf, inner index ascending).
+template <int DIM, int M, int R>
+struct PlainEval {
+  static constexpr int REC = SweepShape<DIM, M, R>::REC;
+  const Mats<M, R>& Mx;
+  __device__ __forceinline__ float operator()(const float* buf) const {
+    return DIM == 1 ? tile_err_1d<M, R>(Mx, buf) : tile_err_2d<M, R>(Mx, buf);
+  }
+};
+
+template <int DIM, int M, int R>
+__device__ __forceinline__ void lane_eval_mats(const Mats<M, R>& Mx, bool ok,
+                                               const float* __restrict__ rec, int trials,
+                                               int ch0, int ch1, double ysum, bool partial,
+                                               double* __restrict__ out, int64_t stride,
+                                               bool active) {
+  lane_eval_ev(PlainEval<DIM, M, R>{Mx}, ok, rec, trials, ch0, ch1, ysum, partial, out, stride,
+               active);
 }
 
 // lane_eval_mats for the instance (mask, c, d) of a sweep.
@@ -226,6 +245,28 @@ __device__ __forceinline__ void lane_eval(const float* __restrict__ rec, int tri
   const bool ok = build_instance<M, R>(mask, c, d, Mx);
   lane_eval_mats<DIM, M, R>(Mx, ok, rec, trials, ch0, ch1, ysum, partial, out, stride, active);
 }
+
+// Valid masks of one size (at most 256) and their positions in the caller's
+// subset list.
+struct MaskList {
+  unsigned char mask[256];
+  short q[256];  // index of the mask in the caller's subset list
+  int n;
+};
+
+// Mask-sweep kernel of one size: (rec, trials, c_grid, n_c, d, masks, ysum,
+// err, split, ch_per, part, n_out), one warp per (mask, 32 c values, chunk
+// group) -- k_sweep_eval in sweep.cu, k_order_sweep in sweep_order.cu.
+typedef void (*EvalFn)(const float*, int, const double*, int, double, const MaskList,
+                       const double*, double*, int, int, double*, int64_t);
+// Point-set kernel of one size: (rec, trials, sorted finite points, n_sets,
+// ysum, err), one lane per set.
+typedef void (*PointsetFn)(const float*, int, const double*, int, const double*, double*);
+
+// Summation-order variants (sweep_order.cu): the kernels of one size for
+// order 1 (Huffman, FP32) or 2 (Huffman, FP64 transforms); null otherwise.
+EvalFn order_sweep_kernel(int order, int dim, int m, int r);
+PointsetFn order_pointset_kernel(int order, int dim, int m, int r);
 
 // Partial chunk sums -> errors: err[i] = (sum over chunks ascending of
 // part[ch * stride + i]) / ysum of the instance's size, where the size is

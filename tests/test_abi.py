@@ -88,3 +88,22 @@ def test_pointset_validation_on_host(wino):
     assert L.wino_pointset_error(1, 2, 3, pts, 2, 10, 0, err, None) == wino.WINO_EINVAL
     pts2 = (ctypes.c_double * 4)(0.0, math.inf, -1.0, math.inf)
     assert L.wino_pointset_error(1, 2, 3, pts2, 1, 10, 0, err, None) == wino.WINO_EINVAL
+
+
+def test_order_validation_on_host(wino):
+    """An order outside WINO_ORDER_FMA .. WINO_ORDER_HUFFMAN_MIXED is rejected
+    before any device work, by both order entry points."""
+    import ctypes
+    import math
+    L = wino.load()
+    pts = (ctypes.c_double * 4)(0.0, 1.0, -1.0, math.inf)
+    err = (ctypes.c_double * 1)()
+    for order in (-1, 3):
+        assert L.wino_pointset_error_order(1, 2, 3, pts, 1, 10, 0, order, err,
+                                           None) == wino.WINO_EINVAL
+        cg = (ctypes.c_double * 1)(2.0)
+        sz = (wino.WinoSize * 1)(wino.WinoSize(1, 2, 3, 1.0))
+        mk = (ctypes.c_ubyte * 1)(0x60)
+        assert L.wino_error_sweep_order(cg, 1, sz, 1, mk, 1, 10, 0, order, err,
+                                        None) == wino.WINO_EINVAL
+    assert "order" in wino.wino_last_error()
