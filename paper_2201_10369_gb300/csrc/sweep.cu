@@ -295,7 +295,8 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
     double* es = err + (size_t)s * n_out;
     {
       ProfScope ps(order == 0 ? kKSweepEval : kKSweepOrder, st);
-      fn<<<grid, 32 * warps_per_block, 0, st>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
+      const size_t smem = order == 0 ? 0 : order_smem_bytes(order, sizes[s].m, sizes[s].r);
+      fn<<<grid, 32 * warps_per_block, smem, st>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
                                                  ml[s], ysum + s, es, split[s] > 1 ? sp : 1,
                                                  ch_per, chunk, n_out);
       note_launches(1);
@@ -381,7 +382,8 @@ int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int 
   if (rc != WINO_OK) return rc;
   {
     ProfScope ps(order == 0 ? kKSweepEval : kKSweepOrder, st);
-    fn<<<(n_sets + 127) / 128, 128, 0, st>>>(rec, trials, pts, n_sets, ysum, err);
+    const size_t smem = order == 0 ? 0 : order_smem_bytes(order, m, r);
+    fn<<<(n_sets + 127) / 128, 128, smem, st>>>(rec, trials, pts, n_sets, ysum, err);
     note_launches(1);
   }
   WINO_CUDA_TRY(cudaGetLastError());

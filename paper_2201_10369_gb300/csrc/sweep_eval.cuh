@@ -265,8 +265,12 @@ typedef void (*PointsetFn)(const float*, int, const double*, int, const double*,
 
 // Summation-order variants (sweep_order.cu): the kernels of one size for
 // order 1 (Huffman, FP32) or 2 (Huffman, FP64 transforms); null otherwise.
+// The kernels take order_smem_bytes(order, m, r) of dynamic shared memory
+// per 128-thread block; null when the size is not compiled or the device
+// refuses that much shared memory.
 EvalFn order_sweep_kernel(int order, int dim, int m, int r);
 PointsetFn order_pointset_kernel(int order, int dim, int m, int r);
+size_t order_smem_bytes(int order, int m, int r);
 
 // Partial chunk sums -> errors: err[i] = (sum over chunks ascending of
 // part[ch * stride + i]) / ysum of the instance's size, where the size is

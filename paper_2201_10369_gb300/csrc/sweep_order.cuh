@@ -94,12 +94,20 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(double v) { return __double2float_rn(v); }
 
-// sum_k c[k] x[k * xs] along the tree tw.  sv is this thread's slot 0 in
-// shared memory; slot j sits at sv[j * kOrderThreads].
-template <int N, typename T, typename X>
-__device__ __forceinline__ T tree_dot(const T* c, const X* x, int xs, const uint32_t* tw, T* sv) {
+// Shared-memory slot q of this thread is sv[q * kOrderThreads].
+//
+// tree_apply: out[v * os] = sum_k c[k] x[v * xv + k * xk] for v < NV, all
+// along the one tree tw.  The NV sums are independent chains, merged in
+// lock step: per merge the 2 NV loads issue before the NV stores, so the
+// chains overlap instead of waiting on one another.
+template <int N, int NV, typename T, typename X>
+__device__ __forceinline__ void tree_apply(const T* c, const X* x, int xv, int xk,
+                                           const uint32_t* tw, T* sv, T* out, int os) {
 #pragma unroll
-  for (int k = 0; k < N; ++k) sv[k * kOrderThreads] = mul_rn(c[k], (T)x[k * xs]);
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      sv[(v * N + k) * kOrderThreads] = mul_rn(c[k], (T)x[v * xv + k * xk]);
   const uint32_t w0 = tw[0];
   const int cnt = (int)(w0 & 15u);
   uint32_t cur = w0 >> 8;  // merge bytes still unread in the current word
@@ -110,13 +118,71 @@ __device__ __forceinline__ T tree_dot(const T* c, const X* x, int xs, const uint
       cur = tw[++q];
       left = 4;
     }
-    const uint32_t b = cur & 255u;
+    const int a = (int)(cur & 15u), b = (int)((cur >> 4) & 15u);
     cur >>= 8;
     --left;
-    T* a = sv + (b & 15u) * kOrderThreads;
-    *a = add_rn(*a, sv[(b >> 4) * kOrderThreads]);
+    T va[NV], vb[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      va[v] = sv[(v * N + a) * kOrderThreads];
+      vb[v] = sv[(v * N + b) * kOrderThreads];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sv[(v * N + a) * kOrderThreads] = add_rn(va[v], vb[v]);
   }
-  return sv[((w0 >> 4) & 15u) * kOrderThreads];
+  const int root = (int)((w0 >> 4) & 15u);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v * os] = sv[(v * N + root) * kOrderThreads];
+}
+
+// rows_apply: out[j] = sum_k c[j * N + k] x[k] for j < NR, row j along its
+// own tree trees[j]; the rows' merges run in lock step like tree_apply's.
+template <int N, int NR, typename T, typename X>
+__device__ __forceinline__ void rows_apply(const T* c, const X* x, const Tree<N>* trees, T* sv,
+                                           T* out) {
+#pragma unroll
+  for (int j = 0; j < NR; ++j)
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      sv[(j * N + k) * kOrderThreads] = mul_rn(c[j * N + k], (T)x[k]);
+  uint32_t cur[NR];
+  int cnt[NR], left[NR], q[NR];
+  int most = 0;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const uint32_t w0 = trees[j].w[0];
+    cnt[j] = (int)(w0 & 15u);
+    cur[j] = w0 >> 8;
+    left[j] = 3;
+    q[j] = 0;
+    most = max(most, cnt[j]);
+  }
+#pragma unroll 1
+  for (int s = 0; s < most; ++s) {
+    int a[NR], b[NR];
+    T va[NR], vb[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      if (s < cnt[j]) {
+        if (left[j] == 0) {
+          cur[j] = trees[j].w[++q[j]];
+          left[j] = 4;
+        }
+        a[j] = (int)(cur[j] & 15u);
+        b[j] = (int)((cur[j] >> 4) & 15u);
+        cur[j] >>= 8;
+        --left[j];
+        va[j] = sv[(j * N + a[j]) * kOrderThreads];
+        vb[j] = sv[(j * N + b[j]) * kOrderThreads];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (s < cnt[j]) sv[(j * N + a[j]) * kOrderThreads] = add_rn(va[j], vb[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < NR; ++j)
+    out[j] = sv[(j * N + (int)((trees[j].w[0] >> 4) & 15u)) * kOrderThreads];
 }
 
 template <int DIM, int M, int R, typename T>
@@ -131,25 +197,23 @@ __device__ __forceinline__ float order_err_1d(const OrderEval<1, M, R, T>& Q,
   const float* d = rc + R;
   const float* yh = d + A;
   const float* yl = yh + M;
+  T u[A], v[A], y[M];
+  rows_apply<R, A>(Q.G, g, Q.tG, Q.sv, u);
+  rows_apply<A, A>(Q.BT, d, Q.tB, Q.sv, v);
   float p[A];
-#pragma unroll 1
-  for (int i = 0; i < A; ++i) {
-    const float u = to_f32(tree_dot<R>(&Q.G[i * R], g, 1, Q.tG[i].w, Q.sv));
-    const float v = to_f32(tree_dot<A>(&Q.BT[i * A], d, 1, Q.tB[i].w, Q.sv));
-    p[i] = __fmul_rn(u, v);
-  }
+#pragma unroll
+  for (int i = 0; i < A; ++i) p[i] = __fmul_rn(to_f32(u[i]), to_f32(v[i]));
+  rows_apply<A, M>(Q.AT, p, Q.tA, Q.sv, y);
   float e = 0.0f;
-#pragma unroll 1
-  for (int j = 0; j < M; ++j) {
-    const float y = to_f32(tree_dot<A>(&Q.AT[j * A], p, 1, Q.tA[j].w, Q.sv));
-    e = __fadd_rn(e, abs_err(y, yh[j], yl[j]));
-  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) e = __fadd_rn(e, abs_err(to_f32(y[j]), yh[j], yl[j]));
   return e;
 }
 
-// 2D, one frequency row i at a time: W_i = G_i g, U_i = W_i G^T,
-// T_i = B^T_i d, V_i = T_i B, P_i = U_i .* V_i (FP32); then per output row
-// a: Z_a = A^T_a P, Y_a = Z_a A.
+// 2D, each pass one matrix row's tree over all the vectors it multiplies:
+// W = G g (row i of G over the columns of g), U = W G^T (row j of G over
+// the rows of W), T = B^T d, V = T B, P = U .* V (FP32), Z = A^T P,
+// Y = Z A; the per-trial error summed over Y in row-major order.
 template <int M, int R, typename T>
 __device__ __forceinline__ float order_err_2d(const OrderEval<2, M, R, T>& Q,
                                               const float* __restrict__ rc) {
@@ -158,33 +222,37 @@ __device__ __forceinline__ float order_err_2d(const OrderEval<2, M, R, T>& Q,
   const float* d = rc + R * R;
   const float* yh = d + A * A;
   const float* yl = yh + M * M;
-  float P[A * A];
+  T W[A * R], U[A * A], Tm[A * A], Z[M * A];
+  float P[A * A], Y[M * M];
 #pragma unroll 1
-  for (int i = 0; i < A; ++i) {
-    T Wi[R], Ti[A];
-#pragma unroll
-    for (int k = 0; k < R; ++k) Wi[k] = tree_dot<R>(&Q.G[i * R], g + k, R, Q.tG[i].w, Q.sv);
-#pragma unroll
-    for (int l = 0; l < A; ++l) Ti[l] = tree_dot<A>(&Q.BT[i * A], d + l, A, Q.tB[i].w, Q.sv);
+  for (int i = 0; i < A; ++i)  // W[i][k] = sum_l G[i][l] g[l][k]
+    tree_apply<R, R>(&Q.G[i * R], g, 1, R, Q.tG[i].w, Q.sv, &W[i * R], 1);
 #pragma unroll 1
-    for (int j = 0; j < A; ++j) {
-      const float u = to_f32(tree_dot<R>(&Q.G[j * R], Wi, 1, Q.tG[j].w, Q.sv));
-      const float v = to_f32(tree_dot<A>(&Q.BT[j * A], Ti, 1, Q.tB[j].w, Q.sv));
-      P[i * A + j] = __fmul_rn(u, v);
-    }
+  for (int j = 0; j < A; ++j)  // U[i][j] = sum_k W[i][k] G[j][k]
+    tree_apply<R, A>(&Q.G[j * R], W, R, 1, Q.tG[j].w, Q.sv, &U[j], A);
+#pragma unroll 1
+  for (int i = 0; i < A; ++i)  // T[i][l] = sum_k BT[i][k] d[k][l]
+    tree_apply<A, A>(&Q.BT[i * A], d, 1, A, Q.tB[i].w, Q.sv, &Tm[i * A], 1);
+#pragma unroll 1
+  for (int j = 0; j < A; ++j) {  // V[i][j] = sum_l T[i][l] BT[j][l]; P = U .* V
+    T Vj[A];
+    tree_apply<A, A>(&Q.BT[j * A], Tm, A, 1, Q.tB[j].w, Q.sv, Vj, 1);
+#pragma unroll
+    for (int i = 0; i < A; ++i) P[i * A + j] = __fmul_rn(to_f32(U[i * A + j]), to_f32(Vj[i]));
+  }
+#pragma unroll 1
+  for (int a = 0; a < M; ++a)  // Z[a][j] = sum_i AT[a][i] P[i][j]
+    tree_apply<A, A>(&Q.AT[a * A], P, 1, A, Q.tA[a].w, Q.sv, &Z[a * A], 1);
+#pragma unroll 1
+  for (int b = 0; b < M; ++b) {  // Y[a][b] = sum_j Z[a][j] AT[b][j]
+    T Yb[M];
+    tree_apply<A, M>(&Q.AT[b * A], Z, A, 1, Q.tA[b].w, Q.sv, Yb, 1);
+#pragma unroll
+    for (int a = 0; a < M; ++a) Y[a * M + b] = to_f32(Yb[a]);
   }
   float e = 0.0f;
-#pragma unroll 1
-  for (int a = 0; a < M; ++a) {
-    T Za[A];
 #pragma unroll
-    for (int j = 0; j < A; ++j) Za[j] = tree_dot<A>(&Q.AT[a * A], P + j, A, Q.tA[a].w, Q.sv);
-#pragma unroll 1
-    for (int b = 0; b < M; ++b) {
-      const float y = to_f32(tree_dot<A>(&Q.AT[b * A], Za, 1, Q.tA[b].w, Q.sv));
-      e = __fadd_rn(e, abs_err(y, yh[a * M + b], yl[a * M + b]));
-    }
-  }
+  for (int q = 0; q < M * M; ++q) e = __fadd_rn(e, abs_err(Y[q], yh[q], yl[q]));
   return e;
 }
 
@@ -235,6 +303,19 @@ __device__ __forceinline__ bool order_build(const double* a, OrderEval<DIM, M, R
   return ok;
 }
 
+// One lane's instance from its sorted finite points a[0..alpha-2], over
+// trial chunks [ch0, ch1) (lane_eval_ev's contract).  Not inlined: both
+// kernels below run this one body.
+template <int DIM, int M, int R, typename T>
+__device__ __noinline__ void order_lane(const double* a, T* sv, const float* __restrict__ rec,
+                                        int trials, int ch0, int ch1, double ysum, bool partial,
+                                        double* __restrict__ out, int64_t stride, bool active) {
+  OrderEval<DIM, M, R, T> Q;
+  Q.sv = sv;
+  const bool ok = order_build<DIM, M, R, T>(a, Q);
+  lane_eval_ev(Q, ok, rec, trials, ch0, ch1, ysum, partial, out, stride, active);
+}
+
 // Mask sweep: the grid of k_sweep_eval (one warp per valid mask, block of
 // 32 c values and chunk group; lanes own instances).
 template <int DIM, int M, int R, typename T>
@@ -244,7 +325,8 @@ __global__ void __launch_bounds__(kOrderThreads)
                   double* __restrict__ err, int split, int ch_per, double* __restrict__ part,
                   int64_t n_out) {
   constexpr int A = M + R - 1;
-  __shared__ T sv[A * kOrderThreads];
+  extern __shared__ __align__(16) unsigned char order_smem[];
+  T* sv = reinterpret_cast<T*>(order_smem);  // A * A slots per thread
   const int lane = threadIdx.x & 31;
   const int nblk = (n_c + 31) >> 5;
   const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -261,11 +343,8 @@ __global__ void __launch_bounds__(kOrderThreads)
   const int ch1 = split == 1 ? nch : min(ch0 + ch_per, nch);
   double pts[kMaxAlpha];
   mask_points(masks.mask[qv], A, c, d, pts);  // valid: the host kept valid masks only
-  OrderEval<DIM, M, R, T> Q;
-  Q.sv = sv + threadIdx.x;
-  const bool ok = order_build<DIM, M, R, T>(pts, Q);
-  lane_eval_ev(Q, ok, rec, trials, ch0, ch1, *ysum, split > 1, split == 1 ? err + o : part + o,
-               n_out, active);
+  order_lane<DIM, M, R, T>(pts, sv + threadIdx.x, rec, trials, ch0, ch1, *ysum, split > 1,
+                           split == 1 ? err + o : part + o, n_out, active);
 }
 
 // Explicit point sets, one lane per set.
@@ -274,39 +353,59 @@ __global__ void __launch_bounds__(kOrderThreads)
     k_order_pointset(const float* __restrict__ rec, int trials, const double* __restrict__ pts,
                      int n_sets, const double* __restrict__ ysum, double* __restrict__ err) {
   constexpr int A = M + R - 1;
-  __shared__ T sv[A * kOrderThreads];
+  extern __shared__ __align__(16) unsigned char order_smem[];
+  T* sv = reinterpret_cast<T*>(order_smem);  // A * A slots per thread
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = s < n_sets;
   const int ss = active ? s : 0;
-  double a[A - 1];
+  double a[kMaxAlpha];
 #pragma unroll
   for (int i = 0; i < A - 1; ++i) a[i] = pts[(int64_t)ss * (A - 1) + i];
-  OrderEval<DIM, M, R, T> Q;
-  Q.sv = sv + threadIdx.x;
-  const bool ok = order_build<DIM, M, R, T>(a, Q);
-  lane_eval_ev(Q, ok, rec, trials, 0, trial_chunks(trials), *ysum, false, err + ss, 0, active);
+  order_lane<DIM, M, R, T>(a, sv + threadIdx.x, rec, trials, 0, trial_chunks(trials), *ysum,
+                           false, err + ss, 0, active);
 }
 
 }  // namespace
 
+// Dynamic shared memory of the order kernels of size (m, r): A * A value
+// slots per thread.
+template <typename T>
+inline size_t order_smem_bytes_t(int m, int r) {
+  const size_t a = (size_t)(m + r - 1);
+  return a * a * kOrderThreads * sizeof(T);
+}
+
 // The kernel tables of one value type T (float: the FP32 Huffman form,
-// double: the mixed form).
+// double: the mixed form); each kernel returned is allowed its dynamic
+// shared memory (above the 48 KB default for the larger sizes).
 template <typename T>
 EvalFn order_sweep_kernel_t(int dim, int m, int r) {
+  EvalFn fn = nullptr;
 #define WINO_ORDER_CASE(I, D, MM, RR) \
-  if (dim == D && m == MM && r == RR) return k_order_sweep<D, MM, RR, T>;
+  if (dim == D && m == MM && r == RR) fn = k_order_sweep<D, MM, RR, T>;
   WINO_SWEEP_SIZES(WINO_ORDER_CASE)
 #undef WINO_ORDER_CASE
-  return nullptr;
+  if (fn && cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)order_smem_bytes_t<T>(m, r)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return fn;
 }
 
 template <typename T>
 PointsetFn order_pointset_kernel_t(int dim, int m, int r) {
+  PointsetFn fn = nullptr;
 #define WINO_ORDER_CASE(I, D, MM, RR) \
-  if (dim == D && m == MM && r == RR) return k_order_pointset<D, MM, RR, T>;
+  if (dim == D && m == MM && r == RR) fn = k_order_pointset<D, MM, RR, T>;
   WINO_SWEEP_SIZES(WINO_ORDER_CASE)
 #undef WINO_ORDER_CASE
-  return nullptr;
+  if (fn && cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)order_smem_bytes_t<T>(m, r)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return fn;
 }
 
 }  // namespace wino

@@ -19,4 +19,10 @@ PointsetFn order_pointset_kernel(int order, int dim, int m, int r) {
   return nullptr;
 }
 
+size_t order_smem_bytes(int order, int m, int r) {
+  if (order == 1) return order_smem_bytes_t<float>(m, r);
+  if (order == 2) return order_smem_bytes_t<double>(m, r);
+  return 0;
+}
+
 }  // namespace wino

@@ -108,3 +108,20 @@ def test_order_moves_the_error_by_percents(wino):
         ratio = np.median(e["huffman"][ok] / e["fma"][ok])
         assert 1 / 1.5 < ratio < 1.5, (size, ratio)
         assert np.median(e["huffman_mixed"][ok] / e["huffman"][ok]) < 1.0
+
+
+@pytest.mark.parametrize("order", ["fma"] + ORDERS)
+def test_order_mask_sweep_matches_pointsets_every_size(wino, orc, order):
+    """Every compiled size: the mask sweep's errors for the first valid mask
+    at a few c equal, bit for bit, the point-set errors of the same sets
+    (both front ends, same trials and summation order)."""
+    cg = inputs.c_grid(4096)[::601]
+    masks = inputs.sweep_masks()
+    for size in inputs.SWEEP_SIZES + [(1, m, 5, 2.0) for m in range(2, 7)]:
+        dim, m, r, d = size
+        mk = wino.valid_masks(size, masks)[0]
+        e = wino.wino_error_sweep(cg, [size], [mk], 256, seed=5, order=order)[0, 0]
+        sets = [orc.mask_points(dim, m, r, d, mk, c) for c in cg]
+        p = wino.wino_pointset_error((dim, m, r), sets, 256, seed=5, order=order)
+        assert np.all(np.isfinite(e)), (size, order)
+        assert np.array_equal(e, p), (size, order, e, p)
