@@ -420,6 +420,7 @@ def run_ours(args, rank, world, local_rank):
                 roofs[k] = r
     dom = max(roofs, key=lambda k: prof[k][0])
     comparison = paper_comparison(wino, inputs, ex, cg, masks, sizes)
+    orders = order_sweeps(wino, inputs, cg, sizes, masks, rank)
     plan_info = plan.info()
     plan.close()
     guided.close()
@@ -478,6 +479,7 @@ def run_ours(args, rank, world, local_rank):
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk,
         "paper_comparison": comparison,
+        "sweep_orders": orders,
     }
     if world == 1 and not args.no_cpu_baseline:
         v, dt, nth = oracle_layer_sample(layers)
@@ -504,9 +506,10 @@ def paper_comparison(wino, inputs, ex, cg, masks, sizes):
         if key not in inputs.COMPARISON_SETS:
             continue
         inf = math.inf
-        pn, prop = wino.wino_pointset_error((dim, m, r), [inputs.COMPARISON_SETS[key] + [inf],
-                                                          inputs.PROPOSED_SETS[key] + [inf]],
-                                            inputs.SWEEP_TRIALS, seed=0)
+        pair = [inputs.COMPARISON_SETS[key] + [inf], inputs.PROPOSED_SETS[key] + [inf]]
+        pn, prop = wino.wino_pointset_error((dim, m, r), pair, inputs.SWEEP_TRIALS, seed=0)
+        pn_h, prop_h = wino.wino_pointset_error((dim, m, r), pair, inputs.SWEEP_TRIALS, seed=0,
+                                                order="huffman")
         e = np.where(np.isfinite(ex[s]), ex[s], np.nan)
         q, k = np.unravel_index(np.nanargmin(e), e.shape)
         best = float(e[q, k])
@@ -515,7 +518,9 @@ def paper_comparison(wino, inputs, ex, cg, masks, sizes):
             "sweep_best_mask": "%#04x" % int(masks[q]), "sweep_best_c": float(cg[k]),
             "d": d, "improvement_pct_paper_set": 100.0 * (pn - prop) / pn,
             "improvement_pct_sweep_best": 100.0 * (pn - best) / pn,
-            "improvement_pct_printed": inputs.PAPER_IMPROVEMENT_PCT[key]}
+            "improvement_pct_printed": inputs.PAPER_IMPROVEMENT_PCT[key],
+            "huffman_order": {"barabasz": float(pn_h), "paper_set": float(prop_h),
+                              "improvement_pct_paper_set": 100.0 * (pn_h - prop_h) / pn_h}}
     # two-parameter (c, d) search of the paper's subset for the sizes whose
     # proposed set has a d: 128 d x 1024 c, log-spaced in [1.001, 4] x [0.25, 4]
     dg, cgg = np.geomspace(1.001, 4.0, 128), np.geomspace(0.25, 4.0, 1024)
@@ -529,6 +534,73 @@ def paper_comparison(wino, inputs, ex, cg, masks, sizes):
         row["cd_search"] = {"mask": "%#04x" % mask, "c": float(cgg[k]), "d": float(dg[i]),
                             "err": float(e[i, k]),
                             "improvement_pct": 100.0 * (row["barabasz"] - e[i, k]) / row["barabasz"]}
+    return out
+
+
+def order_smem_ops(dim, m, r):
+    """Shared-memory value accesses of one trial of one instance in the
+    Huffman-order kernels, every matrix entry counted as non-zero: a dot
+    product of n terms stores n products, merges n - 1 times (two loads, one
+    store) and loads its root: 4 n - 2."""
+    a = m + r - 1
+    dot = lambda n: 4 * n - 2  # noqa: E731
+    if dim == 1:
+        return a * dot(r) + a * dot(a) + m * dot(a)
+    return a * r * dot(r) + a * a * dot(r) + 2 * a * a * dot(a) + m * a * dot(a) + m * m * dot(a)
+
+
+def order_fp64_ops(dim, m, r):
+    """FP64 multiplies and adds of one trial in the FP64-transform kernels
+    (2 n - 1 per dot product of n terms, every entry counted as non-zero)."""
+    a = m + r - 1
+    dot = lambda n: 2 * n - 1  # noqa: E731
+    if dim == 1:
+        return a * dot(r) + a * dot(a) + m * dot(a)
+    return a * r * dot(r) + a * a * dot(r) + 2 * a * a * dot(a) + m * a * dot(a) + m * m * dot(a)
+
+
+def order_sweeps(wino, inputs, cg, sizes, masks, rank):
+    """The full sweep grid in the two Huffman orders (Sec. 5), untimed by the
+    step: wall time, kernel time and each kernel's bound -- the shared-memory
+    pipe (128 B per SM per clock) for the FP32 form, the FP64 issue rate for
+    the FP64-transform form."""
+    out = {}
+    n_inst = 0
+    work = {"huffman": 0.0, "huffman_mixed": 0.0}
+    for size in sizes:
+        k = len(wino.valid_masks(size, masks)) * cg.size * inputs.SWEEP_TRIALS
+        n_inst += len(wino.valid_masks(size, masks)) * cg.size
+        work["huffman"] += 4.0 * k * order_smem_ops(*size[:3])
+        work["huffman_mixed"] += 1.0 * k * order_fp64_ops(*size[:3])
+    import torch
+    smem_peak = SMS * 128 * SM_MAX_MHZ * 1e6 / 1e9
+    fp64_peak = 1.25e3 / 2
+    for order in ("huffman", "huffman_mixed"):
+        wino.wino_error_sweep(cg[:64], sizes, masks, 100, seed=rank, order=order)  # warm-up
+        torch.cuda.synchronize()
+        wino.wino_profile_enable(True)
+        t0 = time.perf_counter()
+        wino.wino_error_sweep(cg, sizes, masks, inputs.SWEEP_TRIALS, seed=rank, order=order)
+        dt = time.perf_counter() - t0
+        ms, n = wino.wino_profile_read("sweep_order")
+        wino.wino_profile_enable(False)
+        sec = ms / 1e3
+        if order == "huffman":
+            ach = work[order] / sec / 1e9
+            roof = {"bound": "smem", "unit": "GB/s", "achieved": ach, "peak": smem_peak,
+                    "frac": ach / smem_peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 B/clock x 2070 MHz",
+                    "work": "4 B x (4n - 2) value accesses per n-term dot product"}
+        else:
+            ach = work[order] / sec / 1e9
+            roof = {"bound": "fp64", "unit": "Gop/s", "achieved": ach, "peak": fp64_peak,
+                    "frac": ach / fp64_peak, "traffic": None,
+                    "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA = 2), halved for "
+                                   "separate multiplies and adds",
+                    "work": "2n - 1 FP64 multiplies and adds per n-term dot product"}
+        out[order] = {"value": n_inst / dt, "unit": "evals/s", "wall_ms": 1e3 * dt,
+                      "kernel_ms": ms, "launches": n, "instances": n_inst,
+                      "trials": inputs.SWEEP_TRIALS, "roofline": roof}
     return out
 
 
@@ -673,6 +745,11 @@ def profile_case(name):
         cg = inputs.c_grid()
         for _ in range(4):
             wino.wino_error_sweep(cg, [(2, 4, 3, 1.0)], inputs.sweep_masks(), 1000, seed=0)
+    elif name in ("sweep_huffman", "sweep_huffman_mixed"):
+        cg = inputs.c_grid()
+        for _ in range(4):
+            wino.wino_error_sweep(cg, [(2, 4, 3, 1.0)], inputs.sweep_masks(), 1000, seed=0,
+                                  order=name[6:])
     else:
         raise SystemExit("unknown profile case " + name)
     torch.cuda.synchronize()
@@ -690,7 +767,9 @@ def main():
                     help="run one small workload a few times for an ncu capture: "
                          "f4x4 | f6x6 | f4x4_bf16 | f4x4_split | f4x4_x6 (VGG 64ch 224x224, N=8; "
                          "suffix _vgg: the five VGG16 stages, N=8; suffix _l0.._l4: that "
-                         "VGG16 stage at N=32) | sweep (2D F(4x4), all masks, 4096 c)")
+                         "VGG16 stage at N=32) | sweep (2D F(4x4), all masks, 4096 c) | "
+                         "sweep_huffman | sweep_huffman_mixed (the same in the Huffman "
+                         "orders)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
