@@ -207,7 +207,11 @@ int wino_pointset_error(int dim, int m, int r, const double* points, int n_sets,
  *                            and V rounded to FP32, the Hadamard product in
  *                            FP32, the output transform in FP64 and Y
  *                            rounded to FP32 once.
- * Per-trial and per-chunk summation of the errors as in wino_error_sweep.  */
+ * Error sums of orders 1 and 2: per trial the outputs' errors in FP32
+ * (row-major), the trials t = l, l + 32, l + 64, ... summed in FP64 in trial
+ * order for each l < 32, and the 32 sums combined by a fixed butterfly
+ * (pairs 16 apart, then 8, 4, 2, 1); wino_pointset_error_order uses the
+ * same, so a set that is also a mask instance gets the same bits.         */
 typedef enum {
   WINO_ORDER_FMA = 0,
   WINO_ORDER_HUFFMAN = 1,

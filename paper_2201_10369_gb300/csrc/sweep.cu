@@ -230,8 +230,7 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   size_t rec_total = 0;
   const int nb_prep = sweep_prepare_blocks(trials);
   for (int s = 0; s < n_sizes; ++s) {
-    if (!(order == 0 ? eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)
-                     : order_sweep_kernel(order, sizes[s].dim, sizes[s].m, sizes[s].r))) {
+    if (!eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)) {  // the order kernels: same sizes
       set_error("sweep size not compiled: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6");
       return WINO_EUNSUPPORTED;
     }
@@ -248,7 +247,7 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   for (int s = 0; s < n_sizes; ++s) {
     ml[s] = valid_masks(sizes[s], subsets, n_subsets);
     const int items = ml[s].n * nblk;
-    if (items > 0 && items < sweep_target_warps())
+    if (order == 0 && items > 0 && items < sweep_target_warps())
       split[s] = std::min(n_chunks, (sweep_target_warps() + items - 1) / items);
     if (split[s] > 1) n_part = std::max(n_part, (size_t)n_chunks * n_subsets * n_c);
   }
@@ -290,13 +289,18 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
     const int64_t warps = (int64_t)ml[s].n * nblk * (split[s] > 1 ? sp : 1);
     const int warps_per_block = 4;
     const unsigned grid = (unsigned)((warps + warps_per_block - 1) / warps_per_block);
-    EvalFn fn = order == 0 ? eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)
-                           : order_sweep_kernel(order, sizes[s].dim, sizes[s].m, sizes[s].r);
     double* es = err + (size_t)s * n_out;
+    if (order != 0) {
+      ProfScope ps(kKSweepOrder, st);
+      rc = order_sweep_launch(order, sizes[s], rec + rec_off[s], trials, cg, n_c, ml[s],
+                              ysum + s, es, st);
+      if (rc != WINO_OK) return rc;
+      continue;
+    }
+    EvalFn fn = eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r);
     {
-      ProfScope ps(order == 0 ? kKSweepEval : kKSweepOrder, st);
-      const size_t smem = order == 0 ? 0 : order_smem_bytes(order, sizes[s].m, sizes[s].r);
-      fn<<<grid, 32 * warps_per_block, smem, st>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
+      ProfScope ps(kKSweepEval, st);
+      fn<<<grid, 32 * warps_per_block, 0, st>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
                                                  ml[s], ysum + s, es, split[s] > 1 ? sp : 1,
                                                  ch_per, chunk, n_out);
       note_launches(1);
@@ -354,7 +358,7 @@ static PointsetFn pointset_kernel(int dim, int m, int r) {
 // points: [n_sets][alpha-1] sorted finite points (host); err_out host.
 int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int trials,
                    unsigned long long seed, int order, double* err_out, cudaStream_t st) {
-  PointsetFn fn = order == 0 ? pointset_kernel(dim, m, r) : order_pointset_kernel(order, dim, m, r);
+  PointsetFn fn = pointset_kernel(dim, m, r);  // the order kernels cover the same sizes
   if (!fn) {
     set_error("point-set sizes: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6");
     return WINO_EUNSUPPORTED;
@@ -380,10 +384,13 @@ int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int 
                                 cudaMemcpyHostToDevice, st));
   rc = sweep_prepare(rec, part, ysum, dim, m, r, trials, seed, st);
   if (rc != WINO_OK) return rc;
-  {
-    ProfScope ps(order == 0 ? kKSweepEval : kKSweepOrder, st);
-    const size_t smem = order == 0 ? 0 : order_smem_bytes(order, m, r);
-    fn<<<(n_sets + 127) / 128, 128, smem, st>>>(rec, trials, pts, n_sets, ysum, err);
+  if (order != 0) {
+    ProfScope ps(kKSweepOrder, st);
+    rc = order_pointset_launch(order, dim, m, r, rec, trials, pts, n_sets, ysum, err, st);
+    if (rc != WINO_OK) return rc;
+  } else {
+    ProfScope ps(kKSweepEval, st);
+    fn<<<(n_sets + 127) / 128, 128, 0, st>>>(rec, trials, pts, n_sets, ysum, err);
     note_launches(1);
   }
   WINO_CUDA_TRY(cudaGetLastError());

@@ -254,23 +254,26 @@ struct MaskList {
   int n;
 };
 
-// Mask-sweep kernel of one size: (rec, trials, c_grid, n_c, d, masks, ysum,
-// err, split, ch_per, part, n_out), one warp per (mask, 32 c values, chunk
-// group) -- k_sweep_eval in sweep.cu, k_order_sweep in sweep_order.cu.
+// Mask-sweep kernel of one size (k_sweep_eval in sweep.cu): (rec, trials,
+// c_grid, n_c, d, masks, ysum, err, split, ch_per, part, n_out), one warp per
+// (mask, 32 c values, chunk group).
 typedef void (*EvalFn)(const float*, int, const double*, int, double, const MaskList,
                        const double*, double*, int, int, double*, int64_t);
 // Point-set kernel of one size: (rec, trials, sorted finite points, n_sets,
 // ysum, err), one lane per set.
 typedef void (*PointsetFn)(const float*, int, const double*, int, const double*, double*);
 
-// Summation-order variants (sweep_order.cu): the kernels of one size for
-// order 1 (Huffman, FP32) or 2 (Huffman, FP64 transforms); null otherwise.
-// The kernels take order_smem_bytes(order, m, r) of dynamic shared memory
-// per 128-thread block; null when the size is not compiled or the device
-// refuses that much shared memory.
-EvalFn order_sweep_kernel(int order, int dim, int m, int r);
-PointsetFn order_pointset_kernel(int order, int dim, int m, int r);
-size_t order_smem_bytes(int order, int m, int r);
+// Summation-order variants (sweep_order_f32.cu, sweep_order_f64.cu): enqueue
+// the sweep of one size's valid masks over c_grid (err[q * n_c + k] for the
+// caller's subset index q), or of n_sets explicit sorted point sets, in
+// order 1 (Huffman, FP32) or 2 (Huffman, FP64 transforms).  One warp per
+// instance; the sizes of WINO_SWEEP_SIZES, else WINO_EUNSUPPORTED.
+int order_sweep_launch(int order, const SweepSize& s, const float* rec, int trials,
+                       const double* c_grid, int n_c, const MaskList& masks, const double* ysum,
+                       double* err, cudaStream_t st);
+int order_pointset_launch(int order, int dim, int m, int r, const float* rec, int trials,
+                          const double* pts, int n_sets, const double* ysum, double* err,
+                          cudaStream_t st);
 
 // Partial chunk sums -> errors: err[i] = (sum over chunks ascending of
 // part[ch * stride + i]) / ysum of the instance's size, where the size is

@@ -16,16 +16,24 @@
 // and sums, U and V rounded to FP32, P = U .* V in FP32, the output
 // transform in FP64 and Y rounded once.
 //
-// GPU layout: one lane per instance, as in the plain sweep (sweep.cu), with
-// the same trials, chunking and FP64 trial sums.  The trees depend on the
-// instance (c moves the magnitudes), so each lane builds its own once and
-// keeps them packed per matrix row: byte 0 = merge count | root slot << 4,
-// byte 1 + s = merge s as first slot | second slot << 4 (the sum takes the
-// first slot).  Merging needs per-lane dynamic slot indices, so the values
-// being merged live in shared memory as [slot][thread]: bank = thread mod 32
-// whatever the slot, and the lanes' different trees never conflict.  All
-// lanes of a warp share a mask, hence the positions of the zero entries and
-// every merge count: the merge loops do not diverge.
+// GPU layout: one warp per instance, its lanes taking 32 trials at a time.
+// The instance's matrices (rows padded to 16 bytes) and trees live once per
+// warp in shared memory and are read as broadcasts; the trees are therefore
+// warp-uniform and no merge loop diverges.  A tree is packed per matrix row:
+// byte 0 = merge count | root slot << 4, byte 1 + s = merge s as first slot
+// | second slot << 4 (the sum takes the first slot).  The values being merged
+// need dynamic slot indices, so each lane keeps them in the warp's shared
+// memory as [slot][lane] (bank = lane, conflict-free).  A row's tree is
+// applied to all the vectors it multiplies at once, or all rows' trees in
+// lock step, so 5-10 independent merge chains overlap.  The 2D Hadamard
+// product P = U .* V waits in shared memory ([element][lane]) for the output
+// transform; everything else a trial needs stays in registers.
+//
+// Error sums: per trial the outputs' errors in FP32 (row-major); each lane
+// adds the errors of its trials t = lane, lane + 32, ... in FP64 in trial
+// order, and the 32 lane sums are combined by a fixed butterfly of
+// shuffles (lane l with l ^ 16, then ^ 8, ^ 4, ^ 2, ^ 1), the same in both
+// kernels.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,6 +41,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "../../include/wino.h"
 #include "common.cuh"
 #include "construct.cuh"
 #include "sweep_eval.cuh"
@@ -40,23 +49,64 @@
 namespace wino {
 namespace {
 
-constexpr int kOrderThreads = 128;
+constexpr int kOrderWarps = 4;  // warps (instances) per block
+constexpr int kOrderThreads = 32 * kOrderWarps;
+constexpr unsigned kFull = 0xffffffffu;
 
-template <int N>
-struct Tree {
-  uint32_t w[(N + 3) / 4];
+__host__ __device__ constexpr int pad_to(int n, int v) { return (n + v - 1) / v * v; }
+__host__ __device__ constexpr size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Byte layout of one warp's shared-memory region.
+template <int DIM, int M, int R, typename T>
+struct OrderLayout {
+  static constexpr int A = M + R - 1;
+  static constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte load
+  static constexpr int GS = pad_to(R, V);        // row strides (elements)
+  static constexpr int BS = pad_to(A, V);
+  static constexpr int WG = (R + 3) / 4;  // tree words per row
+  static constexpr int WB = (A + 3) / 4;
+  static constexpr int NSLOT = A * A + 1;  // + one dummy slot for padded merges
+  static constexpr int A4 = pad_to(A, 4), M4 = pad_to(M, 4);  // program row widths
+  static constexpr size_t G_OFF = 0;
+  static constexpr size_t BT_OFF = G_OFF + sizeof(T) * A * GS;
+  static constexpr size_t AT_OFF = BT_OFF + sizeof(T) * A * BS;
+  static constexpr size_t TG_OFF = AT_OFF + sizeof(T) * M * BS;
+  static constexpr size_t TB_OFF = TG_OFF + 4 * (size_t)A * WG;
+  static constexpr size_t TA_OFF = TB_OFF + 4 * (size_t)A * WB;
+  // lock-step merge programs of the three row sets (G, B^T, A^T): per step
+  // one word per row, then each row's root offset, then the step counts
+  static constexpr size_t PG_OFF = pad16(TA_OFF + 4 * (size_t)M * WB);
+  static constexpr size_t PB_OFF = PG_OFF + 4 * (size_t)(R - 1) * A4;
+  static constexpr size_t PA_OFF = PB_OFF + 4 * (size_t)(A - 1) * A4;
+  static constexpr size_t RG_OFF = PA_OFF + 4 * (size_t)(A - 1) * M4;
+  static constexpr size_t RB_OFF = RG_OFF + 4 * (size_t)A4;
+  static constexpr size_t RA_OFF = RB_OFF + 4 * (size_t)A4;
+  static constexpr size_t NS_OFF = RA_OFF + 4 * (size_t)M4;
+  static constexpr size_t SL_OFF = pad16(NS_OFF + 16);
+  static constexpr size_t P_OFF = SL_OFF + sizeof(T) * NSLOT * 32;
+  static constexpr size_t BYTES = pad16(P_OFF + (DIM == 2 ? 4 * (size_t)A * A * 32 : 0));
 };
 
-// Huffman tree of one matrix row (N FP64 entries; leaf weights are the
-// |FP32-rounded| entries, zero entries left out).
-template <int N>
-__device__ __noinline__ void make_tree(const double* row, uint32_t* tw) {
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return __double2float_rn(v); }
+__device__ __forceinline__ float from_f64(double v, float*) { return __double2float_rn(v); }
+__device__ __forceinline__ double from_f64(double v, double*) { return v; }
+
+// Huffman tree of one matrix row of N coefficients (shared memory), packed
+// into (N + 3) / 4 words; leaf weights are the |FP32-rounded| entries, zero
+// entries left out.
+template <int N, typename T>
+__device__ __noinline__ void make_tree(const T* row, uint32_t* tw) {
   double wt[2 * N];
   int slot[2 * N];
   bool live[2 * N];
   int n_live = 0, last = 0;
   for (int k = 0; k < N; ++k) {
-    wt[k] = fabs((double)__double2float_rn(row[k]));
+    wt[k] = fabs((double)to_f32(row[k]));
     live[k] = wt[k] > 0.0;
     slot[k] = k;
     if (live[k]) {
@@ -64,7 +114,8 @@ __device__ __noinline__ void make_tree(const double* row, uint32_t* tw) {
       last = k;
     }
   }
-  for (int q = 0; q < (N + 3) / 4; ++q) tw[q] = 0u;
+  uint32_t w[(N + 3) / 4];
+  for (int q = 0; q < (N + 3) / 4; ++q) w[q] = 0u;
   int nodes = N, s = 0;
   while (n_live > 1) {
     int f = -1, g = -1;
@@ -73,7 +124,7 @@ __device__ __noinline__ void make_tree(const double* row, uint32_t* tw) {
     for (int id = 0; id < nodes; ++id)
       if (live[id] && id != f && (g < 0 || wt[id] < wt[g])) g = id;
     const uint32_t byte = (uint32_t)slot[f] | ((uint32_t)slot[g] << 4);
-    tw[(s + 1) >> 2] |= byte << (8 * ((s + 1) & 3));
+    w[(s + 1) >> 2] |= byte << (8 * ((s + 1) & 3));
     wt[nodes] = __dadd_rn(wt[f], wt[g]);
     slot[nodes] = slot[f];
     live[nodes] = true;
@@ -84,328 +135,382 @@ __device__ __noinline__ void make_tree(const double* row, uint32_t* tw) {
     --n_live;
   }
   const int root = s == 0 ? last : slot[nodes - 1];
-  tw[0] |= (uint32_t)s | ((uint32_t)root << 4);
+  w[0] |= (uint32_t)s | ((uint32_t)root << 4);
+  for (int q = 0; q < (N + 3) / 4; ++q) tw[q] = w[q];
 }
 
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float to_f32(float v) { return v; }
-__device__ __forceinline__ float to_f32(double v) { return __double2float_rn(v); }
+// N coefficients of a shared-memory row (16-byte aligned, zero-padded) in
+// 16-byte loads.
+template <int N>
+__device__ __forceinline__ void load_row(const float* s, float (&c)[N]) {
+  constexpr int NP = pad_to(N, 4);
+  float t[NP];
+#pragma unroll
+  for (int q = 0; q < NP / 4; ++q) {
+    const float4 v = reinterpret_cast<const float4*>(s)[q];
+    t[4 * q] = v.x;
+    t[4 * q + 1] = v.y;
+    t[4 * q + 2] = v.z;
+    t[4 * q + 3] = v.w;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) c[k] = t[k];
+}
+template <int N>
+__device__ __forceinline__ void load_row(const double* s, double (&c)[N]) {
+  constexpr int NP = pad_to(N, 2);
+  double t[NP];
+#pragma unroll
+  for (int q = 0; q < NP / 2; ++q) {
+    const double2 v = reinterpret_cast<const double2*>(s)[q];
+    t[2 * q] = v.x;
+    t[2 * q + 1] = v.y;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) c[k] = t[k];
+}
 
-// Shared-memory slot q of this thread is sv[q * kOrderThreads].
+// Byte offset, from this lane's slot 0, of slot q.
+template <typename T>
+__host__ __device__ constexpr uint32_t slot_off(int q) {
+  return (uint32_t)q * 32u * (uint32_t)sizeof(T);
+}
+
+// Lock-step merge program of NR rows of N entries (row j's slots are
+// j * N .. j * N + N - 1): step s holds one word per row, (first slot's byte
+// offset) | (second slot's byte offset) << 16 for row j's merge s, or the
+// dummy slot twice once row j has no merge s left; roots[j] = the byte
+// offset of row j's root.  Lane j < NR writes row j's column from its tree;
+// returns the step count (the largest merge count), the same in every lane.
+template <int N, int NR, int NRP, int W, typename T>
+__device__ __forceinline__ int make_program(const uint32_t* trees, uint32_t* prog,
+                                            uint32_t* roots, int dummy) {
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+  if (lane < NR) cnt = (int)(trees[lane * W] & 15u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(kFull, cnt, o));
+  if (lane < NR) {
+    const uint32_t* tw = trees + lane * W;
+    const int mine = (int)(tw[0] & 15u);
+    for (int s = 0; s < cnt; ++s) {
+      uint32_t op = slot_off<T>(dummy) | (slot_off<T>(dummy) << 16);
+      if (s < mine) {
+        const uint32_t b = (tw[(s + 1) >> 2] >> (8 * ((s + 1) & 3))) & 255u;
+        op = slot_off<T>(lane * N + (int)(b & 15u)) |
+             (slot_off<T>(lane * N + (int)(b >> 4)) << 16);
+      }
+      prog[s * NRP + lane] = op;
+    }
+    roots[lane] = slot_off<T>(lane * N + (int)((tw[0] >> 4) & 15u));
+  }
+  return cnt;
+}
+
+// Slot q of this lane is sv[q * 32].
 //
-// tree_apply: out[v * os] = sum_k c[k] x[v * xv + k * xk] for v < NV, all
-// along the one tree tw.  The NV sums are independent chains, merged in
-// lock step: per merge the 2 NV loads issue before the NV stores, so the
-// chains overlap instead of waiting on one another.
-template <int N, int NV, typename T, typename X>
-__device__ __forceinline__ void tree_apply(const T* c, const X* x, int xv, int xk,
-                                           const uint32_t* tw, T* sv, T* out, int os) {
+// tree_apply: out[v] = sum_k c[k] x[v * xv + k * xk] for v < NV, all along
+// the tree of row j of a row set: its merges are column j of the set's
+// program (make_program), its merge count is word 0 of its packed tree tw,
+// its root offset roots[j].  Those offsets address slots j * N + ..., so the
+// slot base moves back by j * N slots; vector v uses slots v * N + ....  The
+// NV sums are independent chains merged in lock step: per merge the 2 NV
+// loads issue before the NV stores.
+template <int N, int NV, int NRP, typename T, typename X>
+__device__ __forceinline__ void tree_apply(const T* c_s, const X* x, int xv, int xk,
+                                           const uint32_t* prog, const uint32_t* roots,
+                                           const uint32_t* tw, int j, T* sv, T (&out)[NV]) {
+  T c[N];
+  load_row<N>(c_s, c);
 #pragma unroll
   for (int v = 0; v < NV; ++v)
 #pragma unroll
-    for (int k = 0; k < N; ++k)
-      sv[(v * N + k) * kOrderThreads] = mul_rn(c[k], (T)x[v * xv + k * xk]);
-  const uint32_t w0 = tw[0];
-  const int cnt = (int)(w0 & 15u);
-  uint32_t cur = w0 >> 8;  // merge bytes still unread in the current word
-  int left = 3, q = 0;
+    for (int k = 0; k < N; ++k) sv[(v * N + k) * 32] = mul_rn(c[k], (T)x[v * xv + k * xk]);
+  char* svb = reinterpret_cast<char*>(sv) - slot_off<T>(j * N);
+  const int cnt = (int)(tw[0] & 15u);
 #pragma unroll 1
   for (int s = 0; s < cnt; ++s) {
-    if (left == 0) {
-      cur = tw[++q];
-      left = 4;
-    }
-    const int a = (int)(cur & 15u), b = (int)((cur >> 4) & 15u);
-    cur >>= 8;
-    --left;
+    const uint32_t op = prog[s * NRP + j];
+    char* pa = svb + (op & 0xffffu);
+    const char* pb = svb + (op >> 16);
     T va[NV], vb[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      va[v] = sv[(v * N + a) * kOrderThreads];
-      vb[v] = sv[(v * N + b) * kOrderThreads];
+      va[v] = *reinterpret_cast<const T*>(pa + slot_off<T>(v * N));
+      vb[v] = *reinterpret_cast<const T*>(pb + slot_off<T>(v * N));
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sv[(v * N + a) * kOrderThreads] = add_rn(va[v], vb[v]);
+    for (int v = 0; v < NV; ++v) *reinterpret_cast<T*>(pa + slot_off<T>(v * N)) = add_rn(va[v], vb[v]);
   }
-  const int root = (int)((w0 >> 4) & 15u);
+  const char* pr = svb + roots[j];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) out[v * os] = sv[(v * N + root) * kOrderThreads];
+  for (int v = 0; v < NV; ++v) out[v] = *reinterpret_cast<const T*>(pr + slot_off<T>(v * N));
 }
 
-// rows_apply: out[j] = sum_k c[j * N + k] x[k] for j < NR, row j along its
-// own tree trees[j]; the rows' merges run in lock step like tree_apply's.
-template <int N, int NR, typename T, typename X>
-__device__ __forceinline__ void rows_apply(const T* c, const X* x, const Tree<N>* trees, T* sv,
-                                           T* out) {
-#pragma unroll
-  for (int j = 0; j < NR; ++j)
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-      sv[(j * N + k) * kOrderThreads] = mul_rn(c[j * N + k], (T)x[k]);
-  uint32_t cur[NR];
-  int cnt[NR], left[NR], q[NR];
-  int most = 0;
+// rows_apply: out[j] = sum_k c[j][k] x[k] for j < NR (row stride S), row j
+// along its own tree, by the lock-step program `prog` of `steps` steps
+// (make_program): per step all NR loads pairs issue before the NR stores.
+template <int N, int NR, int NRP, int S, typename T, typename X>
+__device__ __forceinline__ void rows_apply(const T* c_s, const X* x, const uint32_t* prog,
+                                           int steps, const uint32_t* roots, T* sv,
+                                           T (&out)[NR]) {
 #pragma unroll
   for (int j = 0; j < NR; ++j) {
-    const uint32_t w0 = trees[j].w[0];
-    cnt[j] = (int)(w0 & 15u);
-    cur[j] = w0 >> 8;
-    left[j] = 3;
-    q[j] = 0;
-    most = max(most, cnt[j]);
+    T c[N];
+    load_row<N>(c_s + j * S, c);
+#pragma unroll
+    for (int k = 0; k < N; ++k) sv[(j * N + k) * 32] = mul_rn(c[k], (T)x[k]);
   }
+  char* svb = reinterpret_cast<char*>(sv);
 #pragma unroll 1
-  for (int s = 0; s < most; ++s) {
-    int a[NR], b[NR];
+  for (int s = 0; s < steps; ++s) {
+    uint32_t op[NRP];
+#pragma unroll
+    for (int q = 0; q < NRP / 4; ++q) {
+      const uint4 w = reinterpret_cast<const uint4*>(prog + s * NRP)[q];
+      op[4 * q] = w.x;
+      op[4 * q + 1] = w.y;
+      op[4 * q + 2] = w.z;
+      op[4 * q + 3] = w.w;
+    }
     T va[NR], vb[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      if (s < cnt[j]) {
-        if (left[j] == 0) {
-          cur[j] = trees[j].w[++q[j]];
-          left[j] = 4;
-        }
-        a[j] = (int)(cur[j] & 15u);
-        b[j] = (int)((cur[j] >> 4) & 15u);
-        cur[j] >>= 8;
-        --left[j];
-        va[j] = sv[(j * N + a[j]) * kOrderThreads];
-        vb[j] = sv[(j * N + b[j]) * kOrderThreads];
-      }
+      va[j] = *reinterpret_cast<const T*>(svb + (op[j] & 0xffffu));
+      vb[j] = *reinterpret_cast<const T*>(svb + (op[j] >> 16));
     }
 #pragma unroll
-    for (int j = 0; j < NR; ++j)
-      if (s < cnt[j]) sv[(j * N + a[j]) * kOrderThreads] = add_rn(va[j], vb[j]);
+    for (int j = 0; j < NR; ++j) *reinterpret_cast<T*>(svb + (op[j] & 0xffffu)) = add_rn(va[j], vb[j]);
   }
 #pragma unroll
-  for (int j = 0; j < NR; ++j)
-    out[j] = sv[(j * N + (int)((trees[j].w[0] >> 4) & 15u)) * kOrderThreads];
+  for (int j = 0; j < NR; ++j) out[j] = *reinterpret_cast<const T*>(svb + roots[j]);
 }
 
+// The FP32 L1 error of trial record r (layout of sweep_eval.cuh) in this
+// lane, against the instance in shared memory at `base`.
 template <int DIM, int M, int R, typename T>
-struct OrderEval;
-
-// 1D: u = G g, v = B^T d, p = u .* v (FP32), y = A^T p.
-template <int M, int R, typename T>
-__device__ __forceinline__ float order_err_1d(const OrderEval<1, M, R, T>& Q,
-                                              const float* __restrict__ rc) {
-  constexpr int A = M + R - 1;
-  const float* g = rc;
-  const float* d = rc + R;
-  const float* yh = d + A;
-  const float* yl = yh + M;
-  T u[A], v[A], y[M];
-  rows_apply<R, A>(Q.G, g, Q.tG, Q.sv, u);
-  rows_apply<A, A>(Q.BT, d, Q.tB, Q.sv, v);
-  float p[A];
+__device__ __forceinline__ float order_trial(const unsigned char* base, const float* __restrict__ r,
+                                             T* sv, float* pl, int sg, int sb, int sa) {
+  using L = OrderLayout<DIM, M, R, T>;
+  using S = SweepShape<DIM, M, R>;
+  constexpr int A = L::A;
+  const T* Gs = reinterpret_cast<const T*>(base + L::G_OFF);
+  const T* BTs = reinterpret_cast<const T*>(base + L::BT_OFF);
+  const T* ATs = reinterpret_cast<const T*>(base + L::AT_OFF);
+  const uint32_t* tG = reinterpret_cast<const uint32_t*>(base + L::TG_OFF);
+  const uint32_t* tB = reinterpret_cast<const uint32_t*>(base + L::TB_OFF);
+  const uint32_t* tA = reinterpret_cast<const uint32_t*>(base + L::TA_OFF);
+  const uint32_t* pG = reinterpret_cast<const uint32_t*>(base + L::PG_OFF);
+  const uint32_t* pB = reinterpret_cast<const uint32_t*>(base + L::PB_OFF);
+  const uint32_t* pA = reinterpret_cast<const uint32_t*>(base + L::PA_OFF);
+  const uint32_t* rG = reinterpret_cast<const uint32_t*>(base + L::RG_OFF);
+  const uint32_t* rB = reinterpret_cast<const uint32_t*>(base + L::RB_OFF);
+  const uint32_t* rA = reinterpret_cast<const uint32_t*>(base + L::RA_OFF);
+  // g and d in 16-byte loads (the record is 16-byte aligned)
+  constexpr int NIN = pad_to(S::NG + S::ND, 4);
+  float in[NIN];
 #pragma unroll
-  for (int i = 0; i < A; ++i) p[i] = __fmul_rn(to_f32(u[i]), to_f32(v[i]));
-  rows_apply<A, M>(Q.AT, p, Q.tA, Q.sv, y);
+  for (int q = 0; q < NIN / 4; ++q) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(r) + q);
+    in[4 * q] = v.x;
+    in[4 * q + 1] = v.y;
+    in[4 * q + 2] = v.z;
+    in[4 * q + 3] = v.w;
+  }
+  const float* g = in;
+  const float* d = in + S::NG;
+  const float* yh = r + S::NG + S::ND;
+  const float* yl = yh + S::NO;
   float e = 0.0f;
+  if constexpr (DIM == 1) {
+    // u = G g, v = B^T d, p = u .* v (FP32), y = A^T p
+    T u[A], v[A], y[M];
+    rows_apply<R, A, L::A4, L::GS>(Gs, g, pG, sg, rG, sv, u);
+    rows_apply<A, A, L::A4, L::BS>(BTs, d, pB, sb, rB, sv, v);
+    float p[A];
 #pragma unroll
-  for (int j = 0; j < M; ++j) e = __fadd_rn(e, abs_err(to_f32(y[j]), yh[j], yl[j]));
+    for (int i = 0; i < A; ++i) p[i] = __fmul_rn(to_f32(u[i]), to_f32(v[i]));
+    rows_apply<A, M, L::M4, L::BS>(ATs, p, pA, sa, rA, sv, y);
+#pragma unroll
+    for (int j = 0; j < M; ++j) e = __fadd_rn(e, abs_err(to_f32(y[j]), __ldg(yh + j), __ldg(yl + j)));
+  } else {
+    // per frequency row i: W_i = G_i g, U_i = W_i G^T, T_i = B^T_i d,
+    // V_i = T_i B, P_i = U_i .* V_i (FP32, to shared memory); then per output
+    // row a: Z_a = A^T_a P, Y_a = Z_a A, errors in row-major order
+#pragma unroll 1
+    for (int i = 0; i < A; ++i) {
+      T Wi[R], Ui[A], Ti[A], Vi[A];
+      tree_apply<R, R, L::A4>(Gs + i * L::GS, g, 1, R, pG, rG, tG + i * L::WG, i, sv, Wi);
+      rows_apply<R, A, L::A4, L::GS>(Gs, Wi, pG, sg, rG, sv, Ui);
+      tree_apply<A, A, L::A4>(BTs + i * L::BS, d, 1, A, pB, rB, tB + i * L::WB, i, sv, Ti);
+      rows_apply<A, A, L::A4, L::BS>(BTs, Ti, pB, sb, rB, sv, Vi);
+#pragma unroll
+      for (int j = 0; j < A; ++j) pl[(i * A + j) * 32] = __fmul_rn(to_f32(Ui[j]), to_f32(Vi[j]));
+    }
+#pragma unroll 1
+    for (int a = 0; a < M; ++a) {
+      T Za[A], Ya[M];
+      tree_apply<A, A, L::M4>(ATs + a * L::BS, pl, 32, A * 32, pA, rA, tA + a * L::WB, a, sv,
+                              Za);
+      rows_apply<A, M, L::M4, L::BS>(ATs, Za, pA, sa, rA, sv, Ya);
+#pragma unroll
+      for (int b = 0; b < M; ++b)
+        e = __fadd_rn(e, abs_err(to_f32(Ya[b]), __ldg(yh + a * M + b), __ldg(yl + a * M + b)));
+    }
+  }
   return e;
 }
 
-// 2D, each pass one matrix row's tree over all the vectors it multiplies:
-// W = G g (row i of G over the columns of g), U = W G^T (row j of G over
-// the rows of W), T = B^T d, V = T B, P = U .* V (FP32), Z = A^T P,
-// Y = Z A; the per-trial error summed over Y in row-major order.
-template <int M, int R, typename T>
-__device__ __forceinline__ float order_err_2d(const OrderEval<2, M, R, T>& Q,
-                                              const float* __restrict__ rc) {
-  constexpr int A = M + R - 1;
-  const float* g = rc;
-  const float* d = rc + R * R;
-  const float* yh = d + A * A;
-  const float* yl = yh + M * M;
-  T W[A * R], U[A * A], Tm[A * A], Z[M * A];
-  float P[A * A], Y[M * M];
-#pragma unroll 1
-  for (int i = 0; i < A; ++i)  // W[i][k] = sum_l G[i][l] g[l][k]
-    tree_apply<R, R>(&Q.G[i * R], g, 1, R, Q.tG[i].w, Q.sv, &W[i * R], 1);
-#pragma unroll 1
-  for (int j = 0; j < A; ++j)  // U[i][j] = sum_k W[i][k] G[j][k]
-    tree_apply<R, A>(&Q.G[j * R], W, R, 1, Q.tG[j].w, Q.sv, &U[j], A);
-#pragma unroll 1
-  for (int i = 0; i < A; ++i)  // T[i][l] = sum_k BT[i][k] d[k][l]
-    tree_apply<A, A>(&Q.BT[i * A], d, 1, A, Q.tB[i].w, Q.sv, &Tm[i * A], 1);
-#pragma unroll 1
-  for (int j = 0; j < A; ++j) {  // V[i][j] = sum_l T[i][l] BT[j][l]; P = U .* V
-    T Vj[A];
-    tree_apply<A, A>(&Q.BT[j * A], Tm, A, 1, Q.tB[j].w, Q.sv, Vj, 1);
-#pragma unroll
-    for (int i = 0; i < A; ++i) P[i * A + j] = __fmul_rn(to_f32(U[i * A + j]), to_f32(Vj[i]));
+// One instance on one warp: sorted finite points a[0..alpha-2] (the same in
+// every lane) -> err = sum_t ||yhat_t - y_t||_1 / ysum, +inf when two points
+// coincide.  Not inlined: both kernels run this one body.
+template <int DIM, int M, int R, typename T>
+__device__ __noinline__ double order_instance(const double* a, unsigned char* base,
+                                              const float* __restrict__ rec, int trials,
+                                              double ysum) {
+  using L = OrderLayout<DIM, M, R, T>;
+  constexpr int A = L::A;
+  const int lane = threadIdx.x & 31;
+  T* Gs = reinterpret_cast<T*>(base + L::G_OFF);
+  T* BTs = reinterpret_cast<T*>(base + L::BT_OFF);
+  T* ATs = reinterpret_cast<T*>(base + L::AT_OFF);
+  int ok = 0;
+  if (lane == 0) {  // the FP64 matrices, stored as T with zero-padded rows
+    double ATd[M * A], Gd[A * R], BTd[A * A];
+    ok = build_matrices<double>(a, M, R, ATd, Gd, BTd) ? 1 : 0;
+    if (ok) {
+      for (int i = 0; i < A; ++i)
+        for (int k = 0; k < L::GS; ++k)
+          Gs[i * L::GS + k] = k < R ? from_f64(Gd[i * R + k], (T*)nullptr) : (T)0;
+      for (int i = 0; i < A; ++i)
+        for (int k = 0; k < L::BS; ++k)
+          BTs[i * L::BS + k] = k < A ? from_f64(BTd[i * A + k], (T*)nullptr) : (T)0;
+      for (int j = 0; j < M; ++j)
+        for (int k = 0; k < L::BS; ++k)
+          ATs[j * L::BS + k] = k < A ? from_f64(ATd[j * A + k], (T*)nullptr) : (T)0;
+    }
   }
-#pragma unroll 1
-  for (int a = 0; a < M; ++a)  // Z[a][j] = sum_i AT[a][i] P[i][j]
-    tree_apply<A, A>(&Q.AT[a * A], P, 1, A, Q.tA[a].w, Q.sv, &Z[a * A], 1);
-#pragma unroll 1
-  for (int b = 0; b < M; ++b) {  // Y[a][b] = sum_j Z[a][j] AT[b][j]
-    T Yb[M];
-    tree_apply<A, M>(&Q.AT[b * A], Z, A, 1, Q.tA[b].w, Q.sv, Yb, 1);
+  ok = __shfl_sync(kFull, ok, 0);
+  if (!ok) return (double)INFINITY;
+  __syncwarp();
+  // one tree per lane: G rows, then B^T rows, then A^T rows
+  if (lane < A)
+    make_tree<R>(Gs + lane * L::GS, reinterpret_cast<uint32_t*>(base + L::TG_OFF) + lane * L::WG);
+  else if (lane < 2 * A)
+    make_tree<A>(BTs + (lane - A) * L::BS,
+                 reinterpret_cast<uint32_t*>(base + L::TB_OFF) + (lane - A) * L::WB);
+  else if (lane < 2 * A + M)
+    make_tree<A>(ATs + (lane - 2 * A) * L::BS,
+                 reinterpret_cast<uint32_t*>(base + L::TA_OFF) + (lane - 2 * A) * L::WB);
+  __syncwarp();
+  // the lock-step programs of the three row sets
+  auto u32 = [&](size_t off) { return reinterpret_cast<uint32_t*>(base + off); };
+  const int dummy = L::NSLOT - 1;
+  const int sg = make_program<R, A, L::A4, L::WG, T>(u32(L::TG_OFF), u32(L::PG_OFF),
+                                                     u32(L::RG_OFF), dummy);
+  const int sb = make_program<A, A, L::A4, L::WB, T>(u32(L::TB_OFF), u32(L::PB_OFF),
+                                                     u32(L::RB_OFF), dummy);
+  const int sa = make_program<A, M, L::M4, L::WB, T>(u32(L::TA_OFF), u32(L::PA_OFF),
+                                                     u32(L::RA_OFF), dummy);
+  __syncwarp();
+  T* sv = reinterpret_cast<T*>(base + L::SL_OFF) + lane;
+  float* pl = reinterpret_cast<float*>(base + L::P_OFF) + lane;
+  constexpr int REC = SweepShape<DIM, M, R>::REC;
+  double num = 0.0;
+  for (int t = lane; t < trials; t += 32)
+    num += (double)order_trial<DIM, M, R, T>(base, rec + (int64_t)t * REC, sv, pl, sg, sb, sa);
 #pragma unroll
-    for (int a = 0; a < M; ++a) Y[a * M + b] = to_f32(Yb[a]);
-  }
-  float e = 0.0f;
-#pragma unroll
-  for (int q = 0; q < M * M; ++q) e = __fadd_rn(e, abs_err(Y[q], yh[q], yl[q]));
-  return e;
+  for (int o = 16; o > 0; o >>= 1) num += __shfl_xor_sync(kFull, num, o);
+  return num / ysum;
 }
 
-// One instance: its matrices (FP32 for the FP32 form, FP64 for the mixed
-// form), its trees, and this thread's shared-memory slots.
+// Mask sweep: one warp per (valid mask, c) instance.
 template <int DIM, int M, int R, typename T>
-struct OrderEval {
-  static constexpr int A = M + R - 1;
-  static constexpr int REC = SweepShape<DIM, M, R>::REC;
-  T AT[M * A], G[A * R], BT[A * A];
-  Tree<R> tG[A];
-  Tree<A> tB[A];
-  Tree<A> tA[M];
-  T* sv;
-  __device__ __forceinline__ float operator()(const float* buf) const {
-    if constexpr (DIM == 1)
-      return order_err_1d<M, R, T>(*this, buf);
-    else
-      return order_err_2d<M, R, T>(*this, buf);
-  }
-};
-
-__device__ __forceinline__ float from_f64(double v, float*) { return __double2float_rn(v); }
-__device__ __forceinline__ double from_f64(double v, double*) { return v; }
-
-// Builds the instance from sorted finite points a[0..alpha-2]; false when
-// two coincide (the matrices are then all zero).
-template <int DIM, int M, int R, typename T>
-__device__ __forceinline__ bool order_build(const double* a, OrderEval<DIM, M, R, T>& Q) {
-  constexpr int A = M + R - 1;
-  double ATd[M * A], Gd[A * R], BTd[A * A];
-#pragma unroll
-  for (int i = 0; i < M * A; ++i) ATd[i] = 0.0;
-#pragma unroll
-  for (int i = 0; i < A * R; ++i) Gd[i] = 0.0;
-#pragma unroll
-  for (int i = 0; i < A * A; ++i) BTd[i] = 0.0;
-  const bool ok = build_matrices<double>(a, M, R, ATd, Gd, BTd);
-#pragma unroll
-  for (int i = 0; i < M * A; ++i) Q.AT[i] = from_f64(ATd[i], (T*)nullptr);
-#pragma unroll
-  for (int i = 0; i < A * R; ++i) Q.G[i] = from_f64(Gd[i], (T*)nullptr);
-#pragma unroll
-  for (int i = 0; i < A * A; ++i) Q.BT[i] = from_f64(BTd[i], (T*)nullptr);
-  for (int i = 0; i < A; ++i) make_tree<R>(&Gd[i * R], Q.tG[i].w);
-  for (int i = 0; i < A; ++i) make_tree<A>(&BTd[i * A], Q.tB[i].w);
-  for (int j = 0; j < M; ++j) make_tree<A>(&ATd[j * A], Q.tA[j].w);
-  return ok;
-}
-
-// One lane's instance from its sorted finite points a[0..alpha-2], over
-// trial chunks [ch0, ch1) (lane_eval_ev's contract).  Not inlined: both
-// kernels below run this one body.
-template <int DIM, int M, int R, typename T>
-__device__ __noinline__ void order_lane(const double* a, T* sv, const float* __restrict__ rec,
-                                        int trials, int ch0, int ch1, double ysum, bool partial,
-                                        double* __restrict__ out, int64_t stride, bool active) {
-  OrderEval<DIM, M, R, T> Q;
-  Q.sv = sv;
-  const bool ok = order_build<DIM, M, R, T>(a, Q);
-  lane_eval_ev(Q, ok, rec, trials, ch0, ch1, ysum, partial, out, stride, active);
-}
-
-// Mask sweep: the grid of k_sweep_eval (one warp per valid mask, block of
-// 32 c values and chunk group; lanes own instances).
-template <int DIM, int M, int R, typename T>
-__global__ void __launch_bounds__(kOrderThreads)
+__global__ void __launch_bounds__(kOrderThreads, 3)
     k_order_sweep(const float* __restrict__ rec, int trials, const double* __restrict__ c_grid,
                   int n_c, double d, const MaskList masks, const double* __restrict__ ysum,
-                  double* __restrict__ err, int split, int ch_per, double* __restrict__ part,
-                  int64_t n_out) {
-  constexpr int A = M + R - 1;
+                  double* __restrict__ err) {
+  using L = OrderLayout<DIM, M, R, T>;
   extern __shared__ __align__(16) unsigned char order_smem[];
-  T* sv = reinterpret_cast<T*>(order_smem);  // A * A slots per thread
-  const int lane = threadIdx.x & 31;
-  const int nblk = (n_c + 31) >> 5;
-  const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (item >= (int64_t)masks.n * nblk * split) return;
-  const int grp = (int)(item % split);
-  const int cell = (int)(item / split);
-  const int qv = cell / nblk;
-  const int ci = (cell - qv * nblk) * 32 + lane;
-  const bool active = ci < n_c;
-  const double c = active ? c_grid[ci] : c_grid[0];
-  const int64_t o = (int64_t)masks.q[qv] * n_c + ci;
-  const int nch = trial_chunks(trials);
-  const int ch0 = split == 1 ? 0 : grp * ch_per;
-  const int ch1 = split == 1 ? nch : min(ch0 + ch_per, nch);
+  const int warp = threadIdx.x >> 5;
+  const int64_t inst = (int64_t)blockIdx.x * kOrderWarps + warp;
+  if (inst >= (int64_t)masks.n * n_c) return;  // the whole warp
+  const int qv = (int)(inst / n_c);
+  const int ci = (int)(inst - (int64_t)qv * n_c);
   double pts[kMaxAlpha];
-  mask_points(masks.mask[qv], A, c, d, pts);  // valid: the host kept valid masks only
-  order_lane<DIM, M, R, T>(pts, sv + threadIdx.x, rec, trials, ch0, ch1, *ysum, split > 1,
-                           split == 1 ? err + o : part + o, n_out, active);
+  mask_points(masks.mask[qv], L::A, c_grid[ci], d, pts);  // valid: the host kept valid masks
+  const double e =
+      order_instance<DIM, M, R, T>(pts, order_smem + warp * L::BYTES, rec, trials, *ysum);
+  if ((threadIdx.x & 31) == 0) err[(int64_t)masks.q[qv] * n_c + ci] = e;
 }
 
-// Explicit point sets, one lane per set.
+// Explicit point sets: one warp per set.
 template <int DIM, int M, int R, typename T>
-__global__ void __launch_bounds__(kOrderThreads)
+__global__ void __launch_bounds__(kOrderThreads, 3)
     k_order_pointset(const float* __restrict__ rec, int trials, const double* __restrict__ pts,
                      int n_sets, const double* __restrict__ ysum, double* __restrict__ err) {
-  constexpr int A = M + R - 1;
+  using L = OrderLayout<DIM, M, R, T>;
   extern __shared__ __align__(16) unsigned char order_smem[];
-  T* sv = reinterpret_cast<T*>(order_smem);  // A * A slots per thread
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = s < n_sets;
-  const int ss = active ? s : 0;
+  const int warp = threadIdx.x >> 5;
+  const int s = blockIdx.x * kOrderWarps + warp;
+  if (s >= n_sets) return;  // the whole warp
   double a[kMaxAlpha];
-#pragma unroll
-  for (int i = 0; i < A - 1; ++i) a[i] = pts[(int64_t)ss * (A - 1) + i];
-  order_lane<DIM, M, R, T>(a, sv + threadIdx.x, rec, trials, 0, trial_chunks(trials), *ysum,
-                           false, err + ss, 0, active);
+  for (int i = 0; i < L::A - 1; ++i) a[i] = pts[(int64_t)s * (L::A - 1) + i];
+  const double e = order_instance<DIM, M, R, T>(a, order_smem + warp * L::BYTES, rec, trials,
+                                                *ysum);
+  if ((threadIdx.x & 31) == 0) err[s] = e;
 }
 
 }  // namespace
 
-// Dynamic shared memory of the order kernels of size (m, r): A * A value
-// slots per thread.
+// Launches of one value type T (float: the FP32 Huffman form, double: the
+// mixed form).  Each kernel is allowed its dynamic shared memory (above the
+// 48 KB default for the larger sizes) before its first launch.
 template <typename T>
-inline size_t order_smem_bytes_t(int m, int r) {
-  const size_t a = (size_t)(m + r - 1);
-  return a * a * kOrderThreads * sizeof(T);
-}
-
-// The kernel tables of one value type T (float: the FP32 Huffman form,
-// double: the mixed form); each kernel returned is allowed its dynamic
-// shared memory (above the 48 KB default for the larger sizes).
-template <typename T>
-EvalFn order_sweep_kernel_t(int dim, int m, int r) {
-  EvalFn fn = nullptr;
-#define WINO_ORDER_CASE(I, D, MM, RR) \
-  if (dim == D && m == MM && r == RR) fn = k_order_sweep<D, MM, RR, T>;
+int order_sweep_launch_t(const SweepSize& s, const float* rec, int trials, const double* c_grid,
+                         int n_c, const MaskList& masks, const double* ysum, double* err,
+                         cudaStream_t st) {
+  const int64_t n = (int64_t)masks.n * n_c;
+  if (n == 0) return WINO_OK;
+  const unsigned grid = (unsigned)((n + kOrderWarps - 1) / kOrderWarps);
+#define WINO_ORDER_CASE(I, D, MM, RR)                                                       \
+  if (s.dim == D && s.m == MM && s.r == RR) {                                                \
+    const size_t smem = kOrderWarps * OrderLayout<D, MM, RR, T>::BYTES;                      \
+    WINO_CUDA_TRY(cudaFuncSetAttribute((const void*)k_order_sweep<D, MM, RR, T>,             \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                       (int)smem));                                          \
+    k_order_sweep<D, MM, RR, T><<<grid, kOrderThreads, smem, st>>>(rec, trials, c_grid, n_c, \
+                                                                   s.d, masks, ysum, err);   \
+    note_launches(1);                                                                        \
+    WINO_CUDA_TRY(cudaGetLastError());                                                       \
+    return WINO_OK;                                                                          \
+  }
   WINO_SWEEP_SIZES(WINO_ORDER_CASE)
 #undef WINO_ORDER_CASE
-  if (fn && cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)order_smem_bytes_t<T>(m, r)) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return nullptr;
-  }
-  return fn;
+  return WINO_EUNSUPPORTED;
 }
 
 template <typename T>
-PointsetFn order_pointset_kernel_t(int dim, int m, int r) {
-  PointsetFn fn = nullptr;
-#define WINO_ORDER_CASE(I, D, MM, RR) \
-  if (dim == D && m == MM && r == RR) fn = k_order_pointset<D, MM, RR, T>;
+int order_pointset_launch_t(int dim, int m, int r, const float* rec, int trials,
+                            const double* pts, int n_sets, const double* ysum, double* err,
+                            cudaStream_t st) {
+  if (n_sets <= 0) return WINO_OK;
+  const unsigned grid = (unsigned)((n_sets + kOrderWarps - 1) / kOrderWarps);
+#define WINO_ORDER_CASE(I, D, MM, RR)                                                         \
+  if (dim == D && m == MM && r == RR) {                                                        \
+    const size_t smem = kOrderWarps * OrderLayout<D, MM, RR, T>::BYTES;                        \
+    WINO_CUDA_TRY(cudaFuncSetAttribute((const void*)k_order_pointset<D, MM, RR, T>,            \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                                       (int)smem));                                            \
+    k_order_pointset<D, MM, RR, T><<<grid, kOrderThreads, smem, st>>>(rec, trials, pts, n_sets, \
+                                                                      ysum, err);              \
+    note_launches(1);                                                                          \
+    WINO_CUDA_TRY(cudaGetLastError());                                                         \
+    return WINO_OK;                                                                            \
+  }
   WINO_SWEEP_SIZES(WINO_ORDER_CASE)
 #undef WINO_ORDER_CASE
-  if (fn && cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)order_smem_bytes_t<T>(m, r)) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return nullptr;
-  }
-  return fn;
+  return WINO_EUNSUPPORTED;
 }
 
 }  // namespace wino

@@ -4,25 +4,31 @@
 
 namespace wino {
 
-EvalFn order_sweep_kernel_f64(int dim, int m, int r);        // sweep_order_f64.cu
-PointsetFn order_pointset_kernel_f64(int dim, int m, int r);  // sweep_order_f64.cu
+int order_sweep_launch_f64(const SweepSize& s, const float* rec, int trials,
+                           const double* c_grid, int n_c, const MaskList& masks,
+                           const double* ysum, double* err, cudaStream_t st);  // _f64.cu
+int order_pointset_launch_f64(int dim, int m, int r, const float* rec, int trials,
+                              const double* pts, int n_sets, const double* ysum, double* err,
+                              cudaStream_t st);  // _f64.cu
 
-EvalFn order_sweep_kernel(int order, int dim, int m, int r) {
-  if (order == 1) return order_sweep_kernel_t<float>(dim, m, r);
-  if (order == 2) return order_sweep_kernel_f64(dim, m, r);
-  return nullptr;
+int order_sweep_launch(int order, const SweepSize& s, const float* rec, int trials,
+                       const double* c_grid, int n_c, const MaskList& masks, const double* ysum,
+                       double* err, cudaStream_t st) {
+  if (order == 1)
+    return order_sweep_launch_t<float>(s, rec, trials, c_grid, n_c, masks, ysum, err, st);
+  if (order == 2)
+    return order_sweep_launch_f64(s, rec, trials, c_grid, n_c, masks, ysum, err, st);
+  return WINO_EINVAL;
 }
 
-PointsetFn order_pointset_kernel(int order, int dim, int m, int r) {
-  if (order == 1) return order_pointset_kernel_t<float>(dim, m, r);
-  if (order == 2) return order_pointset_kernel_f64(dim, m, r);
-  return nullptr;
-}
-
-size_t order_smem_bytes(int order, int m, int r) {
-  if (order == 1) return order_smem_bytes_t<float>(m, r);
-  if (order == 2) return order_smem_bytes_t<double>(m, r);
-  return 0;
+int order_pointset_launch(int order, int dim, int m, int r, const float* rec, int trials,
+                          const double* pts, int n_sets, const double* ysum, double* err,
+                          cudaStream_t st) {
+  if (order == 1)
+    return order_pointset_launch_t<float>(dim, m, r, rec, trials, pts, n_sets, ysum, err, st);
+  if (order == 2)
+    return order_pointset_launch_f64(dim, m, r, rec, trials, pts, n_sets, ysum, err, st);
+  return WINO_EINVAL;
 }
 
 }  // namespace wino
