@@ -231,7 +231,7 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   const int nb_prep = sweep_prepare_blocks(trials);
   for (int s = 0; s < n_sizes; ++s) {
     if (!eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)) {  // the order kernels: same sizes
-      set_error("sweep size not compiled: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6");
+      set_error("sweep size not compiled: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6, 2D r=5 m=2..4");
       return WINO_EUNSUPPORTED;
     }
     rec_off[s] = rec_total;
@@ -360,7 +360,7 @@ int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int 
                    unsigned long long seed, int order, double* err_out, cudaStream_t st) {
   PointsetFn fn = pointset_kernel(dim, m, r);  // the order kernels cover the same sizes
   if (!fn) {
-    set_error("point-set sizes: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6");
+    set_error("point-set sizes: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6, 2D r=5 m=2..4");
     return WINO_EUNSUPPORTED;
   }
   const int A = m + r - 1;

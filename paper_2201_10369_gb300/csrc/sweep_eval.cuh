@@ -303,7 +303,10 @@ int sweep_target_warps();
   X(13, 2, 3, 3)            \
   X(14, 2, 4, 3)            \
   X(15, 2, 5, 3)            \
-  X(16, 2, 6, 3)
+  X(16, 2, 6, 3)            \
+  X(17, 2, 2, 5)            \
+  X(18, 2, 3, 5)            \
+  X(19, 2, 4, 5)
 
 // Index of (dim, m, r) in WINO_SWEEP_SIZES, or -1.
 inline int sweep_kind(int dim, int m, int r) {

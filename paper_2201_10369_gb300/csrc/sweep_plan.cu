@@ -369,7 +369,7 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
     p->kind[s] = sweep_kind(z.dim, z.m, z.r);
     if (p->kind[s] < 0 || !(z.d > 0.0) || isinf(z.d)) {
       plan_free(p);
-      set_error("sweep size not compiled (1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6) or d <= 0");
+      set_error("sweep size not compiled (1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6, 2D r=5 m=2..4) or d <= 0");
       return WINO_EUNSUPPORTED;
     }
   }

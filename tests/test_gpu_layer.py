@@ -63,6 +63,19 @@ def test_layer_bitwise_vs_oracle(wino, orc, m, shape):
     assert np.array_equal(y, yo)
 
 
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 6])
+def test_layer_5x5_bitwise_vs_oracle(wino, orc, m):
+    """The 5x5-kernel column of Table 1: F(m x m, 5 x 5), alpha = m + 4 up to 10,
+    pad 2, ragged tiles: bit-identical to the oracle and at the FP32 error scale
+    against FP64 direct correlation."""
+    x, w = inputs.layer_uniform(2, 6, 5, 19, 14, r=5, seed=20 + m)
+    pts = [0.0, -0.5, 0.5, -2.0, 2.0, -1.0, 1.0, -0.25, 4.0][: m + 3] + [math.inf]
+    y = _run2d(wino, x, w, pts, m, 2)
+    assert np.array_equal(y, orc.wino_layer(x, w, 2, 2, pts, m, 5))
+    ref = orc.direct_f64(x, w, 2, 2, 5)
+    assert np.abs(y - ref).sum() / np.abs(ref).sum() < 1e-4
+
+
 @pytest.mark.parametrize("m,r", [(2, 3), (4, 3), (6, 3), (3, 5)])
 def test_layer_1d_bitwise_vs_oracle(wino, orc, m, r):
     import torch

@@ -117,7 +117,8 @@ def test_order_mask_sweep_matches_pointsets_every_size(wino, orc, order):
     (both front ends, same trials and summation order)."""
     cg = inputs.c_grid(4096)[::601]
     masks = inputs.sweep_masks()
-    for size in inputs.SWEEP_SIZES + [(1, m, 5, 2.0) for m in range(2, 7)]:
+    for size in (inputs.SWEEP_SIZES + [(1, m, 5, 2.0) for m in range(2, 7)]
+                 + [(2, m, 5, 2.0) for m in range(2, 5)]):
         dim, m, r, d = size
         mk = wino.valid_masks(size, masks)[0]
         e = wino.wino_error_sweep(cg, [size], [mk], 256, seed=5, order=order)[0, 0]

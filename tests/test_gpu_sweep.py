@@ -70,6 +70,24 @@ def test_sweep_small_grid_vs_oracle(wino, orc):
     assert exact >= 0.99 * 123 * 10
 
 
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_sweep_2d_r5_vs_oracle(wino, orc, m):
+    """2D F(m x m, 5 x 5) (the 5x5 column of Table 1) in the sweep: every
+    valid mask of the 66 with d = 2, 32 c values, 300 trials, against the
+    oracle; the same top-10 c per mask."""
+    cg = inputs.c_grid(4096)[::128]
+    size = (2, m, 5, 2.0)
+    masks = np.array(wino.valid_masks(size, inputs.sweep_masks()), np.uint8)
+    eg = wino.wino_error_sweep(cg, [size], masks, 300, seed=1)[0]
+    eo = orc.error_sweep(cg, [size], masks, 300, 1, n_threads=8)[0]
+    assert np.array_equal(np.isinf(eg), np.isinf(eo))
+    fin = np.isfinite(eo)
+    assert fin.sum() > 0.9 * eo.size
+    assert np.all(np.abs(eg[fin] - eo[fin]) <= REL * eo[fin])
+    for q in range(masks.size):
+        assert _top10_consistent(eg[q], eo[q]) >= 9
+
+
 def test_sweep_seed_and_trials_change_results(wino):
     cg = inputs.c_grid(32)
     a = wino.wino_error_sweep(cg, [(2, 4, 3, 1.0)], [0x0F], 100, seed=0)
