@@ -864,7 +864,14 @@ static int launch_split(const float* x, const float* w, float* y, const LayerGeo
 // LK MK output channels per CTA, CC channels per chunk, NS stages, MINB CTAs
 // per SM for the register budget.  The layer autotuner times each.  (A
 // 32 x 16 tile with an 8 x 8 microtile per thread and two CTAs per SM was
-// measured slower: its register cap forces spills.)
+// measured slower: its register cap forces spills.)  The shared-memory path
+// delivers one float per lane per 4 FMA lanes of the SM, so a thread tile of
+// MT x MK outputs per frequency keeps the FMA pipe busy only when
+// MT MK / (MT + MK) >= 4: the 4 x 8 tiles of the F(4x4) shapes cap it near
+// 67%.  8 x 16 tiles for F(4x4) (one frequency per thread, four frequency
+// groups per warp) need 9-warp CTAs, which three warps on one SM
+// sub-partition cap at 168 registers: measured 14-25% slower than shape 1
+// on the VGG16 stack (spills, one CTA per SM).
 #define SPLIT_M2_0 2, 2, 4, 4, 1, 8, 16, 8, 2, 1
 #define SPLIT_M4_0 4, 1, 4, 8, 3, 4, 8, 8, 2, 1
 #define SPLIT_M4_1 4, 1, 8, 4, 3, 4, 8, 8, 2, 1
