@@ -698,20 +698,29 @@ def wino_pointset_error(size, point_sets, trials: int, seed: int = 0, stream=Non
     return err
 
 
+# Sizes the sweep runs with one warp per instance only (their per-lane tile
+# does not fit the registers): no planned persistent form.
+WIDE_SWEEP_SIZES = {(2, 7, 3), (2, 8, 3)}
+
+
 def cd_sweep(dim: int, m: int, c_grid, d_grid, masks, trials: int, seed: int = 0, r: int = 3,
              mode: int = WINO_SWEEP_PERSISTENT) -> np.ndarray:
     """The two-parameter sweep (Sec. 4: the c-group {-1/c, -c, c, 1/c} with a
     subset of the d-group {-1/d, -d, d, 1/d} for larger sizes): the errors of
     every valid mask at every (d, c), err[n_d][n_masks][n_c], NaN where a
     mask is invalid for that d.  Runs as planned persistent launches of at
-    most 64 d values each (one plan size per d); the same trials as
-    wino_error_sweep for size (dim, m, r)."""
+    most 64 d values each (one plan size per d), or for the wide 2D sizes
+    F(7x7,3x3), F(8x8,3x3) as wino_error_sweep calls of 64 sizes (one per d);
+    the same trials as wino_error_sweep for size (dim, m, r)."""
     cg = np.ascontiguousarray(c_grid, dtype=np.float64)
     dg = [float(d) for d in d_grid]
     masks = [int(mk) for mk in masks]
     err = np.full((len(dg), len(masks), cg.size), np.nan)
     for d0 in range(0, len(dg), 64):
         sizes = [(dim, m, r, d) for d in dg[d0:d0 + 64]]
+        if (dim, m, r) in WIDE_SWEEP_SIZES:
+            err[d0:d0 + len(sizes)] = wino_error_sweep(cg, sizes, masks, trials, seed=seed)
+            continue
         si, mi, ks = [], [], []
         for s, size in enumerate(sizes):
             for mk in valid_masks(size, masks):

@@ -230,8 +230,10 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   size_t rec_total = 0;
   const int nb_prep = sweep_prepare_blocks(trials);
   for (int s = 0; s < n_sizes; ++s) {
-    if (!eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r)) {  // the order kernels: same sizes
-      set_error("sweep size not compiled: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6, 2D r=5 m=2..4");
+    if (!eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r) &&
+        !sweep_wide(sizes[s].dim, sizes[s].m, sizes[s].r)) {
+      set_error("sweep size not compiled: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..8, "
+                "2D r=5 m=2..4");
       return WINO_EUNSUPPORTED;
     }
     rec_off[s] = rec_total;
@@ -247,7 +249,8 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   for (int s = 0; s < n_sizes; ++s) {
     ml[s] = valid_masks(sizes[s], subsets, n_subsets);
     const int items = ml[s].n * nblk;
-    if (order == 0 && items > 0 && items < sweep_target_warps())
+    if (order == 0 && !sweep_wide(sizes[s].dim, sizes[s].m, sizes[s].r) && items > 0 &&
+        items < sweep_target_warps())
       split[s] = std::min(n_chunks, (sweep_target_warps() + items - 1) / items);
     if (split[s] > 1) n_part = std::max(n_part, (size_t)n_chunks * n_subsets * n_c);
   }
@@ -290,8 +293,10 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
     const int warps_per_block = 4;
     const unsigned grid = (unsigned)((warps + warps_per_block - 1) / warps_per_block);
     double* es = err + (size_t)s * n_out;
-    if (order != 0) {
-      ProfScope ps(kKSweepOrder, st);
+    // the Huffman orders, and the wide sizes in any order: one warp per
+    // instance (sweep_order.cuh)
+    if (order != 0 || sweep_wide(sizes[s].dim, sizes[s].m, sizes[s].r)) {
+      ProfScope ps(order != 0 ? kKSweepOrder : kKSweepEval, st);
       rc = order_sweep_launch(order, sizes[s], rec + rec_off[s], trials, cg, n_c, ml[s],
                               ysum + s, es, st);
       if (rc != WINO_OK) return rc;
@@ -358,9 +363,10 @@ static PointsetFn pointset_kernel(int dim, int m, int r) {
 // points: [n_sets][alpha-1] sorted finite points (host); err_out host.
 int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int trials,
                    unsigned long long seed, int order, double* err_out, cudaStream_t st) {
-  PointsetFn fn = pointset_kernel(dim, m, r);  // the order kernels cover the same sizes
-  if (!fn) {
-    set_error("point-set sizes: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..6, 2D r=5 m=2..4");
+  PointsetFn fn = pointset_kernel(dim, m, r);
+  const bool wide = sweep_wide(dim, m, r);
+  if (!fn && !wide) {
+    set_error("point-set sizes: 1D r=3 m=2..8, 1D r=5 m=2..6, 2D r=3 m=2..8, 2D r=5 m=2..4");
     return WINO_EUNSUPPORTED;
   }
   const int A = m + r - 1;
@@ -384,8 +390,8 @@ int pointset_error(int dim, int m, int r, const double* sorted, int n_sets, int 
                                 cudaMemcpyHostToDevice, st));
   rc = sweep_prepare(rec, part, ysum, dim, m, r, trials, seed, st);
   if (rc != WINO_OK) return rc;
-  if (order != 0) {
-    ProfScope ps(kKSweepOrder, st);
+  if (order != 0 || wide) {
+    ProfScope ps(order != 0 ? kKSweepOrder : kKSweepEval, st);
     rc = order_pointset_launch(order, dim, m, r, rec, trials, pts, n_sets, ysum, err, st);
     if (rc != WINO_OK) return rc;
   } else {

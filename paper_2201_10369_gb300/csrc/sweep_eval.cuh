@@ -263,11 +263,12 @@ typedef void (*EvalFn)(const float*, int, const double*, int, double, const Mask
 // ysum, err), one lane per set.
 typedef void (*PointsetFn)(const float*, int, const double*, int, const double*, double*);
 
-// Summation-order variants (sweep_order_f32.cu, sweep_order_f64.cu): enqueue
+// Warp-per-instance sweeps (sweep_order_f32.cu, sweep_order_f64.cu): enqueue
 // the sweep of one size's valid masks over c_grid (err[q * n_c + k] for the
 // caller's subset index q), or of n_sets explicit sorted point sets, in
-// order 1 (Huffman, FP32) or 2 (Huffman, FP64 transforms).  One warp per
-// instance; the sizes of WINO_SWEEP_SIZES, else WINO_EUNSUPPORTED.
+// order 0 (the plain fmaf order: the wide sizes only), 1 (Huffman, FP32) or
+// 2 (Huffman, FP64 transforms; orders 1 and 2 for every size of
+// WINO_SWEEP_SIZES and WINO_SWEEP_SIZES_WIDE), else WINO_EUNSUPPORTED.
 int order_sweep_launch(int order, const SweepSize& s, const float* rec, int trials,
                        const double* c_grid, int n_c, const MaskList& masks, const double* ysum,
                        double* err, cudaStream_t st);
@@ -307,6 +308,21 @@ int sweep_target_warps();
   X(17, 2, 2, 5)            \
   X(18, 2, 3, 5)            \
   X(19, 2, 4, 5)
+
+// Wide sizes: 2D F(7x7,3x3) and F(8x8,3x3) (alpha 9, 10), whose per-lane
+// tile does not fit the registers: swept only by the warp-per-instance
+// kernels of sweep_order.cuh (plain order and Huffman orders alike).
+#define WINO_SWEEP_SIZES_WIDE(X) \
+  X(20, 2, 7, 3)                 \
+  X(21, 2, 8, 3)
+
+inline bool sweep_wide(int dim, int m, int r) {
+#define WINO_WIDE_CASE(I, D, MM, RR) \
+  if (dim == D && m == MM && r == RR) return true;
+  WINO_SWEEP_SIZES_WIDE(WINO_WIDE_CASE)
+#undef WINO_WIDE_CASE
+  return false;
+}
 
 // Index of (dim, m, r) in WINO_SWEEP_SIZES, or -1.
 inline int sweep_kind(int dim, int m, int r) {

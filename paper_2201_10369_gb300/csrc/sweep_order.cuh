@@ -56,8 +56,9 @@ constexpr unsigned kFull = 0xffffffffu;
 __host__ __device__ constexpr int pad_to(int n, int v) { return (n + v - 1) / v * v; }
 __host__ __device__ constexpr size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// Byte layout of one warp's shared-memory region.
-template <int DIM, int M, int R, typename T>
+// Byte layout of one warp's shared-memory region.  HUFF = false (the plain
+// fmaf order of the wide sizes) keeps only the matrices and P.
+template <int DIM, int M, int R, typename T, bool HUFF = true>
 struct OrderLayout {
   static constexpr int A = M + R - 1;
   static constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte load
@@ -65,24 +66,24 @@ struct OrderLayout {
   static constexpr int BS = pad_to(A, V);
   static constexpr int WG = (R + 3) / 4;  // tree words per row
   static constexpr int WB = (A + 3) / 4;
-  static constexpr int NSLOT = A * A + 1;  // + one dummy slot for padded merges
+  static constexpr int NSLOT = HUFF ? A * A + 1 : 0;  // + one dummy slot for padded merges
   static constexpr int A4 = pad_to(A, 4), M4 = pad_to(M, 4);  // program row widths
   static constexpr size_t G_OFF = 0;
   static constexpr size_t BT_OFF = G_OFF + sizeof(T) * A * GS;
   static constexpr size_t AT_OFF = BT_OFF + sizeof(T) * A * BS;
   static constexpr size_t TG_OFF = AT_OFF + sizeof(T) * M * BS;
-  static constexpr size_t TB_OFF = TG_OFF + 4 * (size_t)A * WG;
-  static constexpr size_t TA_OFF = TB_OFF + 4 * (size_t)A * WB;
+  static constexpr int HW = HUFF ? 1 : 0;
+  static constexpr size_t TB_OFF = TG_OFF + 4 * (size_t)A * WG * HW;
+  static constexpr size_t TA_OFF = TB_OFF + 4 * (size_t)A * WB * HW;
   // lock-step merge programs of the three row sets (G, B^T, A^T): per step
-  // one word per row, then each row's root offset, then the step counts
-  static constexpr size_t PG_OFF = pad16(TA_OFF + 4 * (size_t)M * WB);
-  static constexpr size_t PB_OFF = PG_OFF + 4 * (size_t)(R - 1) * A4;
-  static constexpr size_t PA_OFF = PB_OFF + 4 * (size_t)(A - 1) * A4;
-  static constexpr size_t RG_OFF = PA_OFF + 4 * (size_t)(A - 1) * M4;
-  static constexpr size_t RB_OFF = RG_OFF + 4 * (size_t)A4;
-  static constexpr size_t RA_OFF = RB_OFF + 4 * (size_t)A4;
-  static constexpr size_t NS_OFF = RA_OFF + 4 * (size_t)M4;
-  static constexpr size_t SL_OFF = pad16(NS_OFF + 16);
+  // one word per row, then each row's root offset
+  static constexpr size_t PG_OFF = pad16(TA_OFF + 4 * (size_t)M * WB * HW);
+  static constexpr size_t PB_OFF = PG_OFF + 4 * (size_t)(R - 1) * A4 * HW;
+  static constexpr size_t PA_OFF = PB_OFF + 4 * (size_t)(A - 1) * A4 * HW;
+  static constexpr size_t RG_OFF = PA_OFF + 4 * (size_t)(A - 1) * M4 * HW;
+  static constexpr size_t RB_OFF = RG_OFF + 4 * (size_t)A4 * HW;
+  static constexpr size_t RA_OFF = RB_OFF + 4 * (size_t)A4 * HW;
+  static constexpr size_t SL_OFF = pad16(RA_OFF + 4 * (size_t)M4 * HW);
   static constexpr size_t P_OFF = SL_OFF + sizeof(T) * NSLOT * 32;
   static constexpr size_t BYTES = pad16(P_OFF + (DIM == 2 ? 4 * (size_t)A * A * 32 : 0));
 };
@@ -361,14 +362,129 @@ __device__ __forceinline__ float order_trial(const unsigned char* base, const fl
   return e;
 }
 
+// The same error in the plain fmaf order of the lane-per-instance sweep
+// (tile_err_1d / tile_err_2d in sweep_eval.cuh, operation for operation),
+// the matrices read from shared memory: used for the wide 2D sizes whose
+// per-lane form would not fit the registers.
+template <int DIM, int M, int R>
+__device__ __forceinline__ float fma_trial(const unsigned char* base, const float* __restrict__ r,
+                                           float* pl) {
+  using L = OrderLayout<DIM, M, R, float, false>;
+  using S = SweepShape<DIM, M, R>;
+  constexpr int A = L::A;
+  const float* Gs = reinterpret_cast<const float*>(base + L::G_OFF);
+  const float* BTs = reinterpret_cast<const float*>(base + L::BT_OFF);
+  const float* ATs = reinterpret_cast<const float*>(base + L::AT_OFF);
+  constexpr int NIN = pad_to(S::NG + S::ND, 4);
+  float in[NIN];
+#pragma unroll
+  for (int q = 0; q < NIN / 4; ++q) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(r) + q);
+    in[4 * q] = v.x;
+    in[4 * q + 1] = v.y;
+    in[4 * q + 2] = v.z;
+    in[4 * q + 3] = v.w;
+  }
+  const float* g = in;
+  const float* d = in + S::NG;
+  const float* yh = r + S::NG + S::ND;
+  const float* yl = yh + S::NO;
+  float e = 0.0f;
+  if constexpr (DIM == 1) {
+    float p[A];
+#pragma unroll
+    for (int i = 0; i < A; ++i) {
+      float gr[R], br[A];
+      load_row<R>(Gs + i * L::GS, gr);
+      load_row<A>(BTs + i * L::BS, br);
+      float u = 0.0f, v = 0.0f;
+#pragma unroll
+      for (int k = 0; k < R; ++k) u = fmaf(gr[k], g[k], u);
+#pragma unroll
+      for (int l = 0; l < A; ++l) v = fmaf(br[l], d[l], v);
+      p[i] = __fmul_rn(u, v);
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float ar[A];
+      load_row<A>(ATs + j * L::BS, ar);
+      float y = 0.0f;
+#pragma unroll
+      for (int i = 0; i < A; ++i) y = fmaf(ar[i], p[i], y);
+      e = __fadd_rn(e, abs_err(y, __ldg(yh + j), __ldg(yl + j)));
+    }
+  } else {
+    // per frequency row i: W_i = G_i g, T_i = B^T_i d, then U[i][j], V[i][j],
+    // P[i][j] = U .* V to shared memory; Z = A^T P (i ascending), Y = Z A
+#pragma unroll 1
+    for (int i = 0; i < A; ++i) {
+      float gi[R], bi[A], Wi[R], Ti[A];
+      load_row<R>(Gs + i * L::GS, gi);
+      load_row<A>(BTs + i * L::BS, bi);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int l = 0; l < R; ++l) acc = fmaf(gi[l], g[l * R + k], acc);
+        Wi[k] = acc;
+      }
+#pragma unroll
+      for (int l = 0; l < A; ++l) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < A; ++k) acc = fmaf(bi[k], d[k * A + l], acc);
+        Ti[l] = acc;
+      }
+#pragma unroll 2
+      for (int j = 0; j < A; ++j) {
+        float gj[R], bj[A];
+        load_row<R>(Gs + j * L::GS, gj);
+        load_row<A>(BTs + j * L::BS, bj);
+        float u = 0.0f, v = 0.0f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) u = fmaf(Wi[k], gj[k], u);
+#pragma unroll
+        for (int l = 0; l < A; ++l) v = fmaf(Ti[l], bj[l], v);
+        pl[(i * A + j) * 32] = __fmul_rn(u, v);
+      }
+    }
+#pragma unroll 1
+    for (int a = 0; a < M; ++a) {
+      float ar[A], Za[A];
+      load_row<A>(ATs + a * L::BS, ar);
+#pragma unroll
+      for (int j = 0; j < A; ++j) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < A; ++i) acc = fmaf(ar[i], pl[(i * A + j) * 32], acc);
+        Za[j] = acc;
+      }
+#pragma unroll 2
+      for (int b = 0; b < M; ++b) {
+        float br[A];
+        load_row<A>(ATs + b * L::BS, br);
+        float y = 0.0f;
+#pragma unroll
+        for (int j = 0; j < A; ++j) y = fmaf(Za[j], br[j], y);
+        e = __fadd_rn(e, abs_err(y, __ldg(yh + a * M + b), __ldg(yl + a * M + b)));
+      }
+    }
+  }
+  return e;
+}
+
 // One instance on one warp: sorted finite points a[0..alpha-2] (the same in
 // every lane) -> err = sum_t ||yhat_t - y_t||_1 / ysum, +inf when two points
-// coincide.  Not inlined: both kernels run this one body.
-template <int DIM, int M, int R, typename T>
+// coincide.  HUFF: the Huffman order, trial sums per lane then a butterfly.
+// !HUFF (T = float): the plain fmaf order and the plain sweep's chunked
+// trial sums (each round's 32 errors gathered in trial order), so its bits
+// are the lane-per-instance sweep's.  Not inlined: both kernels run this one
+// body.
+template <int DIM, int M, int R, typename T, bool HUFF>
 __device__ __noinline__ double order_instance(const double* a, unsigned char* base,
                                               const float* __restrict__ rec, int trials,
                                               double ysum) {
-  using L = OrderLayout<DIM, M, R, T>;
+  using L = OrderLayout<DIM, M, R, T, HUFF>;
   constexpr int A = L::A;
   const int lane = threadIdx.x & 31;
   T* Gs = reinterpret_cast<T*>(base + L::G_OFF);
@@ -393,6 +509,28 @@ __device__ __noinline__ double order_instance(const double* a, unsigned char* ba
   ok = __shfl_sync(kFull, ok, 0);
   if (!ok) return (double)INFINITY;
   __syncwarp();
+  constexpr int REC = SweepShape<DIM, M, R>::REC;
+  float* pl = reinterpret_cast<float*>(base + L::P_OFF) + lane;
+  if constexpr (!HUFF) {
+    static_assert(kTrialChunk % 32 == 0, "chunks are whole rounds of 32 trials");
+    double num = 0.0, chunk = 0.0;
+    const int rounds = (trials + 31) / 32;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int t = rd * 32 + lane;
+      float e = 0.0f;
+      if (t < trials) e = fma_trial<DIM, M, R>(base, rec + (int64_t)t * REC, pl);
+      const int n_here = min(32, trials - rd * 32);
+      for (int j = 0; j < 32; ++j) {  // this round's errors in trial order
+        const float ej = __shfl_sync(kFull, e, j);
+        if (j < n_here) chunk += (double)ej;
+      }
+      if ((rd + 1) % (kTrialChunk / 32) == 0 || rd + 1 == rounds) {
+        num += chunk;
+        chunk = 0.0;
+      }
+    }
+    return num / ysum;
+  }
   // one tree per lane: G rows, then B^T rows, then A^T rows
   if (lane < A)
     make_tree<R>(Gs + lane * L::GS, reinterpret_cast<uint32_t*>(base + L::TG_OFF) + lane * L::WG);
@@ -414,8 +552,6 @@ __device__ __noinline__ double order_instance(const double* a, unsigned char* ba
                                                      u32(L::RA_OFF), dummy);
   __syncwarp();
   T* sv = reinterpret_cast<T*>(base + L::SL_OFF) + lane;
-  float* pl = reinterpret_cast<float*>(base + L::P_OFF) + lane;
-  constexpr int REC = SweepShape<DIM, M, R>::REC;
   double num = 0.0;
   for (int t = lane; t < trials; t += 32)
     num += (double)order_trial<DIM, M, R, T>(base, rec + (int64_t)t * REC, sv, pl, sg, sb, sa);
@@ -425,12 +561,12 @@ __device__ __noinline__ double order_instance(const double* a, unsigned char* ba
 }
 
 // Mask sweep: one warp per (valid mask, c) instance.
-template <int DIM, int M, int R, typename T>
-__global__ void __launch_bounds__(kOrderThreads, 3)
+template <int DIM, int M, int R, typename T, bool HUFF>
+__global__ void __launch_bounds__(kOrderThreads, HUFF ? 3 : 2)
     k_order_sweep(const float* __restrict__ rec, int trials, const double* __restrict__ c_grid,
                   int n_c, double d, const MaskList masks, const double* __restrict__ ysum,
                   double* __restrict__ err) {
-  using L = OrderLayout<DIM, M, R, T>;
+  using L = OrderLayout<DIM, M, R, T, HUFF>;
   extern __shared__ __align__(16) unsigned char order_smem[];
   const int warp = threadIdx.x >> 5;
   const int64_t inst = (int64_t)blockIdx.x * kOrderWarps + warp;
@@ -440,75 +576,86 @@ __global__ void __launch_bounds__(kOrderThreads, 3)
   double pts[kMaxAlpha];
   mask_points(masks.mask[qv], L::A, c_grid[ci], d, pts);  // valid: the host kept valid masks
   const double e =
-      order_instance<DIM, M, R, T>(pts, order_smem + warp * L::BYTES, rec, trials, *ysum);
+      order_instance<DIM, M, R, T, HUFF>(pts, order_smem + warp * L::BYTES, rec, trials, *ysum);
   if ((threadIdx.x & 31) == 0) err[(int64_t)masks.q[qv] * n_c + ci] = e;
 }
 
 // Explicit point sets: one warp per set.
-template <int DIM, int M, int R, typename T>
-__global__ void __launch_bounds__(kOrderThreads, 3)
+template <int DIM, int M, int R, typename T, bool HUFF>
+__global__ void __launch_bounds__(kOrderThreads, HUFF ? 3 : 2)
     k_order_pointset(const float* __restrict__ rec, int trials, const double* __restrict__ pts,
                      int n_sets, const double* __restrict__ ysum, double* __restrict__ err) {
-  using L = OrderLayout<DIM, M, R, T>;
+  using L = OrderLayout<DIM, M, R, T, HUFF>;
   extern __shared__ __align__(16) unsigned char order_smem[];
   const int warp = threadIdx.x >> 5;
   const int s = blockIdx.x * kOrderWarps + warp;
   if (s >= n_sets) return;  // the whole warp
   double a[kMaxAlpha];
   for (int i = 0; i < L::A - 1; ++i) a[i] = pts[(int64_t)s * (L::A - 1) + i];
-  const double e = order_instance<DIM, M, R, T>(a, order_smem + warp * L::BYTES, rec, trials,
-                                                *ysum);
+  const double e = order_instance<DIM, M, R, T, HUFF>(a, order_smem + warp * L::BYTES, rec,
+                                                      trials, *ysum);
   if ((threadIdx.x & 31) == 0) err[s] = e;
 }
 
 }  // namespace
 
-// Launches of one value type T (float: the FP32 Huffman form, double: the
-// mixed form).  Each kernel is allowed its dynamic shared memory (above the
-// 48 KB default for the larger sizes) before its first launch.
-template <typename T>
+// Launches of one form: T = float, HUFF (the FP32 Huffman order), T =
+// double, HUFF (its FP64-transform form) or T = float, !HUFF (the plain fmaf
+// order, for the wide sizes).  SIZES is the size list compiled for the form.
+// Each kernel is allowed its dynamic shared memory (above the 48 KB default
+// for the larger sizes) before its launch.
+#define WINO_ORDER_SIZES_HUFF(X) WINO_SWEEP_SIZES(X) WINO_SWEEP_SIZES_WIDE(X)
+template <typename T, bool HUFF>
 int order_sweep_launch_t(const SweepSize& s, const float* rec, int trials, const double* c_grid,
                          int n_c, const MaskList& masks, const double* ysum, double* err,
                          cudaStream_t st) {
   const int64_t n = (int64_t)masks.n * n_c;
   if (n == 0) return WINO_OK;
   const unsigned grid = (unsigned)((n + kOrderWarps - 1) / kOrderWarps);
-#define WINO_ORDER_CASE(I, D, MM, RR)                                                       \
-  if (s.dim == D && s.m == MM && s.r == RR) {                                                \
-    const size_t smem = kOrderWarps * OrderLayout<D, MM, RR, T>::BYTES;                      \
-    WINO_CUDA_TRY(cudaFuncSetAttribute((const void*)k_order_sweep<D, MM, RR, T>,             \
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                                       (int)smem));                                          \
-    k_order_sweep<D, MM, RR, T><<<grid, kOrderThreads, smem, st>>>(rec, trials, c_grid, n_c, \
-                                                                   s.d, masks, ysum, err);   \
-    note_launches(1);                                                                        \
-    WINO_CUDA_TRY(cudaGetLastError());                                                       \
-    return WINO_OK;                                                                          \
+#define WINO_ORDER_CASE(I, D, MM, RR)                                                        \
+  if (s.dim == D && s.m == MM && s.r == RR) {                                                 \
+    const size_t smem = kOrderWarps * OrderLayout<D, MM, RR, T, HUFF>::BYTES;                 \
+    WINO_CUDA_TRY(cudaFuncSetAttribute((const void*)k_order_sweep<D, MM, RR, T, HUFF>,        \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                       (int)smem));                                           \
+    k_order_sweep<D, MM, RR, T, HUFF><<<grid, kOrderThreads, smem, st>>>(                     \
+        rec, trials, c_grid, n_c, s.d, masks, ysum, err);                                     \
+    note_launches(1);                                                                         \
+    WINO_CUDA_TRY(cudaGetLastError());                                                        \
+    return WINO_OK;                                                                           \
   }
-  WINO_SWEEP_SIZES(WINO_ORDER_CASE)
+  if constexpr (HUFF) {
+    WINO_ORDER_SIZES_HUFF(WINO_ORDER_CASE)
+  } else {
+    WINO_SWEEP_SIZES_WIDE(WINO_ORDER_CASE)
+  }
 #undef WINO_ORDER_CASE
   return WINO_EUNSUPPORTED;
 }
 
-template <typename T>
+template <typename T, bool HUFF>
 int order_pointset_launch_t(int dim, int m, int r, const float* rec, int trials,
                             const double* pts, int n_sets, const double* ysum, double* err,
                             cudaStream_t st) {
   if (n_sets <= 0) return WINO_OK;
   const unsigned grid = (unsigned)((n_sets + kOrderWarps - 1) / kOrderWarps);
-#define WINO_ORDER_CASE(I, D, MM, RR)                                                         \
-  if (dim == D && m == MM && r == RR) {                                                        \
-    const size_t smem = kOrderWarps * OrderLayout<D, MM, RR, T>::BYTES;                        \
-    WINO_CUDA_TRY(cudaFuncSetAttribute((const void*)k_order_pointset<D, MM, RR, T>,            \
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,            \
-                                       (int)smem));                                            \
-    k_order_pointset<D, MM, RR, T><<<grid, kOrderThreads, smem, st>>>(rec, trials, pts, n_sets, \
-                                                                      ysum, err);              \
-    note_launches(1);                                                                          \
-    WINO_CUDA_TRY(cudaGetLastError());                                                         \
-    return WINO_OK;                                                                            \
+#define WINO_ORDER_CASE(I, D, MM, RR)                                                        \
+  if (dim == D && m == MM && r == RR) {                                                       \
+    const size_t smem = kOrderWarps * OrderLayout<D, MM, RR, T, HUFF>::BYTES;                 \
+    WINO_CUDA_TRY(cudaFuncSetAttribute((const void*)k_order_pointset<D, MM, RR, T, HUFF>,     \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                       (int)smem));                                           \
+    k_order_pointset<D, MM, RR, T, HUFF><<<grid, kOrderThreads, smem, st>>>(                  \
+        rec, trials, pts, n_sets, ysum, err);                                                 \
+    note_launches(1);                                                                         \
+    WINO_CUDA_TRY(cudaGetLastError());                                                        \
+    return WINO_OK;                                                                           \
   }
-  WINO_SWEEP_SIZES(WINO_ORDER_CASE)
+  if constexpr (HUFF) {
+    WINO_ORDER_SIZES_HUFF(WINO_ORDER_CASE)
+  } else {
+    WINO_SWEEP_SIZES_WIDE(WINO_ORDER_CASE)
+  }
 #undef WINO_ORDER_CASE
   return WINO_EUNSUPPORTED;
 }

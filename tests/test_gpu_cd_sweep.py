@@ -15,6 +15,19 @@ pytestmark = pytest.mark.gpu
 INF = math.inf
 
 
+def test_cd_sweep_wide_vs_oracle(wino, orc):
+    """The wide 2D size F(7x7,3x3) (no planned form: one warp per instance)."""
+    dg = [1.8, 2.485]
+    cg = [0.7, 1.305, 2.1]
+    masks = [0x7F, 0xEF, 0xF7]
+    got = wino.cd_sweep(2, 7, cg, dg, masks, 200, seed=3)
+    for i, d in enumerate(dg):
+        want = orc.error_sweep(cg, [(2, 7, 3, d)], masks, 200, 3)[0]
+        fin = np.isfinite(want)
+        assert np.array_equal(np.isfinite(got[i]), fin)
+        assert np.all(np.abs(got[i][fin] - want[fin]) <= 1e-6 * want[fin])
+
+
 def test_cd_sweep_vs_oracle(wino, orc):
     dg = [1.5, 2.478, 3.1]
     cg = [0.4, 0.77, 1.313, 1.9, 2.6, 3.3]
@@ -31,6 +44,8 @@ def test_cd_sweep_vs_oracle(wino, orc):
     (1, 9, 0x7F, 1.313, 2.478),    # Table 7, n=9: {0,-1/c,-c,c,1/c,-1/d,-d,d}
     (1, 10, 0xFF, 1.953, 1.229),   # Table 7, n=10: all eight points
     (2, 8, 0x5F, 2.0, 1.003),      # Table 8, n=8: {0,-1/c,-c,c,1/c,-1/d,d}
+    (2, 9, 0x7F, 1.305, 2.485),    # Table 8, n=9: {0,-1/c,-c,c,1/c,-1/d,-d,d}
+    (2, 10, 0xFF, 1.272, 2.099),   # Table 8, n=10: all eight points
 ])
 def test_cd_search_reaches_paper_point(wino, dim, n, mask, c, d):
     """A 64 x 512 (d, c) grid over the paper's subset finds an error no more

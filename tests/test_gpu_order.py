@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 INF = math.inf
 REL = 1e-6
 ORDERS = ["huffman", "huffman_mixed"]
-GPU_N = [(1, n) for n in range(4, 11)] + [(2, n) for n in range(4, 9)]
+GPU_N = [(1, n) for n in range(4, 11)] + [(2, n) for n in range(4, 11)]
 
 
 @pytest.mark.parametrize("order", ORDERS)
@@ -118,7 +118,7 @@ def test_order_mask_sweep_matches_pointsets_every_size(wino, orc, order):
     cg = inputs.c_grid(4096)[::601]
     masks = inputs.sweep_masks()
     for size in (inputs.SWEEP_SIZES + [(1, m, 5, 2.0) for m in range(2, 7)]
-                 + [(2, m, 5, 2.0) for m in range(2, 5)]):
+                 + [(2, m, 5, 2.0) for m in range(2, 5)] + [(2, 7, 3, 2.485), (2, 8, 3, 2.099)]):
         dim, m, r, d = size
         mk = wino.valid_masks(size, masks)[0]
         e = wino.wino_error_sweep(cg, [size], [mk], 256, seed=5, order=order)[0, 0]

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 INF = math.inf
 REL = 1e-6
 # sizes the GPU sweep is compiled for: (dim, n) with n = m + 2 points
-GPU_N = [(1, n) for n in range(4, 11)] + [(2, n) for n in range(4, 9)]
+GPU_N = [(1, n) for n in range(4, 11)] + [(2, n) for n in range(4, 11)]
 
 
 @pytest.mark.parametrize("dim,n", GPU_N)
@@ -45,8 +45,8 @@ def test_pointset_degenerate_and_unsupported(wino):
     with pytest.raises(wino.WinoError) as ex:
         wino.wino_pointset_error((1, 2, 3), [[0.0, 1.0, -1.0, 2.0]], 64)
     assert ex.value.status == wino.WINO_EINVAL
-    with pytest.raises(wino.WinoError) as ex:
-        wino.wino_pointset_error((2, 7, 3), [COMPARISON_SETS[(2, 9)] + [INF]], 64)
+    with pytest.raises(wino.WinoError) as ex:  # 2D 7x7 kernels: not compiled
+        wino.wino_pointset_error((2, 3, 7), [COMPARISON_SETS[(2, 9)] + [INF]], 64)
     assert ex.value.status == wino.WINO_EUNSUPPORTED
 
 
@@ -61,6 +61,9 @@ def test_paper_comparison(wino):
     cg = inputs.c_grid()
     masks = inputs.sweep_masks()
     sizes = {s[:2]: s for s in inputs.SWEEP_SIZES}
+    # the wide 2D sizes at the paper's d (Table 8, n = 9, 10)
+    sizes[(2, 7)] = (2, 7, 3, 2.485)
+    sizes[(2, 8)] = (2, 8, 3, 2.099)
     for dim, n in GPU_N:
         m = n - 2
         pn, prop = wino.wino_pointset_error(

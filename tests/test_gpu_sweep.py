@@ -88,6 +88,24 @@ def test_sweep_2d_r5_vs_oracle(wino, orc, m):
         assert _top10_consistent(eg[q], eo[q]) >= 9
 
 
+@pytest.mark.parametrize("size", [(2, 7, 3, 2.485), (2, 8, 3, 2.099)])
+def test_sweep_wide_2d_vs_oracle(wino, orc, size):
+    """2D F(7x7,3x3) and F(8x8,3x3) (Table 8, n = 9, 10), swept one warp per
+    instance: every valid mask of the 66 at the paper's d, 24 c values, 200
+    trials, against the oracle; the same top-10 c per mask."""
+    cg = inputs.c_grid(4096)[::171]
+    masks = np.array(wino.valid_masks(size, inputs.sweep_masks()), np.uint8)
+    assert masks.size > 0
+    eg = wino.wino_error_sweep(cg, [size], masks, 200, seed=2)[0]
+    eo = orc.error_sweep(cg, [size], masks, 200, 2, n_threads=8)[0]
+    assert np.array_equal(np.isinf(eg), np.isinf(eo))
+    fin = np.isfinite(eo)
+    assert fin.sum() > 0.9 * eo.size
+    assert np.all(np.abs(eg[fin] - eo[fin]) <= REL * eo[fin])
+    for q in range(masks.size):
+        assert _top10_consistent(eg[q], eo[q]) >= 9
+
+
 def test_sweep_seed_and_trials_change_results(wino):
     cg = inputs.c_grid(32)
     a = wino.wino_error_sweep(cg, [(2, 4, 3, 1.0)], [0x0F], 100, seed=0)
