@@ -500,17 +500,22 @@ def paper_comparison(wino, inputs, ex, cg, masks, sizes):
     exhaustive sweep found (same trials), and the improvements over
     Barabasz's set beside the paper's."""
     out = {}
-    for s, (dim, m, r, d) in enumerate(sizes):
+    # the wide 2D sizes (Table 8, n = 9, 10) at the paper's d, swept here
+    # (untimed) for the comparison
+    wide = [(2, 7, 3, 2.485), (2, 8, 3, 2.099)]
+    ex_wide = wino.wino_error_sweep(cg, wide, masks, inputs.SWEEP_TRIALS, seed=0)
+    for s, (dim, m, r, d) in enumerate(list(sizes) + wide):
         n = m + 2
         key = (dim, n)
         if key not in inputs.COMPARISON_SETS:
             continue
+        ex_s = ex[s] if s < len(sizes) else ex_wide[s - len(sizes)]
         inf = math.inf
         pair = [inputs.COMPARISON_SETS[key] + [inf], inputs.PROPOSED_SETS[key] + [inf]]
         pn, prop = wino.wino_pointset_error((dim, m, r), pair, inputs.SWEEP_TRIALS, seed=0)
         pn_h, prop_h = wino.wino_pointset_error((dim, m, r), pair, inputs.SWEEP_TRIALS, seed=0,
                                                 order="huffman")
-        e = np.where(np.isfinite(ex[s]), ex[s], np.nan)
+        e = np.where(np.isfinite(ex_s), ex_s, np.nan)
         q, k = np.unravel_index(np.nanargmin(e), e.shape)
         best = float(e[q, k])
         out["%dd_n%d" % (dim, n)] = {
@@ -605,7 +610,8 @@ def order_sweeps(wino, inputs, cg, sizes, masks, rank):
 
 
 # sizes (dim, n) whose proposed set in Tables 7-8 uses the d-group, with its subset
-CD_SEARCH = [(1, 9, 0x7F), (1, 10, 0xFF), (2, 7, 0x4F), (2, 8, 0x5F)]
+CD_SEARCH = [(1, 9, 0x7F), (1, 10, 0xFF), (2, 7, 0x4F), (2, 8, 0x5F), (2, 9, 0x7F),
+             (2, 10, 0xFF)]
 
 
 def fp32_peak_tflops():

@@ -179,7 +179,7 @@ int wino_error_sweep(const double* c_grid, int n_c,
  * on the same trials of size (dim, m, r), in the same summation order (a set
  * that is also a mask instance gets the same bits).  +INFINITY when two
  * points coincide.  Sizes as compiled for the sweep (1D r = 3 m = 2..8, 1D
- * r = 5 m = 2..6, 2D r = 3 m = 2..6, 2D r = 5 m = 2..4), else
+ * r = 5 m = 2..6, 2D r = 3 m = 2..8, 2D r = 5 m = 2..4), else
  * WINO_EUNSUPPORTED; WINO_EINVAL
  * for a set without exactly one +INFINITY.  points, err_out: host arrays.
  * Synchronises `cuda_stream`.                                              */
