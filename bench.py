@@ -41,6 +41,10 @@ PTS4 = [0.0, -1 / C4, -C4, C4, 1 / C4, math.inf]
 PTS6 = [0.0, -1 / C6, -C6, C6, 1 / C6, -D6, D6, math.inf]
 METRIC = "Winograd layer effective TFLOP/s at stated FP64 error; c-sweep evals/s vs plain"
 # the layer stacks of one step: key -> (m, points, contraction dtype)
+# sub-batches per layer in the end-to-end pipeline (measured on GB300, F(4x4)
+# stack: 1 -> 7.18 ms per step, 2 -> 5.94, 4 -> 6.45, 8 -> 7.66; beyond 2 the
+# host's per-call enqueue cost outweighs the earlier start of the copies)
+E2E_CHUNKS = 2
 STACKS = {"f4x4": (4, PTS4, "f32"), "f6x6": (6, PTS6, "f32"),
           "f4x4_bf16": (4, PTS4, "bf16"), "f4x4_split_bf16x3": (4, PTS4, "split_bf16x3"),
           "f4x4_split_bf16x6": (4, PTS4, "split_bf16x6"),
@@ -374,40 +378,46 @@ def run_ours(args, rank, world, local_rank):
                       for s_, q_ in zip(*np.nonzero(rows))])
 
     # e2e: the F(4x4) FP32 stack through the public API with host buffers,
-    # pipelined as a caller of the API would: each layer's input is copied in
-    # on one stream, the layer runs on a second once that input has landed,
-    # and its output is copied out on a third once computed, so transfers of
-    # one layer overlap the compute of another.  Timed from the first copy-in
-    # to the last copy-out of each step, the device idle in between steps.
+    # pipelined as a caller of the API would: each layer's batch runs as
+    # E2E_CHUNKS sub-batches (wino_conv2d on a batch slice computes the same
+    # outputs); a sub-batch's input is copied in on one stream, it runs on a
+    # second once that input has landed, and its output is copied out on a
+    # third once computed, so the host transfers (the bound: ~200 GB/s each
+    # way) overlap compute and each other from the first sub-batch on.  Timed
+    # from the first copy-in to the last copy-out of each step, the device
+    # idle in between steps.
     xh = [x.cpu().pin_memory() for x in X]
     yh = [torch.empty(y.shape, dtype=y.dtype).pin_memory() for y in Y["f4x4"]]
     h2d = sum(x.numel() * 4 for x in X)
     d2h = sum(y.numel() * 4 for y in Y["f4x4"])
     s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     nl = len(layers)
-    ev_in = [torch.cuda.Event() for _ in range(nl)]
-    ev_c = [torch.cuda.Event() for _ in range(nl)]
+    units = [(li, c * N // E2E_CHUNKS, (c + 1) * N // E2E_CHUNKS)
+             for li in range(nl) for c in range(E2E_CHUNKS)]
+    ev_in = [torch.cuda.Event() for _ in units]
+    ev_c = [torch.cuda.Event() for _ in units]
     m4, p4, dt4 = STACKS["f4x4"]
     te2e = 0.0
-    for s in range(args.steps + 1):
+    for s in range(args.steps + 2):  # the first two untimed (the sub-batch shape's tuning)
         flush.fill_(float(s))
         torch.cuda.synchronize()
         t_a = torch.cuda.Event(enable_timing=True)
         t_b = torch.cuda.Event(enable_timing=True)
         t_a.record(s_in)
-        for li in range(nl):
+        for u, (li, n0, n1) in enumerate(units):
             with torch.cuda.stream(s_in):
-                X[li].copy_(xh[li], non_blocking=True)
-            ev_in[li].record(s_in)
-            s_comp.wait_event(ev_in[li])
-            wino.wino_conv2d(X[li], Wt[li], Y["f4x4"][li], p4, m4, 3, 1, dt4, stream=s_comp)
-            ev_c[li].record(s_comp)
-            s_out.wait_event(ev_c[li])
+                X[li][n0:n1].copy_(xh[li][n0:n1], non_blocking=True)
+            ev_in[u].record(s_in)
+            s_comp.wait_event(ev_in[u])
+            wino.wino_conv2d(X[li][n0:n1], Wt[li], Y["f4x4"][li][n0:n1], p4, m4, 3, 1, dt4,
+                             stream=s_comp)
+            ev_c[u].record(s_comp)
+            s_out.wait_event(ev_c[u])
             with torch.cuda.stream(s_out):
-                yh[li].copy_(Y["f4x4"][li], non_blocking=True)
+                yh[li][n0:n1].copy_(Y["f4x4"][li][n0:n1], non_blocking=True)
         t_b.record(s_out)
         torch.cuda.synchronize()
-        if s > 0:
+        if s > 1:
             te2e += t_a.elapsed_time(t_b) / 1e3
     ve2e = world * fl * args.steps / te2e / 1e12
 
@@ -472,9 +482,10 @@ def run_ours(args, rank, world, local_rank):
         "rooflines": roofs,
         "e2e": {"value": ve2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "how": "F(4x4) FP32 stack via wino_conv2d from pinned host buffers; per layer "
-                       "copy-in, layer and copy-out on three streams (event-ordered), so "
-                       "transfers overlap other layers' compute"},
+                "how": "F(4x4) FP32 stack via wino_conv2d from pinned host buffers; each "
+                       "layer as %d sub-batches, per sub-batch copy-in, layer and copy-out on "
+                       "three streams (event-ordered), so transfers overlap compute" % E2E_CHUNKS,
+                "sub_batches_per_layer": E2E_CHUNKS},
         "gpu_launches": int(launches),
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk,
