@@ -26,7 +26,8 @@ PTS = {4: [0.0, -1 / 1.622, -1.622, 1.622, 1 / 1.622, math.inf],
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp16", "split_bf16x3", "split_bf16x6"])
 @pytest.mark.parametrize("m", [4, 6, 2])
-@pytest.mark.parametrize("shape", [(2, 64, 64, 10, 10), (1, 80, 128, 9, 13), (1, 64, 256, 6, 6)])
+@pytest.mark.parametrize("shape", [(2, 64, 64, 10, 10), (1, 80, 128, 9, 13), (1, 64, 256, 6, 6),
+                                   (1, 300, 128, 7, 9)])
 def test_tc_layer_vs_oracle_emulation(wino, orc, dtype, m, shape):
     import torch
     N, C, K, H, W = shape
@@ -41,16 +42,39 @@ def test_tc_layer_vs_oracle_emulation(wino, orc, dtype, m, shape):
     yo = orc.wino_layer(x, w, 2, 1, PTS[m], m, 3, dtype)
     assert np.all(np.isfinite(yg))
     scale = np.abs(yo).max()
-    assert np.abs(yg - yo).max() <= 2e-5 * scale
+    # the tensor cores accumulate in their own order: the difference grows
+    # with the contraction length (C = 300: 8e-5 of the scale measured)
+    assert np.abs(yg - yo).max() <= 2e-5 * max(1.0, C / 64) * scale
     ref = orc.direct_f64(x, w, 2, 1, 3)
     eg = np.abs(yg - ref).sum() / np.abs(ref).sum()
     eo = np.abs(yo.astype(np.float64) - ref).sum() / np.abs(ref).sum()
     if dtype == "split_bf16x6":
-        # operands exact to 2^-24: the accumulation order is the dominant
-        # error term, and the tensor cores' order may be the better one
-        assert eg <= 1.05 * eo, (eg, eo)
+        # operands exact to 2^-24: the accumulation is the dominant error
+        # term.  Up to C = 128 the tensor cores' is as good as sequential
+        # FP32 or better; over long contractions it is not (C = 300 at
+        # F(2x2,3x3): 1.5x measured)
+        assert eg <= (1.05 if C <= 128 else 2.0) * eo, (eg, eo)
     else:
         assert abs(eg / eo - 1) < 0.05, (eg, eo)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp16", "split_bf16x3", "split_bf16x6"])
+@pytest.mark.parametrize("C", [64, 128, 300, 512])
+def test_tc_exact_regime_every_chunk(wino, orc, dtype, C):
+    """Integer inputs in [-2, 2] with F(2x2,3x3) on {0, 1, -1, inf}: every
+    operand and partial sum is exact, so the result is the exact correlation
+    whatever the accumulation order -- a chunk lost, repeated or read from the
+    wrong stage of the multi-stage ring (C > 64) would show."""
+    import torch
+    rng = np.random.default_rng(C)
+    x = rng.integers(-2, 3, (1, C, 10, 12)).astype(np.float32)
+    w = rng.integers(-2, 3, (32, C, 3, 3)).astype(np.float32)
+    y = torch.full((1, 32, 10, 12), float("nan"), device="cuda")
+    wino.wino_conv2d(torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda(), y, PTS[2], 2, 3, 1,
+                     dtype)
+    torch.cuda.synchronize()
+    ref = orc.direct_f64(x, w, 2, 1, 3)
+    assert np.array_equal(y.cpu().numpy().astype(np.float64), ref)
 
 
 def test_tc_error_ordering_matches_precision(wino, orc):
