@@ -871,7 +871,9 @@ static int launch_split(const float* x, const float* w, float* y, const LayerGeo
 // 67%.  8 x 16 tiles for F(4x4) (one frequency per thread, four frequency
 // groups per warp) need 9-warp CTAs, which three warps on one SM
 // sub-partition cap at 168 registers: measured 14-25% slower than shape 1
-// on the VGG16 stack (spills, one CTA per SM).
+// on the VGG16 stack (spills, one CTA per SM).  8 x 8 tiles (ratio 4, 112
+// registers, no spills; 16 x 32 outputs per CTA, 9 warps) measured 18-35%
+// slower: one CTA per SM does not hide the per-chunk waits and the epilogue.
 #define SPLIT_M2_0 2, 2, 4, 4, 1, 8, 16, 8, 2, 1
 #define SPLIT_M4_0 4, 1, 4, 8, 3, 4, 8, 8, 2, 1
 #define SPLIT_M4_1 4, 1, 8, 4, 3, 4, 8, 8, 2, 1
