@@ -762,6 +762,16 @@ def profile_case(name):
         cg = inputs.c_grid()
         for _ in range(4):
             wino.wino_error_sweep(cg, [(2, 4, 3, 1.0)], inputs.sweep_masks(), 1000, seed=0)
+    elif name == "fp64_ref":
+        # the FP64 direct reference and the FP64 error reduction on one VGG16
+        # stage-2 shape (128 ch, 112x112, N = 2): 1.2 GFLOP in FP64
+        x, w = inputs.vgg_layer_device(128, 112, N=2, seed=0)
+        y = torch.empty_like(x)
+        y64 = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+        wino.wino_conv2d(x, w, y, PTS4, 4, 3, 1, "f32")
+        for _ in range(4):
+            wino.wino_direct_conv_f64(x, w, y64, 1)
+            wino.wino_error_stats(y, y64)
     elif name in ("sweep_huffman", "sweep_huffman_mixed"):
         cg = inputs.c_grid()
         for _ in range(4):
@@ -786,7 +796,8 @@ def main():
                          "suffix _vgg: the five VGG16 stages, N=8; suffix _l0.._l4: that "
                          "VGG16 stage at N=32) | sweep (2D F(4x4), all masks, 4096 c) | "
                          "sweep_huffman | sweep_huffman_mixed (the same in the Huffman "
-                         "orders)")
+                         "orders) | fp64_ref (FP64 direct reference and error reduction, "
+                         "128 ch 112x112, N=2)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -11,33 +11,67 @@
 
 namespace wino {
 
-// K5: one thread per output (n, k, p, q), q fastest: neighbouring threads
-// read neighbouring input columns, the filter tap is warp-uniform.
-__global__ void k_direct_f64(const float* __restrict__ x, const float* __restrict__ w,
-                             double* __restrict__ y, int N, int C, int K, int H, int W, int pad,
-                             int rh, int r, int padh, int Ho, int Wo) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)N * K * Ho * Wo;
-  if (idx >= total) return;
-  const int q = (int)(idx % Wo);
-  const int p = (int)((idx / Wo) % Ho);
-  const int k = (int)((idx / ((int64_t)Wo * Ho)) % K);
-  const int n = (int)(idx / ((int64_t)Wo * Ho * K));
-  double acc = 0.0;
-  for (int c = 0; c < C; ++c) {
-    const float* xc = x + ((int64_t)n * C + c) * H * W;
-    const float* wk = w + ((int64_t)k * C + c) * rh * r;
-    for (int u = 0; u < rh; ++u) {
-      const int hh = p + u - padh;
-      if (hh < 0 || hh >= H) continue;
-      for (int v = 0; v < r; ++v) {
-        const int ww = q + v - pad;
-        if (ww < 0 || ww >= W) continue;
-        acc = fma((double)__ldg(xc + (int64_t)hh * W + ww), (double)__ldg(wk + u * r + v), acc);
+// K5: one thread per output position (n, p, q) and kDirKT output channels,
+// positions (p, q) of a plane flattened across the blocks, q fastest
+// (neighbouring threads read neighbouring input columns; a narrow plane
+// still fills the block).  The
+// block's filters for kDirCC channels at a time are staged in shared memory
+// already widened to FP64 (read as broadcasts), and each input value is
+// widened once for the kDirKT channels it feeds: per multiply-add one FP64
+// FMA and an eighth of a conversion, where converting both operands at every
+// use took three FP64-pipe slots.  Every output's operations are those of
+// the plain loop (c, then u, then v ascending, one fma each), so the bits do
+// not depend on the blocking.
+constexpr int kDirKT = 8, kDirCC = 8, kDirThreads = 128;
+
+__global__ void __launch_bounds__(kDirThreads)
+    k_direct_f64(const float* __restrict__ x, const float* __restrict__ w, double* __restrict__ y,
+                 int N, int C, int K, int H, int W, int pad, int rh, int r, int padh, int Ho,
+                 int Wo) {
+  __shared__ double ws[kDirCC][kDirKT][kMaxR * kMaxR];
+  const int64_t pq = (int64_t)blockIdx.x * kDirThreads + threadIdx.x;
+  const bool live = pq < (int64_t)Ho * Wo;
+  const int p = live ? (int)(pq / Wo) : 0;
+  const int q = live ? (int)(pq - (int64_t)p * Wo) : 0;
+  const int nk = (K + kDirKT - 1) / kDirKT;
+  const int n = blockIdx.y / nk, k0 = (blockIdx.y % nk) * kDirKT;
+  const int taps = rh * r;
+  double acc[kDirKT];
+#pragma unroll
+  for (int kk = 0; kk < kDirKT; ++kk) acc[kk] = 0.0;
+  for (int c0 = 0; c0 < C; c0 += kDirCC) {
+    const int cn = min(kDirCC, C - c0);
+    __syncthreads();  // the previous chunk's filters are no longer read
+    for (int e = threadIdx.x; e < cn * kDirKT * taps; e += kDirThreads) {
+      const int t = e % taps, kk = (e / taps) % kDirKT, cc = e / (taps * kDirKT);
+      const int k = k0 + kk;
+      ws[cc][kk][t] = k < K ? (double)__ldg(w + ((int64_t)k * C + c0 + cc) * taps + t) : 0.0;
+    }
+    __syncthreads();
+    if (live) {
+      for (int cc = 0; cc < cn; ++cc) {
+        const float* xc = x + ((int64_t)n * C + c0 + cc) * H * W;
+        for (int u = 0; u < rh; ++u) {
+          const int hh = p + u - padh;
+          if (hh < 0 || hh >= H) continue;
+          for (int v = 0; v < r; ++v) {
+            const int ww = q + v - pad;
+            if (ww < 0 || ww >= W) continue;
+            const double xv = (double)__ldg(xc + (int64_t)hh * W + ww);
+#pragma unroll
+            for (int kk = 0; kk < kDirKT; ++kk) acc[kk] = fma(xv, ws[cc][kk][u * r + v], acc[kk]);
+          }
+        }
       }
     }
   }
-  y[idx] = acc;
+  if (live) {
+#pragma unroll
+    for (int kk = 0; kk < kDirKT; ++kk) {
+      const int k = k0 + kk;
+      if (k < K) y[(((int64_t)n * K + k) * Ho + p) * Wo + q] = acc[kk];
+    }
+  }
 }
 
 int direct_conv_f64(const float* x, const float* w, double* y, int dim, int N, int C, int K,
@@ -49,9 +83,15 @@ int direct_conv_f64(const float* x, const float* w, double* y, int dim, int N, i
   const int Wo = W + 2 * pad - r + 1;
   const int64_t total = (int64_t)N * K * Ho * Wo;
   if (total == 0) return WINO_OK;
+  const int64_t nz = (int64_t)N * ((K + kDirKT - 1) / kDirKT);
+  const int64_t nb = ((int64_t)Ho * Wo + kDirThreads - 1) / kDirThreads;
+  if (r > kMaxR || nz > 65535 || nb > 0x7fffffffLL) {
+    set_error("direct reference: r <= 7, N * ceil(K / 8) <= 65535");
+    return WINO_EUNSUPPORTED;
+  }
   ProfScope ps(kKDirect, st);
-  k_direct_f64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(x, w, y, N, C, K, Hin, W, pad,
-                                                                 rh, r, padh, Ho, Wo);
+  const dim3 grid((unsigned)nb, (unsigned)nz);
+  k_direct_f64<<<grid, kDirThreads, 0, st>>>(x, w, y, N, C, K, Hin, W, pad, rh, r, padh, Ho, Wo);
   note_launches(1);
   WINO_CUDA_TRY(cudaGetLastError());
   return WINO_OK;
