@@ -3,7 +3,7 @@ matrix construction (wino_instance_matrices) against the CPU oracle.
 
 Bars: matrices 1e-13 relative; per-instance error 1e-6 relative (the GPU
 reduces |yhat - y| per trial in FP32 with y split into two FP32 words, the
-oracle in FP64; the benchmark spec allows 3%); NaN / +inf positions identical; the
+oracle in FP64; the parity bar is 3%); NaN / +inf positions identical; the
 top-10 c ranking of each (size, mask) identical up to near-ties (oracle
 errors within 1e-6 relative may swap)."""
 import math
