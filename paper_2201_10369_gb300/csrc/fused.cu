@@ -575,14 +575,70 @@ struct SplitCfg {
 #define SPLIT_TPARAMS FUSED_TPARAMS, int NS, int MINB
 #define SPLIT_TARGS FUSED_TARGS, NS, MINB
 
+// Output transform Y = A^T M A of one (tile, output channel): M[q] (q = i A
+// + j, frequencies row-major) from `ld(q)`, Y's valid rows x cols written
+// to y_t (row stride Wo).  Z = A^T M, then Y = Z A, sums over i and j
+// ascending; the pairs (j, j + 1) of Z and (b, b + 1) of Y run as one
+// fma.rn.f32x2 each (two IEEE fused multiply-adds, the same bits).
+template <int MM, typename LdM>
+__device__ __forceinline__ void otx_tile(LdM ld, const LayerMats& Mx, float* yt, int rows,
+                                         int cols, int Wo) {
+  constexpr int A = MM + 2, F = A * A;
+  unsigned long long Mp[F / 2];  // (M[i][j], M[i][j + 1]), j even
+#pragma unroll
+  for (int q = 0; q < F; q += 2) Mp[q / 2] = pack2(ld(q), ld(q + 1));
+  float Z[MM * A];
+#pragma unroll
+  for (int a = 0; a < MM; ++a)
+#pragma unroll
+    for (int j = 0; j < A; j += 2) {
+      unsigned long long z = 0ull;
+#pragma unroll
+      for (int i = 0; i < A; ++i) z = fma2(pack_dup(Mx.AT[a * A + i]), Mp[(i * A + j) / 2], z);
+      const float2 zz = unpack2(z);
+      Z[a * A + j] = zz.x;
+      Z[a * A + j + 1] = zz.y;
+    }
+#pragma unroll
+  for (int a = 0; a < MM; ++a) {
+    float yr[MM];
+#pragma unroll
+    for (int b = 0; b < MM; b += 2) {
+      unsigned long long v = 0ull;
+#pragma unroll
+      for (int j = 0; j < A; ++j)
+        v = fma2(pack_dup(Z[a * A + j]), pack2(Mx.AT[b * A + j], Mx.AT[(b + 1) * A + j]), v);
+      const float2 vv = unpack2(v);
+      yr[b] = vv.x;
+      yr[b + 1] = vv.y;
+    }
+    if (a >= rows) continue;
+    float* yrow = yt + (int64_t)a * Wo;
+    if (MM % 4 == 0 && cols == MM && (((uintptr_t)yrow) & 15) == 0) {
+#pragma unroll
+      for (int b = 0; b < MM; b += 4)
+        *reinterpret_cast<float4*>(yrow + b) = make_float4(yr[b], yr[b + 1], yr[b + 2], yr[b + 3]);
+    } else if (MM % 2 == 0 && cols == MM && (((uintptr_t)yrow) & 7) == 0) {
+#pragma unroll
+      for (int b = 0; b < MM; b += 2)
+        *reinterpret_cast<float2*>(yrow + b) = make_float2(yr[b], yr[b + 1]);
+    } else {
+#pragma unroll
+      for (int b = 0; b < MM; ++b)
+        if (b < cols) yrow[b] = yr[b];
+    }
+  }
+}
+
 template <SPLIT_TPARAMS>
 __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, MINB)
     k_gemm_otx(const float* __restrict__ Ub, const float* __restrict__ Vb, float* __restrict__ y,
                const LayerGeom g, const LayerMats Mx, const SplitGeom sg, int* err) {
   using Cfg = FusedCfg<FUSED_TARGS>;
   using SC = SplitCfg<SPLIT_TARGS>;
-  constexpr int A = Cfg::A, F = Cfg::F, NT = Cfg::NT, TB = Cfg::TB, KB = Cfg::KB;
-  extern __shared__ __align__(128) float sm[];
+  constexpr int NT = Cfg::NT, TB = Cfg::TB, KB = Cfg::KB;
+  extern __shared__ __align__(128) float gsm_[];
+  float* sm = gsm_;
   __shared__ __align__(8) uint64_t full[NS];
   const int tid = threadIdx.x;
   const int nkb = g.K / KB;
@@ -740,63 +796,283 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, MINB)
         }
       }
   __syncthreads();
-  // A^T M A per (t, k), the same order as the fused kernel's epilogue; the
-  // pairs (j, j + 1) of Z = A^T M and (b, b + 1) of Y = Z A run as one
-  // fma.rn.f32x2 each (two IEEE fused multiply-adds, the same bits).
+  // A^T M A per (t, k), the same order as the fused kernel's epilogue
   const int64_t plane = (int64_t)g.Ho * g.Wo;
   for (int p = tid; p < TB * KB; p += NT) {
     const int t = p % TB, kl = p / TB;
-    const int rows = s_rows[t], cols = s_cols[t];
+    const int rows = s_rows[t];
     if (rows == 0) continue;
-    const int k = k0 + kl;
-    unsigned long long Mp[F / 2];  // (M[i][j], M[i][j + 1]), j even
+    otx_tile<MM>([&](int q) { return Es[((size_t)q * KB + kl) * ETB + t]; }, Mx,
+                 y + s_ybase[t] + (int64_t)(k0 + kl) * plane, rows, s_cols[t], g.Wo);
+  }
+}
+
+// ===========================================================================
+// Cluster form of the GEMM + output-transform kernel.  The alpha^2
+// frequencies of a (TB tiles x KB output channels) block are split over a
+// cluster of NCL CTAs, FC = alpha^2 / NCL each.  A CTA holds the
+// accumulators of its FC frequencies only, which leaves registers for 8 x 8
+// outputs per thread: 16 operand floats per 64 FMAs, the ratio at which
+// the shared-memory operand path (one float per lane per 4 FMA lanes of the
+// SM) keeps the FMA pipe busy.  Each CTA streams its frequencies' slice of
+// every chunk (one contiguous run of the blocked U and V layouts, so the
+// transform kernels are shared with the single-CTA form) and stores its
+// accumulators to its own shared memory; after a cluster barrier the CTAs
+// split the block's (tile, channel) pairs and read the other frequencies
+// from their peers' shared memory (distributed shared memory).  Inner
+// products (c ascending, fused multiply-add) and output transform are those
+// of the single-CTA form, bit for bit.
+// ===========================================================================
+template <int MM, int NCL, int LX, int LT, int LK, int MT, int MK, int CC, int NS, int MINB>
+struct ClCfg {
+  static constexpr int A = MM + 2, F = A * A, FC = F / NCL;
+  static constexpr int TB = LT * MT, KB = LK * MK;
+  static constexpr int NW = FC / LX, NT = NW * 32;
+  static constexpr int UPL = CC * TB + 4, VPL = CC * KB + 16;  // the blocked layouts' planes
+  static constexpr int SU = FC * UPL, SV = FC * VPL, STAGE = SU + SV;
+  static constexpr int MAIN_FL = NS * STAGE;
+  static constexpr int ETB = TB + 4;               // epilogue row: TB tiles (padded)
+  static constexpr int EPI_FL = FC * KB * ETB;     // Es[fl][k][t]
+  static constexpr int SMEM_FL = MAIN_FL > EPI_FL ? MAIN_FL : EPI_FL;
+  static constexpr size_t SMEM = (size_t)SMEM_FL * sizeof(float);
+  static_assert(F % NCL == 0 && FC % LX == 0, "whole frequency slices and warps");
+  static_assert(LX * LT * LK == 32, "a warp is 32 lanes");
+  static_assert(MT % 4 == 0 && MK % 4 == 0, "float4 operand loads");
+  static_assert(NS >= 2 && NCL >= 2 && NCL <= 8, "double buffering; portable cluster size");
+  static_assert((SU * 4) % 16 == 0 && (SV * 4) % 16 == 0 && (UPL * 4) % 16 == 0 &&
+                    (VPL * 4) % 16 == 0,
+                "bulk copies move 16-byte multiples from 16-byte boundaries");
+};
+
+#define CL_TPARAMS int MM, int NCL, int LX, int LT, int LK, int MT, int MK, int CC, int NS, int MINB
+#define CL_TARGS MM, NCL, LX, LT, LK, MT, MK, CC, NS, MINB
+
+namespace {
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// The address of shared-memory word `a` (this CTA's) in CTA `rank` of the
+// cluster.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float ld_dsmem(uint32_t a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+}  // namespace
+
+// Launch: grid NCL x (K / KB) x ceil(T / TB) CTAs (cluster NCL x 1 x 1, the
+// NCL CTAs of one block adjacent), NT threads, ClCfg::SMEM bytes of dynamic
+// shared memory.
+template <CL_TPARAMS>
+__global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(ClCfg<CL_TARGS>::NT, MINB)
+    k_gemm_otx_cl(const float* __restrict__ Ub, const float* __restrict__ Vb,
+                  float* __restrict__ y, const LayerGeom g, const LayerMats Mx,
+                  const SplitGeom sg, int* err) {
+  using Cfg = ClCfg<CL_TARGS>;
+  constexpr int F = Cfg::F, FC = Cfg::FC, NT = Cfg::NT, TB = Cfg::TB, KB = Cfg::KB;
+  constexpr int ETB = Cfg::ETB;
+  extern __shared__ __align__(128) float csm_[];
+  float* sm = csm_;
+  __shared__ __align__(8) uint64_t full[NS];
+  __shared__ uint32_t s_done[NS];  // warps done with stage s, counted over its chunks
+  __shared__ int s_issued;         // chunks 0 .. s_issued - 1 issued
+  __shared__ int64_t s_ybase[TB];
+  __shared__ int s_rows[TB], s_cols[TB];
+  const int tid = threadIdx.x;
+  uint32_t rank;
+  asm("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(rank));
+  const int64_t blk = blockIdx.x / NCL;
+  const int nkb = g.K / KB;
+  const int kb = (int)(blk % nkb);
+  const int64_t tb = blk / nkb;
+  const int k0 = kb * KB;
+  const int64_t t0 = tb * TB;
+  const int nchunks = sg.nch;
+  // chunk ch of this CTA's frequency slice at ublk + ch F UPL (vblk alike)
+  const float* ublk = Ub + tb * nchunks * F * Cfg::UPL + (int64_t)rank * Cfg::SU;
+  const float* vblk = Vb + (int64_t)kb * nchunks * F * Cfg::VPL + (int64_t)rank * Cfg::SV;
+
+  if (tid < TB) {
+    const int64_t tg = t0 + tid;
+    if (tg < g.T) {
+      const int tpi = g.th * g.tw;
+      const int n = (int)(tg / tpi);
+      const int rem = (int)(tg - (int64_t)n * tpi);
+      const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
+      s_ybase[tid] = (int64_t)n * g.K * g.Ho * g.Wo + (int64_t)ti * MM * g.Wo + tj * MM;
+      s_rows[tid] = min(MM, g.Ho - ti * MM);
+      s_cols[tid] = min(MM, g.Wo - tj * MM);
+    } else {
+      s_ybase[tid] = 0;
+      s_rows[tid] = 0;
+      s_cols[tid] = 0;
+    }
+  }
+  auto issue = [&](int ch, int st) {
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&full[st]);
+    const uint32_t dst = smem_u32(sm + st * Cfg::STAGE);
+    mbar_expect_tx(bar, (uint32_t)(Cfg::STAGE * 4));
+    bulk_g2s(dst, ublk + (int64_t)ch * F * Cfg::UPL, (uint32_t)(Cfg::SU * 4), bar);
+    bulk_g2s(dst + Cfg::SU * 4, vblk + (int64_t)ch * F * Cfg::VPL, (uint32_t)(Cfg::SV * 4), bar);
+  };
+  // every stage starts filled: chunks 0 .. NS - 1 in flight
+  if (tid == 0) {
 #pragma unroll
-    for (int q = 0; q < F; q += 2)
-      Mp[q / 2] = pack2(Es[((size_t)q * KB + kl) * ETB + t],
-                        Es[((size_t)(q + 1) * KB + kl) * ETB + t]);
-    float Z[MM * A];
+    for (int st = 0; st < NS; ++st) {
+      mbar_init1((uint32_t)__cvta_generic_to_shared(&full[st]));
+      s_done[st] = 0;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    const int n0 = nchunks < NS ? nchunks : NS;
+    for (int st = 0; st < n0; ++st) issue(st, st);
+    s_issued = n0;
+  }
+  __syncthreads();
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int lx = lane / (LT * LK);
+  const int lt = (lane / LK) % LT;
+  const int lk = lane % LK;
+  const int fl = warp * LX + lx;  // this lane's frequency within the slice
+  // acc[i][j2] holds output channels (2 j2, 2 j2 + 1) of tile i
+  unsigned long long acc[MT][MK / 2];
 #pragma unroll
-    for (int a = 0; a < MM; ++a)
+  for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int j = 0; j < A; j += 2) {
-        unsigned long long z = 0ull;
+    for (int j = 0; j < MK / 2; ++j) acc[i][j] = 0ull;
+
+  // No CTA-wide barrier per chunk: each warp waits for the chunk's bytes
+  // and, when done with it, counts itself out of the stage; the last warp
+  // out refills the stage with chunk ch + NS.
+  bool ok = true;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int st = ch % NS;
+    const bool got =
+        mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&full[st]), (uint32_t)((ch / NS) & 1));
+    if (!__all_sync(0xffffffffu, got)) {
+      ok = false;  // the warp leaves the loop; its peers' waits run out in turn
+      break;
+    }
+    const float* up0 = sm + st * Cfg::STAGE + fl * Cfg::UPL + lt * MT;
+    const float* vp0 = sm + st * Cfg::STAGE + Cfg::SU + fl * Cfg::VPL + lk * 4;
+    auto load_frag = [&](int cc, float (&a)[MT], unsigned long long (&b2)[MK / 2]) {
+      const float* up = up0 + cc * TB;
+      const float* vp = vp0 + cc * KB;
 #pragma unroll
-        for (int i = 0; i < A; ++i) z = fma2(pack_dup(Mx.AT[a * A + i]), Mp[(i * A + j) / 2], z);
-        const float2 zz = unpack2(z);
-        Z[a * A + j] = zz.x;
-        Z[a * A + j + 1] = zz.y;
+      for (int i = 0; i < MT; i += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(up + i);
+        a[i] = v.x;
+        a[i + 1] = v.y;
+        a[i + 2] = v.z;
+        a[i + 3] = v.w;
       }
-    float* yt = y + s_ybase[t] + (int64_t)k * plane;
 #pragma unroll
-    for (int a = 0; a < MM; ++a) {
-      float yr[MM];
-#pragma unroll
-      for (int b = 0; b < MM; b += 2) {
-        unsigned long long v = 0ull;
-#pragma unroll
-        for (int j = 0; j < A; ++j)
-          v = fma2(pack_dup(Z[a * A + j]), pack2(Mx.AT[b * A + j], Mx.AT[(b + 1) * A + j]), v);
-        const float2 vv = unpack2(v);
-        yr[b] = vv.x;
-        yr[b + 1] = vv.y;
+      for (int s4 = 0; s4 < MK / 4; ++s4) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(vp + s4 * 4 * LK);
+        b2[2 * s4] = v.x;
+        b2[2 * s4 + 1] = v.y;
       }
-      if (a >= rows) continue;
-      float* yrow = yt + (int64_t)a * g.Wo;
-      if (MM % 4 == 0 && cols == MM && (((uintptr_t)yrow) & 15) == 0) {
+    };
+    float a[2][MT];
+    unsigned long long b2[2][MK / 2];
+    load_frag(0, a[0], b2[0]);
 #pragma unroll
-        for (int b = 0; b < MM; b += 4)
-          *reinterpret_cast<float4*>(yrow + b) = make_float4(yr[b], yr[b + 1], yr[b + 2], yr[b + 3]);
-      } else if (MM % 2 == 0 && cols == MM && (((uintptr_t)yrow) & 7) == 0) {
+    for (int cc = 0; cc < CC; ++cc) {
+      const int cur = cc & 1;
+      if (cc + 1 < CC) load_frag(cc + 1, a[cur ^ 1], b2[cur ^ 1]);
 #pragma unroll
-        for (int b = 0; b < MM; b += 2)
-          *reinterpret_cast<float2*>(yrow + b) = make_float2(yr[b], yr[b + 1]);
-      } else {
+      for (int i = 0; i < MT; ++i) {
+        const unsigned long long ai = pack_dup(a[cur][i]);
 #pragma unroll
-        for (int b = 0; b < MM; ++b)
-          if (b < cols) yrow[b] = yr[b];
+        for (int j = 0; j < MK / 2; ++j) acc[i][j] = fma2(ai, b2[cur][j], acc[i][j]);
+      }
+    }
+    // every lane's reads of the stage are done (their values are in the
+    // accumulators); lane 0 counts the warp out with release semantics, and
+    // the warp that completes the count acquires the others' releases,
+    // orders them before the async proxy's writes and refills the stage
+    __syncwarp();
+    if (lane == 0) {
+      uint32_t prev;
+      asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;\n"
+                   : "=r"(prev)
+                   : "r"((uint32_t)__cvta_generic_to_shared(&s_done[st]))
+                   : "memory");
+      if (prev + 1 == (uint32_t)(Cfg::NW * (ch / NS + 1)) && ch + NS < nchunks) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        issue(ch + NS, st);
+        atomicMax(&s_issued, ch + NS + 1);
       }
     }
   }
+  // every thread done with the stages the epilogue reuses
+  const bool cta_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (!cta_ok && tid == 0) {
+    // a wait gave up: wait (bounded) for the copies that may still be in
+    // flight -- at most the last chunk issued to each stage -- before the
+    // shared memory is given up; the CTA still takes part in the cluster
+    // barriers below, so that no peer waits forever
+    atomicExch(err, 1);
+    const int iss = s_issued;
+    for (int s2 = 0; s2 < NS && s2 < iss; ++s2) {
+      const int c_last = s2 + ((iss - 1 - s2) / NS) * NS;
+      (void)mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&full[s2]),
+                              (uint32_t)((c_last / NS) & 1));
+    }
+  }
+
+  float* Es = sm;
+  if (cta_ok) {
+#pragma unroll
+    for (int s4 = 0; s4 < MK / 4; ++s4)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int kl = s4 * 4 * LK + lk * 4 + jj;
+        float* dst = Es + ((size_t)fl * KB + kl) * ETB + lt * MT;
+#pragma unroll
+        for (int i = 0; i < MT; i += 4) {
+          float v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 pr = unpack2(acc[i + u][2 * s4 + jj / 2]);
+            v[u] = (jj & 1) ? pr.y : pr.x;
+          }
+          *reinterpret_cast<float4*>(dst + i) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+      }
+  }
+  // every CTA's accumulators are in its shared memory
+  cluster_sync_all();
+  if (cta_ok) {
+    uint32_t es[NCL];  // Es of each CTA of the cluster
+#pragma unroll
+    for (int r = 0; r < NCL; ++r) es[r] = cluster_map(smem_u32(Es), (uint32_t)r);
+    const int64_t plane = (int64_t)g.Ho * g.Wo;
+    const int p_lo = (int)((int64_t)TB * KB * rank / NCL);
+    const int p_hi = (int)((int64_t)TB * KB * (rank + 1) / NCL);
+    for (int p = p_lo + tid; p < p_hi; p += NT) {
+      const int t = p % TB, kl = p / TB;
+      const int rows = s_rows[t];
+      if (rows == 0) continue;
+      otx_tile<MM>(
+          [&](int q) {
+            return ld_dsmem(es[q / FC] + (uint32_t)((((q % FC) * KB + kl) * ETB + t) * 4));
+          },
+          Mx, y + s_ybase[t] + (int64_t)(k0 + kl) * plane, rows, s_cols[t], g.Wo);
+    }
+  }
+  // no CTA leaves while a peer may still read its shared memory.  Relaxed:
+  // the values of every peer read were consumed before its thread arrives,
+  // and the output stores need no ordering here (a release would wait for
+  // them).
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
 }
 
 // Blocked workspace of a tile shape: Vb, then Ub (256-byte aligned).
@@ -810,6 +1086,37 @@ static size_t split_ws_for(const LayerGeom& g) {
   using Cfg = FusedCfg<FUSED_TARGS>;
   if (g.K % Cfg::KB != 0) return 0;
   return split_ws_bytes(split_geom(g, Cfg::TB, Cfg::KB, CC));
+}
+
+// Filter and input transforms into the blocked layouts of `sg`; false when
+// a launch dimension would overflow.
+template <int MM>
+static bool launch_split_transforms(const float* x, const float* w, const LayerGeom& g,
+                                    const LayerMats& M, const SplitGeom& sg, float* Ub, float* Vb,
+                                    cudaStream_t st) {
+  const int64_t nfl = (int64_t)sg.nch * sg.CC * g.K;
+  const size_t csm = (size_t)g.F * sg.UPL * sizeof(float);
+  constexpr int kMaxCsm = 96 * 1024;
+  if (sg.nch > 65535 || (nfl + 255) / 256 > 0x7fffffffLL || csm > (size_t)kMaxCsm) return false;
+  static bool attr_set[16] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (dev < 16 && !attr_set[dev]) {
+    if (cudaFuncSetAttribute(k_input_transform_blk<MM>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxCsm) != cudaSuccess)
+      return false;
+    attr_set[dev] = true;
+  }
+  {
+    ProfScope ps(kKFilter, st);
+    k_filter_transform_blk<<<(unsigned)((nfl + 255) / 256), 256, 0, st>>>(w, Vb, g.C, g.K, M, sg);
+  }
+  {
+    ProfScope ps(kKInput, st);
+    k_input_transform_blk<MM><<<dim3((unsigned)sg.ntb, (unsigned)sg.nch), sg.CC * sg.TB, csm,
+                                st>>>(x, Ub, g, M, sg);
+  }
+  return true;
 }
 
 template <SPLIT_TPARAMS>
@@ -837,22 +1144,58 @@ static int launch_split(const float* x, const float* w, float* y, const LayerGeo
     attr_set[dev] = true;
   }
   const int64_t nblk = (int64_t)sg.nkb * sg.ntb;
-  const int64_t nfl = (int64_t)sg.nch * CC * g.K;
   static_assert(CC * Cfg::TB <= 256, "one input-transform thread per (channel, tile) of a chunk");
-  if (nblk > 0x7fffffffLL || sg.nch > 65535 || (nfl + 255) / 256 > 0x7fffffffLL) return kFallback;
-  {
-    ProfScope ps(kKFilter, st);
-    k_filter_transform_blk<<<(unsigned)((nfl + 255) / 256), 256, 0, st>>>(w, Vb, g.C, g.K, M, sg);
-  }
-  {
-    ProfScope ps(kKInput, st);
-    const size_t csm = (size_t)Cfg::F * sg.UPL * sizeof(float);
-    k_input_transform_blk<MM><<<dim3((unsigned)sg.ntb, (unsigned)sg.nch), CC * Cfg::TB, csm, st>>>(
-        x, Ub, g, M, sg);
-  }
+  if (nblk > 0x7fffffffLL || !launch_split_transforms<MM>(x, w, g, M, sg, Ub, Vb, st))
+    return kFallback;
   {
     ProfScope ps(kKFused, st);
     k_gemm_otx<SPLIT_TARGS><<<(unsigned)nblk, Cfg::NT, SC::SMEM, st>>>(Ub, Vb, y, g, M, sg, err);
+  }
+  note_launches(3);
+  WINO_CUDA_TRY(cudaGetLastError());
+  return WINO_OK;
+}
+
+// The cluster form of a tile shape: the same transforms and blocked
+// layouts, then k_gemm_otx_cl.
+template <CL_TPARAMS>
+static size_t cl_ws_for(const LayerGeom& g) {
+  using Cfg = ClCfg<CL_TARGS>;
+  if (g.F != Cfg::F || g.K % Cfg::KB != 0) return 0;
+  return split_ws_bytes(split_geom(g, Cfg::TB, Cfg::KB, CC));
+}
+
+template <CL_TPARAMS>
+static int launch_split_cl(const float* x, const float* w, float* y, const LayerGeom& g,
+                           const LayerMats& M, void* ws, size_t ws_bytes, cudaStream_t st) {
+  using Cfg = ClCfg<CL_TARGS>;
+  if (g.K % Cfg::KB != 0) return kFallback;
+  const SplitGeom sg = split_geom(g, Cfg::TB, Cfg::KB, CC);
+  if (ws_bytes < split_ws_bytes(sg)) return kFallback;
+  float* Vb = (float*)ws;
+  float* Ub = (float*)((char*)ws + (((size_t)sg.vb_floats() * 4 + 255) & ~(size_t)255));
+  int* err = nullptr;
+  {
+    int rc = wait_error_flag(&err);
+    if (rc != WINO_OK) return rc;
+  }
+  static bool attr_set[16] = {false};
+  int dev = 0;
+  WINO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 16 && !attr_set[dev]) {
+    WINO_CUDA_TRY(cudaFuncSetAttribute(k_gemm_otx_cl<CL_TARGS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg::SMEM));
+    attr_set[dev] = true;
+  }
+  const int64_t nctas = (int64_t)NCL * sg.nkb * sg.ntb;
+  static_assert(CC * Cfg::TB <= 256, "one input-transform thread per (channel, tile) of a chunk");
+  if (nctas > 0x7fffffffLL || !launch_split_transforms<MM>(x, w, g, M, sg, Ub, Vb, st))
+    return kFallback;
+  {
+    ProfScope ps(kKFused, st);
+    k_gemm_otx_cl<CL_TARGS><<<(unsigned)nctas, Cfg::NT, Cfg::SMEM, st>>>(Ub, Vb, y, g, M, sg,
+                                                                        err);
   }
   note_launches(3);
   WINO_CUDA_TRY(cudaGetLastError());
@@ -881,8 +1224,22 @@ static int launch_split(const float* x, const float* w, float* y, const LayerGeo
 #define SPLIT_M6_0 6, 8, 1, 4, 1, 8, 16, 4, 2, 1
 #define SPLIT_M6_1 6, 8, 2, 2, 1, 8, 16, 4, 3, 1
 #define SPLIT_M6_2 6, 8, 2, 2, 1, 8, 16, 2, 4, 1
+// Cluster tile shapes, as (MM, NCL, LX, LT, LK, MT, MK, CC, NS, MINB): 32
+// (the last of each m: 16) tiles x 32 output channels per cluster, 8 x 8
+// outputs of one frequency per thread, alpha^2 / NCL frequencies per CTA.
+// The 16-tile shapes halve the work per cluster, and with it the last,
+// partly filled wave of the deep VGG16 stages (784 clusters at stage 4 are
+// 5.2 waves of 152 SMs' resident clusters; 256 at stage 5 are 1.7).
+#define CL_M4_0 4, 3, 2, 4, 4, 8, 8, 8, 3, 2
+#define CL_M4_1 4, 3, 2, 4, 4, 8, 8, 8, 2, 3
+#define CL_M4_2 4, 6, 2, 4, 4, 8, 8, 8, 3, 4
+#define CL_M6_0 6, 4, 2, 4, 4, 8, 8, 8, 2, 2
+#define CL_M6_1 6, 8, 2, 4, 4, 8, 8, 8, 3, 3
+#define CL_M4_3 4, 3, 4, 2, 4, 8, 8, 8, 2, 5
+#define CL_M6_2 6, 4, 4, 2, 4, 8, 8, 8, 2, 4
 
-int split_configs(int m) { return m == 2 ? 1 : 3; }
+// Tile shapes per m: the single-CTA ones first, then the cluster ones.
+int split_configs(int m) { return m == 2 ? 1 : m == 4 ? 7 : 6; }
 
 size_t split_workspace_bytes(const LayerGeom& g) {
   size_t b = 0;
@@ -892,11 +1249,18 @@ size_t split_workspace_bytes(const LayerGeom& g) {
     mx(split_ws_for<SPLIT_M4_0>(g));
     mx(split_ws_for<SPLIT_M4_1>(g));
     mx(split_ws_for<SPLIT_M4_2>(g));
+    mx(cl_ws_for<CL_M4_0>(g));
+    mx(cl_ws_for<CL_M4_1>(g));
+    mx(cl_ws_for<CL_M4_2>(g));
+    mx(cl_ws_for<CL_M4_3>(g));
   }
   if (g.F == 64) {
     mx(split_ws_for<SPLIT_M6_0>(g));
     mx(split_ws_for<SPLIT_M6_1>(g));
     mx(split_ws_for<SPLIT_M6_2>(g));
+    mx(cl_ws_for<CL_M6_0>(g));
+    mx(cl_ws_for<CL_M6_1>(g));
+    mx(cl_ws_for<CL_M6_2>(g));
   }
   return b;
 }
@@ -911,13 +1275,24 @@ int layer_forward_split(const float* x, const float* w, float* y, const LayerGeo
   if (cfg < 0 || cfg >= split_configs(M.m)) return kFallback;
   if (M.m == 2) return launch_split<SPLIT_M2_0>(x, w, y, g, M, ws, ws_bytes, st);
   if (M.m == 4) {
-    if (cfg == 0) return launch_split<SPLIT_M4_0>(x, w, y, g, M, ws, ws_bytes, st);
-    if (cfg == 1) return launch_split<SPLIT_M4_1>(x, w, y, g, M, ws, ws_bytes, st);
-    return launch_split<SPLIT_M4_2>(x, w, y, g, M, ws, ws_bytes, st);
+    switch (cfg) {
+      case 0: return launch_split<SPLIT_M4_0>(x, w, y, g, M, ws, ws_bytes, st);
+      case 1: return launch_split<SPLIT_M4_1>(x, w, y, g, M, ws, ws_bytes, st);
+      case 2: return launch_split<SPLIT_M4_2>(x, w, y, g, M, ws, ws_bytes, st);
+      case 3: return launch_split_cl<CL_M4_0>(x, w, y, g, M, ws, ws_bytes, st);
+      case 4: return launch_split_cl<CL_M4_1>(x, w, y, g, M, ws, ws_bytes, st);
+      case 5: return launch_split_cl<CL_M4_2>(x, w, y, g, M, ws, ws_bytes, st);
+      default: return launch_split_cl<CL_M4_3>(x, w, y, g, M, ws, ws_bytes, st);
+    }
   }
-  if (cfg == 0) return launch_split<SPLIT_M6_0>(x, w, y, g, M, ws, ws_bytes, st);
-  if (cfg == 1) return launch_split<SPLIT_M6_1>(x, w, y, g, M, ws, ws_bytes, st);
-  return launch_split<SPLIT_M6_2>(x, w, y, g, M, ws, ws_bytes, st);
+  switch (cfg) {
+    case 0: return launch_split<SPLIT_M6_0>(x, w, y, g, M, ws, ws_bytes, st);
+    case 1: return launch_split<SPLIT_M6_1>(x, w, y, g, M, ws, ws_bytes, st);
+    case 2: return launch_split<SPLIT_M6_2>(x, w, y, g, M, ws, ws_bytes, st);
+    case 3: return launch_split_cl<CL_M6_0>(x, w, y, g, M, ws, ws_bytes, st);
+    case 4: return launch_split_cl<CL_M6_1>(x, w, y, g, M, ws, ws_bytes, st);
+    default: return launch_split_cl<CL_M6_2>(x, w, y, g, M, ws, ws_bytes, st);
+  }
 }
 
 }  // namespace wino

@@ -305,8 +305,9 @@ int split_configs(int m);
 // (twice each, keeping the second) and caches the fastest for the process.
 // Timing synchronises the stream, so it is skipped while the stream is being
 // captured into a graph (split tile shape 0 is used then) and when
-// WINO_AUTOTUNE=0.  WINO_LAYER_VARIANT=fused|split|split1|split2|general
-// forces a variant.
+// WINO_AUTOTUNE=0.  WINO_LAYER_VARIANT=fused|split|split<c>|general forces a
+// variant (split<c>: split tile shape c = 1..9; a shape the layer does not
+// have falls back as below).
 // ---------------------------------------------------------------------------
 enum LayerVariant {
   kVarUnknown = 0,
@@ -331,8 +332,8 @@ static int forced_variant() {
   if (!v) return kVarUnknown;
   if (!strcmp(v, "fused")) return kVarFused;
   if (!strcmp(v, "split")) return kVarSplit;
-  if (!strcmp(v, "split1")) return kVarSplitN + 1;
-  if (!strcmp(v, "split2")) return kVarSplitN + 2;
+  if (!strncmp(v, "split", 5) && v[5] >= '1' && v[5] <= '9' && v[6] == 0)
+    return kVarSplitN + (v[5] - '0');
   if (!strcmp(v, "general")) return kVarGeneral;
   return kVarUnknown;
 }
@@ -354,9 +355,9 @@ static int tune_variant(const float* x, const float* w, float* y, const LayerGeo
   WINO_CUDA_TRY(cudaEventCreate(&b));
   float best = 1e30f;
   int best_var = kVarGeneral;
-  int cands[8], nc = 0;
+  int cands[16], nc = 0;
   cands[nc++] = kVarSplit;
-  for (int c = 1; c < split_configs(M.m) && nc < 7; ++c) cands[nc++] = kVarSplitN + c;
+  for (int c = 1; c < split_configs(M.m) && nc < 15; ++c) cands[nc++] = kVarSplitN + c;
   cands[nc++] = kVarFused;
   for (int ci = 0; ci < nc; ++ci) {
     const int var = cands[ci];

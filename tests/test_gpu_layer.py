@@ -125,16 +125,26 @@ def _fused_launches(wino, fn):
     return wino.wino_profile_read("fused_layer")[1]
 
 
-@pytest.mark.parametrize("variant", ["fused", "split", "split1", "split2"])
+# split tile shapes per m: single-CTA shapes, then (m = 4: split3-6, m = 6:
+# split3-5) the cluster shapes whose CTAs split the frequencies
+SPLIT_SHAPES = {2: 1, 4: 7, 6: 6}
+VARIANTS = ["fused", "split"] + [f"split{c}" for c in range(1, 7)]
+
+
+def _has_variant(m, variant):
+    return not variant.startswith("split") or int(variant[5:] or 0) < SPLIT_SHAPES[m]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("m", [2, 4, 6])
 @pytest.mark.parametrize("shape", [(1, 13, 64, 17, 19, 1), (2, 70, 128, 9, 10, 1),
                                    (1, 3, 192, 6, 30, 0), (1, 9, 64, 1, 1, 2)])
 def test_fused_layer_bitwise_vs_oracle(wino, orc, m, shape, variant, monkeypatch):
     """The fused kernel and the split transform + GEMM/output kernels in each
-    tile shape on ragged tile blocks, channel counts off their chunking,
-    several k-blocks, 1x1 images with padding."""
-    if m == 2 and variant in ("split1", "split2"):
-        pytest.skip("F(2x2,3x3) has one split tile shape")
+    tile shape (the cluster shapes included) on ragged tile blocks, channel
+    counts off their chunking, several k-blocks, 1x1 images with padding."""
+    if not _has_variant(m, variant):
+        pytest.skip(f"F({m}x{m},3x3) has {SPLIT_SHAPES[m]} split tile shapes")
     monkeypatch.setenv("WINO_LAYER_VARIANT", variant)
     N, C, K, H, W, pad = shape
     x, w = inputs.layer_uniform(N, C, K, H, W, seed=100 + m)
@@ -145,13 +155,15 @@ def test_fused_layer_bitwise_vs_oracle(wino, orc, m, shape, variant, monkeypatch
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("variant", ["fused", "split", "split1", "split2"])
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("m", [4, 6])
 @pytest.mark.parametrize("layer", [0, 3])
 def test_vgg_full_size_sampled_tiles(wino, orc, m, layer, variant, monkeypatch):
     """The bench's configuration (VGG16 stage, N = 32, the bench's points):
     512 random (tile, k) pairs recomputed by the oracle match bit for bit."""
     import torch
+    if not _has_variant(m, variant):
+        pytest.skip(f"F({m}x{m},3x3) has {SPLIT_SHAPES[m]} split tile shapes")
     monkeypatch.setenv("WINO_LAYER_VARIANT", variant)
     C, H = inputs.VGG16_LAYERS[layer]
     x, w = inputs.vgg_layer_host(C, H, N=inputs.VGG_BATCH, seed=7)
