@@ -1217,6 +1217,8 @@ static int launch_split_cl(const float* x, const float* w, float* y, const Layer
 // on the VGG16 stack (spills, one CTA per SM).  8 x 8 tiles (ratio 4, 112
 // registers, no spills; 16 x 32 outputs per CTA, 9 warps) measured 18-35%
 // slower: one CTA per SM does not hide the per-chunk waits and the epilogue.
+// The cluster shapes below get 8 x 8 tiles at several CTAs per SM by
+// splitting the frequencies over the CTAs of a cluster.
 #define SPLIT_M2_0 2, 2, 4, 4, 1, 8, 16, 8, 2, 1
 #define SPLIT_M4_0 4, 1, 4, 8, 3, 4, 8, 8, 2, 1
 #define SPLIT_M4_1 4, 1, 8, 4, 3, 4, 8, 8, 2, 1
