@@ -219,6 +219,9 @@ __global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ 
 // pairs -- rows of 32 pairs padded to kQRow = 40 words, so the 32 stores of
 // a warp (4 tiles x 8 pairs) hit 32 distinct banks -- and leave as whole
 // 128-byte rows of 64 channels (one cache line per (f, tile) and part).
+// (Splitting the transform's rows over 2-4 blocks, for staging within 36 KB
+// and five blocks per SM, measured 8-15% slower per stack: every block
+// loads the whole patch, and the patch loads are what this kernel waits on.)
 constexpr int kQT = 4, kQC = 64, kQP = kQC / 2, kQRow = kQP + 8;
 constexpr int kQuantThreads = kQT * kQP;
 // largest staging: three parts of F = 64 frequencies (m = 6)
