@@ -216,13 +216,17 @@ __global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ 
 // One block = kQT = 4 tiles x 64 channels; a thread transforms two adjacent
 // channels of one tile (tiles fastest: neighbouring patches share input
 // rows).  The 16-bit results are staged in shared memory as 32-bit channel
-// pairs -- rows of 32 pairs padded to kQRow = 40 words, so the 32 stores of
-// a warp (4 tiles x 8 pairs) hit 32 distinct banks -- and leave as whole
-// 128-byte rows of 64 channels (one cache line per (f, tile) and part).
+// pairs -- rows of kQRow = 32 pairs, pair p of tile tl's row at word
+// p ^ 8 tl, so the 32 stores of a warp (4 tiles x 8 pairs) hit 32 distinct
+// banks with no padding -- and leave as whole 128-byte rows of 64 channels
+// (one cache line per (f, tile) and part).  (Rows padded to 40 words
+// instead held one F(6x6) split-BF16x6 block per SM, not two.)
 // (Splitting the transform's rows over 2-4 blocks, for staging within 36 KB
 // and five blocks per SM, measured 8-15% slower per stack: every block
 // loads the whole patch, and the patch loads are what this kernel waits on.)
-constexpr int kQT = 4, kQC = 64, kQP = kQC / 2, kQRow = kQP + 8;
+constexpr int kQT = 4, kQC = 64, kQP = kQC / 2, kQRow = kQP;
+// staging word of channel pair p in tile tl's row (bank-conflict swizzle)
+__device__ __forceinline__ int qswz(int p, int tl) { return p ^ (tl << 3); }
 constexpr int kQuantThreads = kQT * kQP;
 // largest staging: three parts of F = 64 frequencies (m = 6)
 constexpr int kQuantSmemMax = 3 * 64 * kQT * kQRow * 4;
@@ -294,7 +298,7 @@ __device__ __forceinline__ void quant_pair_rows(const float* __restrict__ x, con
     uint16_t qa[3], qb[3];
     split_parts(ua[f - I0 * A] * S.sU[f], mode, qa);
     split_parts(v * S.sU[f], mode, qb);
-    const int o = (f * kQT + tl) * kQRow + cp;
+    const int o = (f * kQT + tl) * kQRow + qswz(cp, tl);
     qs[o] = (uint32_t)qa[0] | ((uint32_t)qb[0] << 16);
     if (parts > 1) qs[kPart + o] = (uint32_t)qa[1] | ((uint32_t)qb[1] << 16);
     if (parts > 2) qs[2 * kPart + o] = (uint32_t)qa[2] | ((uint32_t)qb[2] << 16);
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(kQuantThreads) k_quant_input_tiled(
       quant_patch<MM, 0, A>(x, g, Mx, t, c + h, [&](int f, float v) {
         uint16_t q[3];
         split_parts(v * S.sU[f], mode, q);
-        const int o = 2 * ((f * kQT + tl) * kQRow + cp) + h;
+        const int o = 2 * ((f * kQT + tl) * kQRow + qswz(cp, tl)) + h;
         qh[o] = q[0];
         if (parts > 1) qh[2 * kPart + o] = q[1];
         if (parts > 2) qh[4 * kPart + o] = q[2];
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(kQuantThreads) k_quant_input_tiled(
     const int64_t dst = f * plane + (tb + tr) * Cp + c0 + seg * 8;
     for (int pp = 0; pp < parts; ++pp)
       *reinterpret_cast<uint4*>(dsts[pp] + dst) =
-          *reinterpret_cast<const uint4*>(qs + pp * kPart + row * kQRow + seg * 4);
+          *reinterpret_cast<const uint4*>(qs + pp * kPart + row * kQRow + qswz(seg * 4, tr));
   }
 }
 
@@ -770,7 +774,11 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
       k_filter_quant<6><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode);
     }
     const dim3 gq((unsigned)(Tp / kQT), (unsigned)(Cp / kQC));
-    const size_t qsm = (size_t)parts * g.F * kQT * kQRow * sizeof(uint32_t);
+    size_t qsm = (size_t)parts * g.F * kQT * kQRow * sizeof(uint32_t);
+    // the patch loads reuse overlapping input rows through L1, which shares
+    // the SM's storage with these blocks' staging: the two-part F(4x4) form
+    // (37 KB) runs best at four blocks per SM (six measured 4% slower)
+    if (parts == 2 && M.m == 4 && qsm < 46 * 1024) qsm = 46 * 1024;
     static bool qattr[16] = {false};
     int qdev = 0;
     WINO_CUDA_TRY(cudaGetDevice(&qdev));
