@@ -417,6 +417,17 @@ unsigned long long wino_kernel_launches(void);
  * device.                                                                  */
 int wino_wait_error(int* flag);
 
+/* The give-up path of those waits, run on purpose for tests: one warp waits
+ * on an mbarrier that nothing arrives at with the layer kernels' bounded
+ * wait, limited to `polls` polls (>= 1), gives up, sets the flag read by
+ * wino_wait_error and returns; *elapsed_ns = device time of the polls
+ * (%globaltimer).  Synchronises cuda_stream (NULL: the default stream).
+ * WINO_EINVAL for elapsed_ns NULL or polls < 1.  The layer kernels poll at
+ * most WINO_WAIT_POLLS times per wait: about a second on a GB300, where a
+ * poll of an incomplete phase suspends ~3.75 us.                          */
+#define WINO_WAIT_POLLS (1 << 18)
+int wino_wait_probe(int polls, long long* elapsed_ns, void* cuda_stream);
+
 const char* wino_last_error(void);  /* thread-local message, never NULL  */
 int wino_device_ok(void);           /* 1 when an sm_103 device is usable  */
 void wino_shutdown(void);           /* frees internal scratch and graphs  */

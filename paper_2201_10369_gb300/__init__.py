@@ -126,6 +126,8 @@ def _declare(L):
     L.wino_pointset_error_kron.restype = _i
     L.wino_wait_error.argtypes = [ctypes.POINTER(ctypes.c_int)]
     L.wino_wait_error.restype = _i
+    L.wino_wait_probe.argtypes = [_i, ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p]
+    L.wino_wait_probe.restype = _i
     L.wino_shutdown.restype = None
     for name in ("wino_make_matrices", "wino_conv1d", "wino_conv2d", "wino_set_workspace",
                  "wino_direct_conv_f64", "wino_error_stats", "wino_error_sweep"):
@@ -790,6 +792,17 @@ def wino_wait_error() -> bool:
     f = ctypes.c_int(0)
     _check(load().wino_wait_error(ctypes.byref(f)))
     return bool(f.value)
+
+
+def wino_wait_probe(polls: int) -> int:
+    """Runs the layer kernels' bounded wait on an mbarrier nothing arrives at,
+    `polls` polls, on the current stream: the wait gives up and sets the flag
+    `wino_wait_error` reports.  Returns the device time of the polls in ns."""
+    import torch
+    ns = ctypes.c_longlong(0)
+    _check(load().wino_wait_probe(int(polls), ctypes.byref(ns),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return int(ns.value)
 
 
 def wino_shutdown():

@@ -475,6 +475,16 @@ int wino_wait_error(int* flag) {
   return WINO_OK;
 }
 
+int wino_wait_probe(int polls, long long* elapsed_ns, void* cuda_stream) {
+  if (!elapsed_ns || polls < 1) {
+    set_error("elapsed_ns is NULL or polls < 1");
+    return WINO_EINVAL;
+  }
+  int st = check_device();
+  if (st != WINO_OK) return st;
+  return wait_probe(polls, elapsed_ns, (cudaStream_t)cuda_stream);
+}
+
 void wino_shutdown(void) {
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   int cur = 0;

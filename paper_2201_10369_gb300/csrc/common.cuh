@@ -7,6 +7,7 @@
 
 #include <string>
 
+#include "../../include/wino.h"
 #include "construct.cuh"
 
 namespace wino {
@@ -71,6 +72,12 @@ __device__ __forceinline__ void filter_transform_one(const float* __restrict__ g
 // up (the kernel then stores 1 and abandons its tile); wino_wait_error
 // reads and clears it.
 int wait_error_flag(int** ptr);
+// Polls of one bounded mbarrier wait in the layer kernels (~1 s).
+constexpr int kWaitPolls = WINO_WAIT_POLLS;
+// Runs the layer kernels' bounded mbarrier wait on a barrier nothing
+// arrives at, `polls` polls, on stream st; sets the flag above and stores
+// the device time of the polls (synchronises st).
+int wait_probe(int polls, long long* elapsed_ns, cudaStream_t st);
 
 // Error reporting (thread-local text, see wino_last_error).
 void set_error(const std::string& msg);

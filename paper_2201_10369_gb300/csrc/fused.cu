@@ -424,9 +424,11 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
-// Waits for phase `parity` of `bar` to complete, at most 2^22 polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
+// Waits for phase `parity` of `bar` to complete, at most `max_polls` polls;
+// false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  int max_polls = kWaitPolls) {
+  for (int it = 0; it < max_polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -440,7 +442,44 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
   return false;
 }
 
+// The failure path of the waits above, run on purpose: one warp waits on an
+// mbarrier that nothing arrives at, gives up after `polls` polls, sets the
+// device's wait-error flag as a layer kernel would and returns; ns[0] = the
+// device time the polls took.
+__global__ void k_wait_probe(int polls, int* err, long long* ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init1((uint32_t)__cvta_generic_to_shared(&bar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  long long t0, t1;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t0));
+  const bool got = mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(&bar), 0u, polls);
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t1));
+  if (threadIdx.x == 0) {
+    if (!got) atomicExch(err, 1);
+    ns[0] = t1 - t0;
+  }
+}
+
 }  // namespace
+
+int wait_probe(int polls, long long* elapsed_ns, cudaStream_t st) {
+  int* err = nullptr;
+  int rc = wait_error_flag(&err);
+  if (rc != WINO_OK) return rc;
+  long long* d_ns = nullptr;
+  WINO_CUDA_TRY(cudaMalloc(&d_ns, sizeof(long long)));
+  k_wait_probe<<<1, 32, 0, st>>>(polls, err, d_ns);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(elapsed_ns, d_ns, sizeof(long long), cudaMemcpyDeviceToHost);
+  (void)cudaFree(d_ns);
+  WINO_CUDA_TRY(e);
+  return WINO_OK;
+}
 
 // Blocked layout geometry of one split tile shape.
 struct SplitGeom {

@@ -199,14 +199,47 @@ def test_error_stats_vs_numpy(wino):
         assert a == pytest.approx(b, rel=1e-12)
 
 
-def test_no_bounded_wait_gave_up(wino):
-    """Every layer form run by this module (FP32 split shapes with their bulk
-    copies, fused, tensor-core) completed its waits: the device's wait-error
-    flag is clear."""
+def test_no_bounded_wait_gave_up(wino, monkeypatch):
+    """Every layer form (each FP32 split tile shape, single-CTA and cluster,
+    with their bulk copies; the fused kernel; the tensor-core forms)
+    completed its waits: the device's wait-error flag is clear."""
     import torch
+    wino.wino_wait_error()
     x, w = inputs.layer_uniform(2, 70, 128, 9, 10, seed=3)
     xt, wt = torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda()
     y = torch.empty((2, 128, 9, 10), device="cuda")
-    for dt in ("f32", "bf16", "split_bf16x6"):
+    for m in (4, 6):
+        for v in [v for v in VARIANTS if _has_variant(m, v)]:
+            monkeypatch.setenv("WINO_LAYER_VARIANT", v)
+            wino.wino_conv2d(xt, wt, y, POINTS[m], m, 3, 1)
+    monkeypatch.delenv("WINO_LAYER_VARIANT")
+    for dt in ("bf16", "split_bf16x6"):
         wino.wino_conv2d(xt, wt, y, POINTS[4], 4, 3, 1, dt)
     assert not wino.wino_wait_error()
+
+
+def test_bounded_wait_gives_up_and_reports(wino):
+    """The give-up path of the layer kernels' bounded waits, run on purpose:
+    a wait on an mbarrier that nothing arrives at ends after its poll limit,
+    the kernel returns, the device flag reads set once and is then clear,
+    and the device stays usable."""
+    import torch
+    wino.wino_wait_error()
+    ns = wino.wino_wait_probe(256)
+    assert ns > 0
+    assert wino.wino_wait_error()
+    assert not wino.wino_wait_error()
+    # the context is intact: a layer still runs and matches the oracle
+    x, w = inputs.layer_uniform(1, 13, 64, 17, 19, seed=5)
+    y = torch.empty((1, 64, 17, 19), device="cuda")
+    wino.wino_conv2d(torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda(), y, POINTS[4], 4, 3,
+                     1)
+    assert np.all(np.isfinite(y.cpu().numpy()))
+    assert not wino.wino_wait_error()
+    # the layer kernels' limit at the measured time per failed poll: a wait
+    # that can never complete is abandoned within a few seconds
+    import pathlib
+    import re
+    hdr = (pathlib.Path(__file__).resolve().parents[1] / "include" / "wino.h").read_text()
+    polls = 1 << int(re.search(r"#define WINO_WAIT_POLLS \(1 << (\d+)\)", hdr).group(1))
+    assert ns / 256 * polls < 5e9, (ns / 256, polls)
