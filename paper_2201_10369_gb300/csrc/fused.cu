@@ -1270,7 +1270,9 @@ static int launch_split_cl(const float* x, const float* w, float* y, const Layer
 // outputs of one frequency per thread, alpha^2 / NCL frequencies per CTA.
 // The 16-tile shapes halve the work per cluster, and with it the last,
 // partly filled wave of the deep VGG16 stages (784 clusters at stage 4 are
-// 5.2 waves of 152 SMs' resident clusters; 256 at stage 5 are 1.7).
+// 5.2 waves of 152 SMs' resident clusters; 256 at stage 5 are 1.7).  32 x
+// 64 blocks (one warp per frequency, 6 or 8 CTAs per cluster, two per SM)
+// measured 10-25% slower than the best shape on every VGG16 stage.
 #define CL_M4_0 4, 3, 2, 4, 4, 8, 8, 8, 3, 2
 #define CL_M4_1 4, 3, 2, 4, 4, 8, 8, 8, 2, 3
 #define CL_M4_2 4, 6, 2, 4, 4, 8, 8, 8, 3, 4
