@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "../../include/wino.h"
+#include "async_copy.cuh"
 #include "common.cuh"
 
 namespace wino {
@@ -408,44 +409,10 @@ int layer_forward_fused(const float* x, const float* w, float* y, const LayerGeo
 
 namespace {
 
-__device__ __forceinline__ void mbar_init1(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-// One bulk copy global -> shared, completion counted on `bar` in bytes.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
-          "r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-// Waits for phase `parity` of `bar` to complete, at most `max_polls` polls;
-// false when it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
-                                                  int max_polls = kWaitPolls) {
-  for (int it = 0; it < max_polls; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// The failure path of the waits above, run on purpose: one warp waits on an
-// mbarrier that nothing arrives at, gives up after `polls` polls, sets the
-// device's wait-error flag as a layer kernel would and returns; ns[0] = the
-// device time the polls took.
+// The give-up path of the layer kernels' bounded waits (mbar_wait_bounded),
+// run on purpose: one warp waits on an mbarrier that nothing arrives at,
+// gives up after `polls` polls, sets the device's wait-error flag as a layer
+// kernel would and returns; ns[0] = the device time the polls took.
 __global__ void k_wait_probe(int polls, int* err, long long* ns) {
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x == 0) {

@@ -24,14 +24,17 @@
 // operands in range; for BF16 it only guards the subnormal range of lo.
 //
 // Pipeline: filter transform (FP32) -> per-frequency max |V| -> V rounded
-// into [F][K][Cp] (K-major B operand); input transform (FP32) rounded into
-// [F][Tp][Cp] (K-major A operand); k_tc_gemm; the general output transform.
+// into the blocked image of [F][K][Cp] (K-major B operand); input transform
+// (FP32) rounded into the blocked image of [F][Tp][Cp] (K-major A operand);
+// k_tc_gemm; the general output transform.
 // k_tc_gemm: one CTA = one frequency x 128 tiles (MMA M) x NB output
 // channels (MMA N <= 256), contraction over Cp in chunks of 64 channels
-// (one 128-byte swizzle row per operand row).  Operands are staged by
-// cp.async into the SWIZZLE_128B K-major layout; one thread issues
-// tcgen05.mma (K = 16 per instruction) and commits to an mbarrier; every
-// wait on it is bounded and records an error instead of hanging.
+// (one 128-byte swizzle row per operand row).  The quantising kernels write
+// the operands as the SWIZZLE_128B K-major shared-memory images of these
+// chunks, so one thread moves each chunk with one bulk copy per operand
+// part (mbarrier-counted), issues tcgen05.mma (K = 16 per instruction) and
+// commits to a second mbarrier; every wait is bounded and records an error
+// instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -42,9 +45,35 @@
 #include <algorithm>
 
 #include "../../include/wino.h"
+#include "async_copy.cuh"
 #include "common.cuh"
 
 namespace wino {
+
+constexpr int kTcM = 128;    // tiles per CTA (MMA M)
+constexpr int kTcKc = 64;    // channels per chunk: one 128-byte row per operand row
+
+// Operand parts in HBM are the shared-memory images the contraction copies
+// whole (one bulk copy per operand part and chunk): U per (frequency,
+// 128-tile block, 64-channel chunk) one 16 KB block, V per (frequency,
+// NB-channel k block, chunk) one NB x 128-byte block.  Row r of a block (a
+// tile, an output channel) is 128 bytes at r x 128, its 16-byte piece j (8
+// channels) at position j ^ (r & 7): the 128-byte swizzle the MMA's K-major
+// operand descriptors name.  Element index of (f, tile t, channel c) in a U
+// part, and of (f, output channel k, c) in a V part:
+__host__ __device__ __forceinline__ int64_t tc_u_index(int f, int64_t t, int c, int64_t ntb,
+                                                       int nch) {
+  const int64_t blk = ((int64_t)f * ntb + t / kTcM) * nch + c / kTcKc;
+  const int r = (int)(t % kTcM), j = (c % kTcKc) / 8;
+  return blk * (kTcM * kTcKc) + r * kTcKc + ((j ^ (r & 7)) * 8) + (c % 8);
+}
+__host__ __device__ __forceinline__ int64_t tc_v_index(int f, int k, int c, int NB, int nkb,
+                                                       int nch) {
+  const int64_t blk = ((int64_t)f * nkb + k / NB) * nch + c / kTcKc;
+  const int r = k % NB, j = (c % kTcKc) / 8;
+  return blk * ((int64_t)NB * kTcKc) + r * kTcKc + ((j ^ (r & 7)) * 8) + (c % 8);
+}
+
 
 __global__ void k_output_transform(const float* __restrict__ Mi, float* __restrict__ y,
                                    const LayerGeom g, const LayerMats M);
@@ -170,10 +199,11 @@ __global__ void __launch_bounds__(kFvThreads) k_filter_vmax(const float* __restr
 }
 
 // Filter transform recomputed, scaled by sV[f] = 2^(1 - e) for max |V[f]| =
-// m 2^e, m in [0.5, 1), and split into the operand parts V0/V1/V2
-// [f][k][Cp] (K-major B operand; channels c >= C zero).  One thread per
-// (k, c), channels fastest (coalesced 16-bit stores).  Block 0 also records
-// sV for the epilogue.
+// m 2^e, m in [0.5, 1), and split into the operand parts V0/V1/V2 (the
+// blocked image of tc_v_index for k blocks of NB; channels c >= C zero).
+// One thread per (k, c), channels fastest (each 64-channel row is one
+// 128-byte line, its pieces permuted).  Block 0 also records sV for the
+// epilogue.
 template <int MM>
 __global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ w, int C, int K,
                                                       int Cp, const LayerMats M,
@@ -181,7 +211,8 @@ __global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ 
                                                       float* __restrict__ sV,
                                                       uint16_t* __restrict__ V0,
                                                       uint16_t* __restrict__ V1,
-                                                      uint16_t* __restrict__ V2, int mode) {
+                                                      uint16_t* __restrict__ V2, int mode,
+                                                      int NB) {
   constexpr int F = (MM + 2) * (MM + 2);
   __shared__ float ss[F];
   if (threadIdx.x < F) {
@@ -204,7 +235,7 @@ __global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ 
   for (int f = 0; f < F; ++f) {
     uint16_t q[3];
     split_parts(v[f] * ss[f], mode, q);
-    const int64_t o = ((int64_t)f * K + k) * Cp + c;
+    const int64_t o = tc_v_index(f, k, c, NB, K / NB, Cp / kTcKc);
     V0[o] = q[0];
     if (parts > 1) V1[o] = q[1];
     if (parts > 2) V2[o] = q[2];
@@ -339,15 +370,14 @@ __global__ void __launch_bounds__(kQuantThreads) k_quant_input_tiled(
   }
   __syncthreads();
   // rows (f, tile) of 64 channels = 8 x 16-byte stores, consecutive threads
-  // on consecutive segments of a row
-  const int64_t plane = Tp * Cp;
+  // on consecutive segments of a row (one 128-byte line of the blocked image)
   const int64_t tb = (int64_t)blockIdx.x * kQT;
   const int c0 = blockIdx.y * kQC;
   uint16_t* const dsts[3] = {U0, U1, U2};
   for (int e = threadIdx.x; e < F * kQT * 8; e += kQuantThreads) {
     const int seg = e % 8, row = e / 8;  // row = f * kQT + tile
     const int f = row / kQT, tr = row % kQT;
-    const int64_t dst = f * plane + (tb + tr) * Cp + c0 + seg * 8;
+    const int64_t dst = tc_u_index(f, tb + tr, c0 + seg * 8, Tp / kTcM, Cp / kTcKc);
     for (int pp = 0; pp < parts; ++pp)
       *reinterpret_cast<uint4*>(dsts[pp] + dst) =
           *reinterpret_cast<const uint4*>(qs + pp * kPart + row * kQRow + qswz(seg * 4, tr));
@@ -454,21 +484,6 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kWaitPolls; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 // 32 lanes x 16 consecutive FP32 columns of TMEM, one row per thread.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
@@ -481,19 +496,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
-}
 
 }  // namespace
 
-constexpr int kTcM = 128;    // tiles per CTA (MMA M)
-constexpr int kTcKc = 64;    // channels per chunk: one 128-byte row per operand row
 constexpr int kTcThreads = 128;
 
 struct TcGemmArgs {
-  const uint16_t* U[3];  // operand parts (hi first), [F][Tp][Cp]
-  const uint16_t* V[3];  // [F][K][Cp]
+  const uint16_t* U[3];  // operand parts (hi first), blocked images (tc_u_index)
+  const uint16_t* V[3];  // blocked images (tc_v_index, k blocks of NB)
   const float* sV;
   float* M;  // [F][K][T]
   int* err;  // the device's wait-error flag: set to 1 when a bounded wait gives up
@@ -503,8 +513,8 @@ struct TcGemmArgs {
 };
 
 // Dynamic shared memory: per operand part a 1024-byte-aligned tile: A parts
-// 128 x 64, then B parts NB x 64 16-bit values, then the mbarrier and the
-// TMEM address.  Products per 16-channel step, as (A part, B part):
+// 128 x 64, then B parts NB x 64 16-bit values, then the two mbarriers and
+// the TMEM address.  Products per 16-channel step, as (A part, B part):
 //   1 part  (BF16, FP16): (0,0)
 //   2 parts (split x3):   (0,0) (0,1) (1,0)
 //   3 parts (split x6):   (0,0) into accumulator D, then (0,1) (1,0) (0,2)
@@ -528,9 +538,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
   unsigned char* As = tsm;                        // part p at As + p * a_bytes
   unsigned char* Bs = As + parts * a_bytes;       // part p at Bs + p * b_bytes
   unsigned char* tail = Bs + parts * b_bytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tail);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 8);
-  const uint32_t bar_a = smem_addr(bar);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tail);  // [0] copies landed, [1] MMAs done
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 16);
+  const uint32_t bar_ld = smem_addr(bar), bar_mma = smem_addr(bar + 1);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -539,7 +549,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a));
+    mbar_init1(bar_ld);
+    mbar_init1(bar_mma);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -550,31 +561,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
   const int fmt = (P.mode == 2) ? 0 : 1;
   const uint32_t idesc = f16_idesc(fmt, kTcM, P.NB);
   const int nchunks = P.Cp / kTcKc;
-  const int64_t aplane = P.Tp * P.Cp;
-  const int64_t bplane = (int64_t)P.K * P.Cp;
+  // this CTA's operand blocks (blocked images, see tc_u_index / tc_v_index):
+  // chunk ch of A part p at U[p] + a0 + ch * 8192, of B part p at V[p] + b0
+  // + ch * NB * 64 (16-bit elements)
+  const int64_t a0 = ((int64_t)f * gridDim.x + blockIdx.x) * nchunks * (kTcM * kTcKc);
+  const int64_t b0 = ((int64_t)f * gridDim.y + blockIdx.y) * nchunks * ((int64_t)P.NB * kTcKc);
+  // Thread 0 runs the chunk loop: two bulk copies per operand part into the
+  // stage, then the MMAs, committed to bar_mma; the stage is refilled once
+  // they completed.  The other threads wait at the barrier below.
   bool ok = true;
-  for (int ch = 0; ch < nchunks && ok; ++ch) {
-    const int c0 = ch * kTcKc;
-    // stage A (128 rows) and B (NB rows), 8 x 16-byte chunks per row, with
-    // the 128-byte swizzle: chunk j of row r goes to position j ^ (r & 7)
-    for (int e = tid; e < kTcM * 8; e += kTcThreads) {
-      const int r = e >> 3, j = e & 7;
-      const uint32_t off = r * 128 + ((j ^ (r & 7)) << 4);
-      const int64_t g = f * aplane + (t0 + r) * P.Cp + c0 + j * 8;
-      for (int pp = 0; pp < parts; ++pp)
-        cp_async16_tc(smem_addr(As + pp * a_bytes + off), P.U[pp] + g);
-    }
-    for (int e = tid; e < P.NB * 8; e += kTcThreads) {
-      const int r = e >> 3, j = e & 7;
-      const uint32_t off = r * 128 + ((j ^ (r & 7)) << 4);
-      const int64_t g = f * bplane + (int64_t)(n0 + r) * P.Cp + c0 + j * 8;
-      for (int pp = 0; pp < parts; ++pp)
-        cp_async16_tc(smem_addr(Bs + pp * b_bytes + off), P.V[pp] + g);
-    }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  if (tid == 0) {
+    for (int ch = 0; ch < nchunks; ++ch) {
+      if (ch > 0 && !mbar_wait_bounded(bar_mma, (uint32_t)((ch - 1) & 1))) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(bar_ld, (uint32_t)parts * (a_bytes + b_bytes));
+      for (int pp = 0; pp < parts; ++pp) {
+        bulk_g2s(smem_addr(As + pp * a_bytes), P.U[pp] + a0 + (int64_t)ch * (kTcM * kTcKc), a_bytes,
+                 bar_ld);
+        bulk_g2s(smem_addr(Bs + pp * b_bytes), P.V[pp] + b0 + (int64_t)ch * P.NB * kTcKc, b_bytes,
+                 bar_ld);
+      }
+      if (!mbar_wait_bounded(bar_ld, (uint32_t)(ch & 1))) {
+        ok = false;
+        // the copies may still land: wait for them (bounded) before the
+        // stage is given up
+        (void)mbar_wait_bounded(bar_ld, (uint32_t)(ch & 1));
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int kk = 0; kk < kTcKc / 16; ++kk) {
@@ -599,16 +614,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              bar_a)
+              bar_mma)
           : "memory");
     }
-    // every thread waits for this chunk's MMAs before the tiles are reused
-    if (!mbar_wait(bar_a, (uint32_t)(ch & 1))) {
-      ok = false;
-      if (lane == 0) atomicExch(P.err, 1);
-    }
-    __syncthreads();
+    // the last chunk's MMAs (and so every earlier one) completed
+    if (ok && !mbar_wait_bounded(bar_mma, (uint32_t)((nchunks - 1) & 1))) ok = false;
+    if (!ok) atomicExch(P.err, 1);
   }
+  ok = __syncthreads_and(tid == 0 ? (ok ? 1 : 0) : 1) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
   if (ok) {
@@ -765,13 +778,16 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     const unsigned bq = (unsigned)(((int64_t)g.K * Cp + 255) / 256);
     if (M.m == 2) {
       k_filter_vmax<2><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<2><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode);
+      k_filter_quant<2><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+                                            NB);
     } else if (M.m == 4) {
       k_filter_vmax<4><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<4><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode);
+      k_filter_quant<4><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+                                            NB);
     } else {
       k_filter_vmax<6><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<6><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode);
+      k_filter_quant<6><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+                                            NB);
     }
     const dim3 gq((unsigned)(Tp / kQT), (unsigned)(Cp / kQC));
     size_t qsm = (size_t)parts * g.F * kQT * kQRow * sizeof(uint32_t);
