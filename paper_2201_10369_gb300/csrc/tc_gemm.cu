@@ -521,9 +521,12 @@ struct TcGemmArgs {
 //                         (2,0) (1,1) into a second accumulator D' (TMEM
 //                         columns NB..2NB-1); the epilogue adds D + D'
 // One stage: two CTAs per SM already overlap one's loads with the other's
-// MMAs and epilogue.  A two-stage ring at two CTAs per SM (one-part forms,
-// NB = 256) measured the same within 2% on the VGG-16 stages; a two-to-four-
-// stage ring at one CTA per SM was 15-35% slower.
+// MMAs and epilogue.  With the per-thread copies this kernel used before the
+// bulk copies, a two-stage ring at two CTAs per SM (one-part forms, NB =
+// 256) measured the same within 2% on the VGG-16 stages and a two-to-four-
+// stage ring at one CTA per SM 15-35% slower; with the bulk copies a
+// two-stage ring of the one-part forms measured 1.5% faster (within run-to-
+// run spread), so the single stage stays.
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   // the swizzled tiles must start on 1024-byte boundaries (the host asks for
