@@ -664,14 +664,16 @@ static int tc_ncols(int NB, int parts) {
   return c < 32 ? 32 : c;
 }
 
-static size_t tc_smem_bytes(int NB, int parts) {
+// Dynamic shared memory of one CTA: its stage, raised so that the CTAs an
+// SM holds at once fit TMEM's 512 columns together -- at most 512 / ncols
+// of them, given the SM's shared memory (smem_sm) and the part reserved per
+// CTA (reserved).
+static size_t tc_smem_bytes(int NB, int parts, size_t smem_sm, size_t reserved) {
   const size_t a = (size_t)kTcM * 128, b = (size_t)NB * 128;
-  size_t s = (a + b) * parts + 64 + 1024;
-  // a CTA holding more than half of TMEM (512 columns) must be alone on its
-  // SM: ask for more than half of the shared memory
-  if (tc_ncols(NB, parts) > 256 && s < 120 * 1024) s = 120 * 1024;
-  // at most two CTAs per SM, so their TMEM columns (NB <= 256 each) fit
-  return s < 80 * 1024 ? 80 * 1024 : s;
+  const size_t s = (a + b) * parts + 64 + 1024;
+  const int fit = 512 / tc_ncols(NB, parts);
+  const size_t floor_b = smem_sm / (fit + 1) + 1 - reserved;
+  return s < floor_b ? floor_b : s;
 }
 
 // Workspace layout of the precision form (bytes), all 1024-aligned.
@@ -837,7 +839,18 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
   P.NB = NB;
   P.ncols = tc_ncols(NB, parts);
   P.mode = mode;
-  const size_t smem = tc_smem_bytes(NB, parts);
+  static size_t smem_sm[16] = {0}, reserved[16] = {0};
+  int sdev = 0;
+  WINO_CUDA_TRY(cudaGetDevice(&sdev));
+  if (sdev >= 16) return WINO_EUNSUPPORTED;
+  if (smem_sm[sdev] == 0) {
+    int v = 0, r = 0;
+    WINO_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, sdev));
+    WINO_CUDA_TRY(cudaDeviceGetAttribute(&r, cudaDevAttrReservedSharedMemoryPerBlock, sdev));
+    reserved[sdev] = (size_t)r;
+    smem_sm[sdev] = (size_t)v;
+  }
+  const size_t smem = tc_smem_bytes(NB, parts, smem_sm[sdev], reserved[sdev]);
   static bool attr_set[16] = {false};
   int dev = 0;
   WINO_CUDA_TRY(cudaGetDevice(&dev));
