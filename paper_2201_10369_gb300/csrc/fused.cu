@@ -1,6 +1,15 @@
 // fused.cu -- fused FP32 Winograd layer F(m x m, 3 x 3), m in {2, 4, 6}.
 //
-// One CTA owns TB consecutive tiles x KB output channels and ALL alpha^2
+// Three forms of the layer, bit-identical to one another and to the general
+// path in layer.cu (the layer autotuner there picks one per shape):
+//   - k_fused_layer (below): input transform, contraction and output
+//     transform in one kernel;
+//   - the split variant: k_input_transform_blk writes U once in a blocked
+//     layout, k_gemm_otx contracts and fuses the output transform;
+//   - its cluster form, k_gemm_otx_cl: a tile block's alpha^2 frequencies
+//     spread over the CTAs of a thread-block cluster.
+//
+// k_fused_layer: one CTA owns TB consecutive tiles x KB output channels and ALL alpha^2
 // frequencies, so neither the transformed input U nor the Winograd-domain
 // products M ever leave the SM (the unfused pipeline in layer.cu writes and
 // re-reads both through HBM).  Per chunk of CC input channels:
