@@ -590,6 +590,27 @@ struct SplitCfg {
 #define SPLIT_TPARAMS FUSED_TPARAMS, int NS, int MINB
 #define SPLIT_TARGS FUSED_TARGS, NS, MINB
 
+// Output coordinates of tile t for an epilogue: ybase = offset of
+// y[n][0][ti m][tj m], rows / cols = the tile's valid output rows and
+// columns (all 0 for t past the last tile).
+template <int MM>
+__device__ __forceinline__ void tile_out_coords(const LayerGeom& g, int64_t t, int64_t& ybase,
+                                                int& rows, int& cols) {
+  if (t < g.T) {
+    const int tpi = g.th * g.tw;
+    const int n = (int)(t / tpi);
+    const int rem = (int)(t - (int64_t)n * tpi);
+    const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
+    ybase = (int64_t)n * g.K * g.Ho * g.Wo + (int64_t)ti * MM * g.Wo + tj * MM;
+    rows = min(MM, g.Ho - ti * MM);
+    cols = min(MM, g.Wo - tj * MM);
+  } else {
+    ybase = 0;
+    rows = 0;
+    cols = 0;
+  }
+}
+
 // Output transform Y = A^T M A of one (tile, output channel): M[q] (q = i A
 // + j, frequencies row-major) from `ld(q)`, Y's valid rows x cols written
 // to y_t (row stride Wo).  Z = A^T M, then Y = Z A, sums over i and j
@@ -668,22 +689,7 @@ __global__ void __launch_bounds__(FusedCfg<FUSED_TARGS>::NT, MINB)
   // per-tile output coordinates for the epilogue, computed once
   __shared__ int64_t s_ybase[TB];  // offset of y[n][0][ti m][tj m]
   __shared__ int s_rows[TB], s_cols[TB];  // valid output rows / columns (0: no tile)
-  if (tid < TB) {
-    const int64_t tg = t0 + tid;
-    if (tg < g.T) {
-      const int tpi = g.th * g.tw;
-      const int n = (int)(tg / tpi);
-      const int rem = (int)(tg - (int64_t)n * tpi);
-      const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
-      s_ybase[tid] = (int64_t)n * g.K * g.Ho * g.Wo + (int64_t)ti * MM * g.Wo + tj * MM;
-      s_rows[tid] = min(MM, g.Ho - ti * MM);
-      s_cols[tid] = min(MM, g.Wo - tj * MM);
-    } else {
-      s_ybase[tid] = 0;
-      s_rows[tid] = 0;
-      s_cols[tid] = 0;
-    }
-  }
+  if (tid < TB) tile_out_coords<MM>(g, t0 + tid, s_ybase[tid], s_rows[tid], s_cols[tid]);
   if (tid == 0) {
 #pragma unroll
     for (int st = 0; st < NS; ++st) mbar_init1((uint32_t)__cvta_generic_to_shared(&full[st]));
@@ -913,22 +919,7 @@ __global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(ClCfg<CL_TARGS>::N
   const float* ublk = Ub + tb * nchunks * F * Cfg::UPL + (int64_t)rank * Cfg::SU;
   const float* vblk = Vb + (int64_t)kb * nchunks * F * Cfg::VPL + (int64_t)rank * Cfg::SV;
 
-  if (tid < TB) {
-    const int64_t tg = t0 + tid;
-    if (tg < g.T) {
-      const int tpi = g.th * g.tw;
-      const int n = (int)(tg / tpi);
-      const int rem = (int)(tg - (int64_t)n * tpi);
-      const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
-      s_ybase[tid] = (int64_t)n * g.K * g.Ho * g.Wo + (int64_t)ti * MM * g.Wo + tj * MM;
-      s_rows[tid] = min(MM, g.Ho - ti * MM);
-      s_cols[tid] = min(MM, g.Wo - tj * MM);
-    } else {
-      s_ybase[tid] = 0;
-      s_rows[tid] = 0;
-      s_cols[tid] = 0;
-    }
-  }
+  if (tid < TB) tile_out_coords<MM>(g, t0 + tid, s_ybase[tid], s_rows[tid], s_cols[tid]);
   auto issue = [&](int ch, int st) {
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&full[st]);
     const uint32_t dst = smem_u32(sm + st * Cfg::STAGE);
