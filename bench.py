@@ -41,10 +41,17 @@ PTS4 = [0.0, -1 / C4, -C4, C4, 1 / C4, math.inf]
 PTS6 = [0.0, -1 / C6, -C6, C6, 1 / C6, -D6, D6, math.inf]
 METRIC = "Winograd layer effective TFLOP/s at stated FP64 error; c-sweep evals/s vs plain"
 # the layer stacks of one step: key -> (m, points, contraction dtype)
-# sub-batches per layer in the end-to-end pipeline (measured on GB300, F(4x4)
-# stack: 1 -> 7.18 ms per step, 2 -> 5.94, 4 -> 6.45, 8 -> 7.66; beyond 2 the
-# host's per-call enqueue cost outweighs the earlier start of the copies)
-E2E_CHUNKS = 2
+# End-to-end pipeline of the F(4x4) stack: sub-batches per VGG16 stage and
+# the order the stages enter the pipeline.  The copies (~170 GB/s each way)
+# bound it, and copy-out can only start once the first sub-batch is in and
+# computed: small first units start it early, large stages split finely keep
+# it fed, and the small deep stages are not split (their calls would be
+# dominated by fixed per-call work).  Measured on GB300 (TFLOP/s): 2
+# sub-batches for every stage, stages in order: 84.9; (8, 4, 2, 1, 1) in
+# order: 89.1; (16, 8, 4, 2, 1): 86.0; (8, 4, 2, 1, 1), stages 4 and 5
+# first: 90.4 (kept); uniform 4 or 8 sub-batches were slower than 2.
+E2E_CHUNKS = (8, 4, 2, 1, 1)
+E2E_ORDER = (4, 3, 0, 1, 2)
 STACKS = {"f4x4": (4, PTS4, "f32"), "f6x6": (6, PTS6, "f32"),
           "f4x4_bf16": (4, PTS4, "bf16"), "f4x4_split_bf16x3": (4, PTS4, "split_bf16x3"),
           "f4x4_split_bf16x6": (4, PTS4, "split_bf16x6"),
@@ -378,9 +385,10 @@ def run_ours(args, rank, world, local_rank):
                       for s_, q_ in zip(*np.nonzero(rows))])
 
     # e2e: the F(4x4) FP32 stack through the public API with host buffers,
-    # pipelined as a caller of the API would: each layer's batch runs as
-    # E2E_CHUNKS sub-batches (wino_conv2d on a batch slice computes the same
-    # outputs); a sub-batch's input is copied in on one stream, it runs on a
+    # pipelined as a caller of the API would: the stages enter in the order
+    # E2E_ORDER, stage l's batch as E2E_CHUNKS[l] sub-batches (wino_conv2d on a
+    # batch slice computes the same outputs); a sub-batch's input is copied in
+    # on one stream, it runs on a
     # second once that input has landed, and its output is copied out on a
     # third once computed, so the host transfers (the bound: ~200 GB/s each
     # way) overlap compute and each other from the first sub-batch on.  Timed
@@ -392,8 +400,10 @@ def run_ours(args, rank, world, local_rank):
     d2h = sum(y.numel() * 4 for y in Y["f4x4"])
     s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     nl = len(layers)
-    units = [(li, c * N // E2E_CHUNKS, (c + 1) * N // E2E_CHUNKS)
-             for li in range(nl) for c in range(E2E_CHUNKS)]
+    order = [li for li in E2E_ORDER if li < nl] + [li for li in range(nl) if li not in E2E_ORDER]
+    chunks = [E2E_CHUNKS[li] if li < len(E2E_CHUNKS) else 1 for li in range(nl)]
+    units = [(li, c * N // chunks[li], (c + 1) * N // chunks[li])
+             for li in order for c in range(chunks[li])]
     ev_in = [torch.cuda.Event() for _ in units]
     ev_c = [torch.cuda.Event() for _ in units]
     m4, p4, dt4 = STACKS["f4x4"]
@@ -482,10 +492,11 @@ def run_ours(args, rank, world, local_rank):
         "rooflines": roofs,
         "e2e": {"value": ve2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "how": "F(4x4) FP32 stack via wino_conv2d from pinned host buffers; each "
-                       "layer as %d sub-batches, per sub-batch copy-in, layer and copy-out on "
-                       "three streams (event-ordered), so transfers overlap compute" % E2E_CHUNKS,
-                "sub_batches_per_layer": E2E_CHUNKS},
+                "how": "F(4x4) FP32 stack via wino_conv2d from pinned host buffers; the "
+                       "stages split into sub-batches, per sub-batch copy-in, layer and "
+                       "copy-out on three streams (event-ordered), so transfers overlap compute",
+                "sub_batches_per_layer": list(E2E_CHUNKS[:len(layers)]),
+                "stage_order": [li for li in E2E_ORDER if li < len(layers)]},
         "gpu_launches": int(launches),
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk,
