@@ -1239,7 +1239,9 @@ static int launch_split_cl(const float* x, const float* w, float* y, const Layer
 // partly filled wave of the deep VGG16 stages (784 clusters at stage 4 are
 // 5.2 waves of 152 SMs' resident clusters; 256 at stage 5 are 1.7).  32 x
 // 64 blocks (one warp per frequency, 6 or 8 CTAs per cluster, two per SM)
-// measured 10-25% slower than the best shape on every VGG16 stage.
+// measured 10-25% slower than the best shape on every VGG16 stage; CL_M4_2
+// with four stages 5% slower; F(6x6) over 8 CTAs of two warps (16 tiles,
+// six CTAs per SM) 2% slower than CL_M6_2.
 #define CL_M4_0 4, 3, 2, 4, 4, 8, 8, 8, 3, 2
 #define CL_M4_1 4, 3, 2, 4, 4, 8, 8, 8, 2, 3
 #define CL_M4_2 4, 6, 2, 4, 4, 8, 8, 8, 3, 4
