@@ -107,3 +107,18 @@ def test_order_validation_on_host(wino):
         assert L.wino_error_sweep_order(cg, 1, sz, 1, mk, 1, 10, 0, order, err,
                                         None) == wino.WINO_EINVAL
     assert "order" in wino.wino_last_error()
+
+
+def test_wait_probe_validation_on_host(wino):
+    """wino_wait_probe rejects a NULL result pointer or a poll count below 1
+    before any device work; WINO_WAIT_POLLS is the layer kernels' limit."""
+    import ctypes
+    import pathlib
+    import re
+    L = wino.load()
+    ns = ctypes.c_longlong(0)
+    assert L.wino_wait_probe(0, ctypes.byref(ns), None) == wino.WINO_EINVAL
+    assert L.wino_wait_probe(16, None, None) == wino.WINO_EINVAL
+    hdr = (pathlib.Path(__file__).resolve().parents[1] / "include" / "wino.h").read_text()
+    m = re.search(r"#define WINO_WAIT_POLLS \(1 << (\d+)\)", hdr)
+    assert m and 1 <= int(m.group(1)) <= 24
