@@ -689,10 +689,10 @@ def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
 NCU_TRAFFIC = {
     # k_gemm_otx_cl F(4x4) cluster tile shape split5, C = K = 512, 28x28,
     # N = 32: U read + y written
-    "fused_layer": (223.11e6, 36 * 1568 * 512 * 4 + 32 * 512 * 28 * 28 * 4),
+    "fused_layer": (223.20e6, 36 * 1568 * 512 * 4 + 32 * 512 * 28 * 28 * 4),
     # k_tc_gemm split-BF16x6, C = K = 64, 224x224, N = 8: three 16-bit parts
     # of U and V read, M written (FP32)
-    "tc_gemm": (542.40e6, 36 * (2 * 3 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
+    "tc_gemm": (538.43e6, 36 * (2 * 3 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
 }
 
 
