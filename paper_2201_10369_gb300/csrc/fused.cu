@@ -484,8 +484,10 @@ static SplitGeom split_geom(const LayerGeom& g, int TB, int KB, int CC) {
 // in L1).  The chunk's F x UPL floats are staged in shared memory and leave
 // as one contiguous run of 16-byte stores (the chunk's rows are UPL floats
 // apart, not a multiple of the 128-byte line, so per-row stores would split
-// lines).  Launch: grid (ntb, nch), blockDim = CC x TB, dynamic shared
-// memory F x UPL floats.
+// lines).  (Unpadded planes for the cluster shapes, UPL = CC TB, stored
+// straight from registers as whole lines, measured the same layer times.)
+// Launch: grid (ntb, nch), blockDim = CC x TB, dynamic shared memory
+// F x UPL floats.
 template <int MM>
 __global__ void __launch_bounds__(256) k_input_transform_blk(const float* __restrict__ x,
                                                              float* __restrict__ Ub,
