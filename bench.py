@@ -34,13 +34,28 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+SMS, SM_MAX_MHZ = 152, 2070.0
 
-C4, C6, D6 = 1.622, 2.0, 1.003
-PTS4 = [0.0, -1 / C4, -C4, C4, 1 / C4, math.inf]
-PTS6 = [0.0, -1 / C6, -C6, C6, 1 / C6, -D6, D6, math.inf]
 METRIC = "Winograd layer effective TFLOP/s at stated FP64 error; c-sweep evals/s vs plain"
-# the layer stacks of one step: key -> (m, points, contraction dtype)
+# The point sets of the layer stacks: the paper's proposed sets for 2D
+# F(4x4,3x3) (n = 6, c = 1.622) and F(6x6,3x3) (n = 8, c = 2, d = 1.003)
+# (Table 8), which the sweep reproduces within its noise, and for contrast
+# the integer / simple-fraction sets of Barabasz et al. the same table
+# compares them with (P4 + {1/2, -2} and P8).
+POINTSETS = {}
+
+
+def _pointsets():
+    from paper_2201_10369_gb300 import inputs
+    inf = math.inf
+    return {4: {"c_form": inputs.PROPOSED_SETS[(2, 6)] + [inf],
+                "integer": inputs.COMPARISON_SETS[(2, 6)] + [inf]},
+            6: {"c_form": inputs.PROPOSED_SETS[(2, 8)] + [inf],
+                "integer": inputs.COMPARISON_SETS[(2, 8)] + [inf]}}
+
+
+POINTSETS.update(_pointsets())
+PTS4, PTS6 = POINTSETS[4]["c_form"], POINTSETS[6]["c_form"]
 # End-to-end pipeline of the F(4x4) stack: sub-batches per VGG16 stage and
 # the order the stages enter the pipeline.  The copies (~170 GB/s each way)
 # bound it, and copy-out can only start once the first sub-batch is in and
@@ -52,10 +67,19 @@ METRIC = "Winograd layer effective TFLOP/s at stated FP64 error; c-sweep evals/s
 # first: 90.4 (kept); uniform 4 or 8 sub-batches were slower than 2.
 E2E_CHUNKS = (8, 4, 2, 1, 1)
 E2E_ORDER = (4, 3, 0, 1, 2)
-STACKS = {"f4x4": (4, PTS4, "f32"), "f6x6": (6, PTS6, "f32"),
-          "f4x4_bf16": (4, PTS4, "bf16"), "f4x4_split_bf16x3": (4, PTS4, "split_bf16x3"),
-          "f4x4_split_bf16x6": (4, PTS4, "split_bf16x6"),
-          "f6x6_split_bf16x6": (6, PTS6, "split_bf16x6")}
+# contraction dtypes of the layer stacks (FP32 SIMT, then the tcgen05 forms)
+STACK_DTYPES = ("f32", "bf16", "fp16", "split_bf16x3", "split_bf16x6")
+
+
+def _stack_key(m, dt):
+    return "f%dx%d" % (m, m) + ("" if dt == "f32" else "_" + dt)
+
+
+# the layer stacks of one step: key -> (m, points, contraction dtype); the
+# timed stacks run the c-form points (the kernels' work does not depend on
+# the point values), the FP64 errors are stated for both point families
+STACKS = {_stack_key(m, dt): (m, POINTSETS[m]["c_form"], dt)
+          for m in (4, 6) for dt in STACK_DTYPES}
 # 16-bit operand parts of each tensor-core dtype
 TC_PARTS = {"bf16": 1, "fp16": 1, "split_bf16x3": 2, "split_bf16x6": 3}
 # surrogate training: sweep labels of random instances of the sweep's sizes
@@ -251,6 +275,15 @@ def run_ours(args, rank, world, local_rank):
     layers = inputs.VGG16_LAYERS
     N = inputs.VGG_BATCH
     stream = torch.cuda.current_stream()
+    gpu_id = str(local_rank)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+
+    # measured arithmetic peaks of the FP32 and FP64 pipes: the denominators
+    # of every ALU roofline below
+    pipe = measure_pipe_peaks(wino, gpu_id)
 
     # inputs resident in HBM (seeded per rank), outputs preallocated
     X, Wt = [], []
@@ -289,18 +322,9 @@ def run_ours(args, rank, world, local_rank):
     t_train = time.perf_counter() - t0
     guided = wino.GuidedSearch(model, sizes, masks, cg, inputs.SWEEP_TRIALS, seed=rank)
 
-    # FP64 error of every stack (stated beside the throughput; untimed)
-    for key in STACKS:
-        stack(key)
-    torch.cuda.synchronize()
-    fp64 = {key: [] for key in STACKS}
-    for li in range(len(layers)):
-        y64 = torch.empty(Y["f4x4"][li].shape, dtype=torch.float64, device=dev)
-        wino.wino_direct_conv_f64(X[li], Wt[li], y64, 1)
-        for key in STACKS:
-            se, sr, me, mr = wino.wino_error_stats(Y[key][li], y64)
-            fp64[key].append({"rel_l1": se / sr, "max_rel_inf": me / mr})
-        del y64
+    # FP64 error of every (m, point family, contraction dtype) on every VGG16
+    # stage (stated beside the throughput; untimed)
+    fp64 = layer_errors(wino, X, Wt, layers, N, dev)
     torch.cuda.synchronize()
 
     # warm-up (the first calls also run the layer and sweep autotuners)
@@ -319,13 +343,10 @@ def run_ours(args, rank, world, local_rank):
              "fused_layer", "sweep_eval", "sweep_prepare", "tc_gemm", "tc_transform")
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STACKS) + 1)]
           for _ in range(args.steps)]
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
     wall = {"sweep": 0.0, "plan": 0.0, "guided": 0.0, "step": 0.0}
     guided_res = []
-    gpu_id = str(local_rank)
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
     clocks = ClockSampler(gpu_id)
     if world > 1:
         torch.distributed.barrier()
@@ -348,7 +369,9 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         sweep()
         t1 = time.perf_counter()
+        pev[s][0].record(stream)
         plan.run(stream)
+        pev[s][1].record(stream)
         t2 = time.perf_counter()
         guided_res.append(guided.run())
         torch.cuda.synchronize()
@@ -365,11 +388,14 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     tk = {key: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / 1e3
           for i, key in enumerate(STACKS)}
-    times = [tk[k] for k in STACKS] + [wall[k] for k in ("sweep", "plan", "guided", "step")]
+    t_plan = sum(a.elapsed_time(b) for a, b in pev) / 1e3
+    times = ([tk[k] for k in STACKS] + [wall[k] for k in ("sweep", "plan", "guided", "step")] +
+             [t_plan])
     times = reduce_max(times, world)
     for i, k in enumerate(STACKS):
         tk[k] = times[i]
-    wall = dict(zip(("sweep", "plan", "guided", "step"), times[len(STACKS):]))
+    wall = dict(zip(("sweep", "plan", "guided", "step"), times[len(STACKS):len(STACKS) + 4]))
+    t_plan = times[-1]
     fl = direct_flops(layers, N)
     tflops = {k: world * fl * args.steps / tk[k] / 1e12 for k in STACKS}
     n_inst = 503808
@@ -388,12 +414,11 @@ def run_ours(args, rank, world, local_rank):
     # pipelined as a caller of the API would: the stages enter in the order
     # E2E_ORDER, stage l's batch as E2E_CHUNKS[l] sub-batches (wino_conv2d on a
     # batch slice computes the same outputs); a sub-batch's input is copied in
-    # on one stream, it runs on a
-    # second once that input has landed, and its output is copied out on a
-    # third once computed, so the host transfers (the bound: ~200 GB/s each
-    # way) overlap compute and each other from the first sub-batch on.  Timed
-    # from the first copy-in to the last copy-out of each step, the device
-    # idle in between steps.
+    # on one stream, it runs on a second once that input has landed, and its
+    # output is copied out on a third once computed, so the host transfers
+    # (the bound: ~200 GB/s each way) overlap compute and each other from the
+    # first sub-batch on.  Timed from the first copy-in to the last copy-out
+    # of each step, the device idle in between steps.
     xh = [x.cpu().pin_memory() for x in X]
     yh = [torch.empty(y.shape, dtype=y.dtype).pin_memory() for y in Y["f4x4"]]
     h2d = sum(x.numel() * 4 for x in X)
@@ -431,16 +456,17 @@ def run_ours(args, rank, world, local_rank):
             te2e += t_a.elapsed_time(t_b) / 1e3
     ve2e = world * fl * args.steps / te2e / 1e12
 
-    # rooflines: the dominant kernel of the step, and each main kernel
+    # rooflines: each main kernel's algorithmic work / its CUDA-event time
+    ctx = RoofCtx(wino, layers, N, args.steps, peaks, peak_src, pipe)
     roofs = {}
     for k, (ms, n) in prof.items():
         if n:
-            r = kernel_roofline(k, ms, n, args.steps, layers, N, peaks, peak_src)
+            r = kernel_roofline(k, ms, n, ctx)
             if r:
                 roofs[k] = r
-    dom = max(roofs, key=lambda k: prof[k][0])
+    roofs["sweep_plan"] = plan_roofline(t_plan, args.steps, ctx)
     comparison = paper_comparison(wino, inputs, ex, cg, masks, sizes)
-    orders = order_sweeps(wino, inputs, cg, sizes, masks, rank)
+    orders = order_sweeps(wino, inputs, cg, sizes, masks, rank, pipe)
     plan_info = plan.info()
     plan.close()
     guided.close()
@@ -456,23 +482,28 @@ def run_ours(args, rank, world, local_rank):
         "config": {
             "workload": "VGG16 3x3 layer stack (C=64..512, H=224..14), N=32/GPU, FP32 Winograd "
                         "F(4x4,3x3) [value]; per step also the F(6x6,3x3) FP32 stack, the "
-                        "BF16, split-BF16x3 and split-BF16x6 tensor-core F(4x4) stacks, the "
-                        "split-BF16x6 F(6x6) stack, the full point sweep "
-                        "(503808 instances x 1000 trials) per-size and as one persistent graph "
-                        "launch, and the surrogate-guided search of the same grid",
-            "points_f4x4": "{0,+-c,+-1/c,inf} c=1.622",
-            "points_f6x6": "{0,+-c,+-1/c,-d,d,inf} c=2 d=1.003", "global_batch": N * world,
+                        "BF16, FP16, split-BF16x3 and split-BF16x6 tensor-core stacks of both "
+                        "sizes, the full point sweep (503808 instances x 1000 trials) "
+                        "per-size and as one persistent graph launch, and the "
+                        "surrogate-guided search of the same grid",
+            "points": {"f%dx%d" % (m, m): {k: [float(v) for v in p] for k, p in fam.items()}
+                       for m, fam in POINTSETS.items()},
+            "timed_points": "c_form (the paper's proposed sets, Table 8 n = 6 and n = 8)",
+            "global_batch": N * world,
             "parallelism": "dp%d" % world if world > 1 else "single",
             "l2": "256 MB flush between steps (untimed); each layer input > L2 except the "
                   "28x28/14x14 stages"},
-        "fp64_error": {k: {"rel_l1_per_layer": [r["rel_l1"] for r in fp64[k]],
-                           "max_rel_inf": max(r["max_rel_inf"] for r in fp64[k])} for k in STACKS},
+        "roofline": roofs["fused_layer"],
+        "rooflines": roofs,
+        "pipe_peaks": pipe,
+        "fp64_error": fp64,
         "stacks": {k: {"value": tflops[k], "unit": "TFLOP/s",
                        "ms_per_step": 1e3 * tk[k] / args.steps} for k in STACKS},
         "sweep": {"value": vsw, "unit": "evals/s", "instances": n_inst, "trials": 1000,
                   "ms_per_step": 1e3 * wall["sweep"] / args.steps, "path": "per-size kernels"},
         "sweep_plan": {"value": vplan, "unit": "evals/s",
                        "ms_per_step": 1e3 * wall["plan"] / args.steps,
+                       "graph_ms_per_step": 1e3 * t_plan / args.steps,
                        "mode": {1: "persistent", 2: "persistent3", 3: "per_size"}.get(
                            plan_info["mode"], plan_info["mode"]),
                        "grid": plan_info["grid"], "work_items": plan_info["items"]},
@@ -482,14 +513,14 @@ def run_ours(args, rank, world, local_rank):
                    "evaluated_instances": g_last["evaluated"], "fallback_rows": g_last["fallback_rows"],
                    "rows": g_last["rows"], "max_best_err_ratio_vs_exhaustive": ratio,
                    "median_best_err_ratio_vs_exhaustive": ratio_med,
+                   "rows_above_1.01x_exhaustive": int((ratios > 1.01).sum()),
                    "best_rank_in_exhaustive_row": {"median": float(np.median(ranks)),
                                                     "p90": float(np.percentile(ranks, 90)),
+                                                    "max": int(ranks.max()),
                                                     "of": int(cg.size)},
                    "phase_ms": g_last["phase_ms"],
                    "training": {"samples": int(ys.numel()), "label_s": t_label,
                                 "train_s": t_train, "epochs": SURROGATE_EPOCHS, "batch": 4096}},
-        "roofline": roofs[dom],
-        "rooflines": roofs,
         "e2e": {"value": ve2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "how": "F(4x4) FP32 stack via wino_conv2d from pinned host buffers; the "
@@ -504,16 +535,98 @@ def run_ours(args, rank, world, local_rank):
         "sweep_orders": orders,
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, dt, nth = oracle_layer_sample(layers)
-        sw_rate, sw_dt, sw_nth, sw_n = oracle_sweep_sample(stride=4)
-        line["cpu_baseline"] = {
-            "value": v, "unit": "TFLOP/s", "cores": nth, "kind": "oracle",
-            "sample": "VGG16 5-layer F(4x4,3x3) stack on %d of the 32 images, one (layer, "
-                      "image) per thread, %.1f s" % (ORACLE_IMAGES, dt),
-            "sweep": {"value": sw_rate, "unit": "evals/s", "cores": sw_nth,
-                      "sample": "every 4th c of the 4096-value grid, all sizes and subsets, "
-                                "1000 trials (%d instances, %.1f s)" % (sw_n, sw_dt)}}
+        line["cpu_baseline"] = cpu_baseline(layers)
     print(json.dumps(line), flush=True)
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo) and core count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                name = ln.split(":", 1)[1].strip()
+                if ln.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"model": name or "unknown", "nproc": os.cpu_count()}
+
+
+def cpu_baseline(layers):
+    """The oracle timed on the host cores on bounded samples of the step's
+    workloads: the F(4x4) layer stack on 4 of the 32 images (all cores), the
+    sweep on every 4th c (all cores) and on every 64th c (one core)."""
+    v, dt, nth = oracle_layer_sample(layers)
+    sw_rate, sw_dt, sw_nth, sw_n = oracle_sweep_sample(stride=4)
+    s1_rate, s1_dt, s1_nth, s1_n = oracle_sweep_sample(stride=64, n_threads=1)
+    return {
+        "value": v, "unit": "TFLOP/s", "cores": nth, "kind": "oracle", "cpu": cpu_model(),
+        "sample": "VGG16 5-layer F(4x4,3x3) stack on %d of the 32 images, one (layer, "
+                  "image) per thread, %.1f s" % (ORACLE_IMAGES, dt),
+        "sweep": {"value": sw_rate, "unit": "evals/s", "cores": sw_nth,
+                  "sample": "every 4th c of the 4096-value grid, all sizes and subsets, "
+                            "1000 trials (%d instances, %.1f s)" % (sw_n, sw_dt)},
+        "sweep_1core": {"value": s1_rate, "unit": "evals/s", "cores": s1_nth,
+                        "sample": "every 64th c of the 4096-value grid, all sizes and subsets, "
+                                  "1000 trials (%d instances, %.1f s)" % (s1_n, s1_dt)}}
+
+
+# launches of the pipe probes (about 60-100 ms each on a GB300)
+PIPE_ITERS = {"fp32": 1 << 20, "fp32x2": 1 << 19, "fp64": 1 << 14}
+
+
+def measure_pipe_peaks(wino, gpu_id, reps=3):
+    """Best of `reps` launches of the library's FMA-throughput probe per pipe
+    (wino_pipe_peak), with the SM clock sampled meanwhile; the FP32 peak is
+    the larger of the scalar and packed forms."""
+    for kind, iters in PIPE_ITERS.items():
+        wino.wino_pipe_peak(kind, max(1, iters // 64))  # warm-up
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    out = {}
+    for kind, iters in PIPE_ITERS.items():
+        runs = [wino.wino_pipe_peak(kind, iters) for _ in range(reps)]
+        out[kind] = {"tflops": max(r[0] for r in runs), "ms": min(r[1] for r in runs),
+                     "iters": iters}
+    out["clocks"] = clocks.stop()
+    out["fp32_peak_tflops"] = max(out["fp32"]["tflops"], out["fp32x2"]["tflops"])
+    out["fp64_peak_tflops"] = out["fp64"]["tflops"]
+    out["how"] = ("wino_pipe_peak: 4 x 152 CTAs of 256 threads, 16 independent register "
+                  "FMA chains per thread, best of %d launches (CUDA events)" % reps)
+    return out
+
+
+def layer_errors(wino, X, Wt, layers, N, dev):
+    """Relative L1 error (and max error / max |y|) against the FP64 direct
+    correlation of every (m, point family, contraction dtype) per VGG16
+    stage: {f4x4: {c_form: {f32: {...}}}}."""
+    import torch
+    out = {}
+    for li, (C, H) in enumerate(layers):
+        y64 = torch.empty((N, C, H, H), dtype=torch.float64, device=dev)
+        wino.wino_direct_conv_f64(X[li], Wt[li], y64, 1)
+        yt = torch.empty((N, C, H, H), device=dev)
+        for m, fam in POINTSETS.items():
+            for pname, pts in fam.items():
+                for dt in STACK_DTYPES:
+                    wino.wino_conv2d(X[li], Wt[li], yt, pts, m, 3, 1, dt)
+                    se, sr, me, mr = wino.wino_error_stats(yt, y64)
+                    d = out.setdefault("f%dx%d" % (m, m), {}).setdefault(pname, {}).setdefault(
+                        dt, {"rel_l1_per_layer": [], "max_rel_inf": 0.0})
+                    d["rel_l1_per_layer"].append(se / sr)
+                    d["max_rel_inf"] = max(d["max_rel_inf"], me / mr)
+        del y64, yt
+    return out
 
 
 def paper_comparison(wino, inputs, ex, cg, masks, sizes):
@@ -586,7 +699,7 @@ def order_fp64_ops(dim, m, r):
     return a * r * dot(r) + a * a * dot(r) + 2 * a * a * dot(a) + m * a * dot(a) + m * m * dot(a)
 
 
-def order_sweeps(wino, inputs, cg, sizes, masks, rank):
+def order_sweeps(wino, inputs, cg, sizes, masks, rank, pipe):
     """The full sweep grid in the two Huffman orders (Sec. 5), untimed by the
     step: wall time, kernel time and each kernel's bound -- the shared-memory
     pipe (128 B per SM per clock) for the FP32 form, the FP64 issue rate for
@@ -600,8 +713,9 @@ def order_sweeps(wino, inputs, cg, sizes, masks, rank):
         work["huffman"] += 4.0 * k * order_smem_ops(*size[:3])
         work["huffman_mixed"] += 1.0 * k * order_fp64_ops(*size[:3])
     import torch
-    smem_peak = SMS * 128 * SM_MAX_MHZ * 1e6 / 1e9
-    fp64_peak = 1.25e3 / 2
+    sm_mhz = pipe["clocks"].get("sm_mhz") or SM_MAX_MHZ
+    smem_peak = SMS * 128 * sm_mhz * 1e6 / 1e9
+    fp64_peak = pipe["fp64_peak_tflops"] * 1e3 / 2  # Gop/s of separate multiplies or adds
     for order in ("huffman", "huffman_mixed"):
         wino.wino_error_sweep(cg[:64], sizes, masks, 100, seed=rank, order=order)  # warm-up
         torch.cuda.synchronize()
@@ -616,14 +730,15 @@ def order_sweeps(wino, inputs, cg, sizes, masks, rank):
             ach = work[order] / sec / 1e9
             roof = {"bound": "smem", "unit": "GB/s", "achieved": ach, "peak": smem_peak,
                     "frac": ach / smem_peak, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 128 B/clock x 2070 MHz",
+                    "peak_source": "derived: 152 SMs x 128 B/clock x %.0f MHz (the SM clock "
+                                   "sampled during the pipe probes)" % sm_mhz,
                     "work": "4 B x (4n - 2) value accesses per n-term dot product"}
         else:
             ach = work[order] / sec / 1e9
             roof = {"bound": "fp64", "unit": "Gop/s", "achieved": ach, "peak": fp64_peak,
                     "frac": ach / fp64_peak, "traffic": None,
-                    "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA = 2), halved for "
-                                   "separate multiplies and adds",
+                    "peak_source": "measured FP64 FMA pipe probe (wino_pipe_peak), halved "
+                                   "for separate multiplies and adds (of measured)",
                     "work": "2n - 1 FP64 multiplies and adds per n-term dot product"}
         out[order] = {"value": n_inst / dt, "unit": "evals/s", "wall_ms": 1e3 * dt,
                       "kernel_ms": ms, "launches": n, "instances": n_inst,
@@ -636,50 +751,128 @@ CD_SEARCH = [(1, 9, 0x7F), (1, 10, 0xFF), (2, 7, 0x4F), (2, 8, 0x5F), (2, 9, 0x7
              (2, 10, 0xFF)]
 
 
-def fp32_peak_tflops():
-    return SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-
-
 def _tiles(m, H, N):
     th = (H + m - 1) // m
     return N * th * th
 
 
-def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
-    """Algorithmic work of one launch of `kernel` (averaged over the launches
-    of one step) / its mean CUDA-event duration, against the kernel's bound."""
-    sec = ms / 1e3 / n
-    per_step = n / steps
-    fp32 = {"bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak_tflops(),
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    hbm = {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-           "peak_source": "%s copy bandwidth (of %s)" % (peak_src, peak_src)}
+class RoofCtx:
+    """What the roofline helpers need: the library (for the transform
+    matrices' non-zeros), the step's layers, and the peaks (HBM from the
+    driver's measurement, FP32 / FP64 from the pipe probes)."""
+
+    def __init__(self, wino, layers, N, steps, peaks, peak_src, pipe):
+        self.wino, self.layers, self.N, self.steps = wino, layers, N, steps
+        self.pipe = pipe
+        sm = pipe["clocks"].get("sm_mhz")
+        clk = (" at median SM clock %.0f MHz" % sm) if sm else ""
+        self.fp32 = {"bound": "alu", "unit": "TFLOP/s", "peak": pipe["fp32_peak_tflops"],
+                     "peak_source": "measured: FP32 FMA pipe probe (wino_pipe_peak, best of "
+                                    "fma.rn.f32 / fma.rn.f32x2)%s (of measured)" % clk}
+        self.fp64 = {"bound": "alu", "unit": "TFLOP/s", "peak": pipe["fp64_peak_tflops"],
+                     "peak_source": "measured: FP64 FMA pipe probe (wino_pipe_peak, "
+                                    "fma.rn.f64)%s (of measured)" % clk}
+        self.hbm = {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                    "peak_source": "copy bandwidth (of %s)" % peak_src}
+
+    def nnz_at(self, m):
+        """Non-zero entries of the FP32 A^T of the timed F(m x m, 3 x 3) points."""
+        AT, _, _ = self.wino.wino_make_matrices(POINTSETS[m]["c_form"], m, 3)
+        return int(np.count_nonzero(AT.astype(np.float32)))
+
+    def stacks(self, kind):
+        """(m, dtype) of the timed stacks that run `kind` ('f32' or 'tc')."""
+        return [(m, dt) for m, _, dt in STACKS.values() if (dt == "f32") == (kind == "f32")]
+
+
+def fp32_layer_work(ctx, m, C, H):
+    """GEMM + output-transform flops of one FP32 layer launch (K = C):
+    2 alpha^2 T C K for the contraction, 2 nnz(A^T) (alpha + m) per
+    (tile, output channel) for A^T M A."""
+    a = m + 2
+    T = _tiles(m, H, ctx.N)
+    return 2.0 * a * a * T * C * C + 2.0 * ctx.nnz_at(m) * (a + m) * T * C
+
+
+def fp32_layer_bytes(ctx, m, C, H):
+    """U read (alpha^2 T C floats), V read (alpha^2 C K), y written."""
+    a = m + 2
+    T = _tiles(m, H, ctx.N)
+    return 4.0 * (a * a * T * C + a * a * C * C + ctx.N * C * H * H)
+
+
+def tc_gemm_bytes(ctx, m, dt, C, H):
+    """Every 16-bit part of U [F][Tp][Cp] and V [F][K][Cp] read once, M [F][K][T]
+    written once in FP32 (K = C)."""
+    F = (m + 2) ** 2
+    T = _tiles(m, H, ctx.N)
+    Tp = (T + 127) // 128 * 128
+    Cp = (C + 63) // 64 * 64
+    return F * (2.0 * TC_PARTS[dt] * (Tp * Cp + C * Cp) + 4.0 * T * C)
+
+
+def tc_transform_bytes(ctx, m, dt, C, H):
+    """The quantising transforms: x read, the 16-bit parts of U written; w
+    read twice (maxima, then quantisation) and the parts of V written."""
+    F = (m + 2) ** 2
+    T = _tiles(m, H, ctx.N)
+    Tp = (T + 127) // 128 * 128
+    Cp = (C + 63) // 64 * 64
+    p = TC_PARTS[dt]
+    return 4.0 * ctx.N * C * H * H + 2.0 * p * F * Tp * Cp + 2 * 4.0 * 9 * C * C + 2.0 * p * F * C * Cp
+
+
+def kernel_roofline(kernel, ms, n, ctx):
+    """Algorithmic work of the step's launches of `kernel` / their summed
+    CUDA-event time (= mean work per launch / mean launch time), against the
+    kernel's bound."""
+    per_step = n / ctx.steps
+    sec = ms / 1e3 / ctx.steps  # event time per step
+    L = ctx.layers
     work = None
-    if kernel == "fused_layer":  # FP32 stacks F(4x4) and F(6x6): GEMM flops per launch
-        w = [2.0 * (m + 2) ** 2 * _tiles(m, H, N) * C * C for m in (4, 6) for C, H in layers]
-        work, base = sum(w) / len(w), fp32
-    elif kernel == "input_transform":  # split variant: read x, write U (FP32 stacks)
-        w = [4.0 * (N * C * H * H + (m + 2) ** 2 * C * _tiles(m, H, N))
-             for m in (4, 6) for C, H in layers]
-        work, base = sum(w) / len(w), hbm
+    if kernel == "fused_layer":  # FP32 stacks: GEMM + fused output transform
+        work, base = sum(fp32_layer_work(ctx, m, C, H) for m, _ in ctx.stacks("f32")
+                         for C, H in L), ctx.fp32
+    elif kernel == "input_transform":  # FP32 stacks: read x, write U
+        work = sum(4.0 * (ctx.N * C * H * H + (m + 2) ** 2 * C * _tiles(m, H, ctx.N))
+                   for m, _ in ctx.stacks("f32") for C, H in L)
+        base = ctx.hbm
     elif kernel == "tc_gemm":
-        # BF16 and split-BF16x3 F(4x4) stacks.  Per frequency 2 T C K flops on
-        # 2 T C + 2 C K + 4 T K bytes: at most 171 flop/byte (C = K = 512),
-        # below the ridge of the measured peaks (~288), so every VGG stage is
-        # HBM-bound: the roofline counts U and V read (16-bit; hi and lo for
-        # the split form) and M written (FP32).
-        work, base = tc_bytes_per_launch(layers, N), hbm
-    elif kernel == "sweep_eval":  # per-size sweep kernels + the persistent launch
-        work = 2 * sweep_flops_total() / per_step
-        base = fp32
+        # per frequency 2 T C K flops on 2 T C + 2 C K + 4 T K bytes: at most
+        # 171 flop/byte (C = K = 512), below the ridge of the measured peaks
+        # (~288), so every VGG stage is HBM-bound
+        work = sum(tc_gemm_bytes(ctx, m, dt, C, H) for m, dt in ctx.stacks("tc") for C, H in L)
+        base = ctx.hbm
+    elif kernel == "tc_transform":
+        work = sum(tc_transform_bytes(ctx, m, dt, C, H) for m, dt in ctx.stacks("tc")
+                   for C, H in L)
+        base = ctx.hbm
+    elif kernel == "output_transform":  # tensor-core stacks: M read, y written
+        work = sum(4.0 * ((m + 2) ** 2 * _tiles(m, H, ctx.N) * C + ctx.N * C * H * H)
+                   for m, dt in ctx.stacks("tc") for C, H in L)
+        base = ctx.hbm
+    elif kernel == "sweep_eval":  # ONE full sweep per step, per-size kernels
+        work, base = sweep_flops_total(), ctx.fp32
     if work is None:
         return None
     scale = 1e9 if base["unit"] == "GB/s" else 1e12
     ach = work / sec / scale
     return dict(kernel=kernel, bound=base["bound"], achieved=ach, peak=base["peak"],
-                unit=base["unit"], frac=ach / base["peak"], traffic=kernel_traffic(kernel, layers, N),
-                peak_source=base["peak_source"], work_per_launch=work, launches_per_step=per_step,
-                mean_launch_ms=ms / n)
+                unit=base["unit"], frac=ach / base["peak"],
+                traffic=kernel_traffic(kernel, ctx, per_step),
+                peak_source=base["peak_source"], work_per_launch=work / per_step,
+                launches_per_step=per_step, mean_launch_ms=ms / n)
+
+
+def plan_roofline(t_plan, steps, ctx):
+    """The planned persistent sweep of the full grid (one graph replay per
+    step, timed with CUDA events on its stream): one sweep's flops / time."""
+    ach = sweep_flops_total() * steps / t_plan / 1e12
+    return dict(kernel="sweep_plan (graph: k_sweep_prepare + k_sweep_persistent)",
+                bound="alu", achieved=ach, peak=ctx.fp32["peak"], unit="TFLOP/s",
+                frac=ach / ctx.fp32["peak"], traffic=None, peak_source=ctx.fp32["peak_source"],
+                work_per_launch=sweep_flops_total(), launches_per_step=1.0,
+                mean_launch_ms=1e3 * t_plan / steps)
 
 
 # DRAM bytes (read + write) of one ncu capture of each kernel on a smaller
@@ -688,41 +881,27 @@ def kernel_roofline(kernel, ms, n, steps, layers, N, peaks, peak_src):
 # proportion to the bytes the launch must move).
 NCU_TRAFFIC = {
     # k_gemm_otx_cl F(4x4) cluster tile shape split5, C = K = 512, 28x28,
-    # N = 32: U read + y written
-    "fused_layer": (223.20e6, 36 * 1568 * 512 * 4 + 32 * 512 * 28 * 28 * 4),
+    # N = 32: U read + V read + y written
+    "fused_layer": (223.20e6, 36 * 1568 * 512 * 4 + 36 * 512 * 512 * 4
+                    + 32 * 512 * 28 * 28 * 4),
     # k_tc_gemm split-BF16x6, C = K = 64, 224x224, N = 8: three 16-bit parts
     # of U and V read, M written (FP32)
     "tc_gemm": (538.43e6, 36 * (2 * 3 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
 }
 
 
-def kernel_traffic(kernel, layers, N):
+def kernel_traffic(kernel, ctx, per_step):
     """Mean DRAM bytes per launch, scaled from the kernel's ncu capture, or
     None when no capture covers it."""
     if kernel not in NCU_TRAFFIC:
         return None
     meas, alg = NCU_TRAFFIC[kernel]
+    L = ctx.layers
     if kernel == "fused_layer":
-        b = [4.0 * ((m + 2) ** 2 * _tiles(m, H, N) * C + N * C * H * H)
-             for m in (4, 6) for C, H in layers]
-        return meas / alg * sum(b) / len(b)
-    return meas / alg * tc_bytes_per_launch(layers, N)
-
-
-def tc_bytes_per_launch(layers, N):
-    """Mean algorithmic bytes of one tcgen05 GEMM launch over the step's
-    tensor-core stacks: every 16-bit part of U [F][Tp][C] and V [F][K][C]
-    read once, M [F][K][T] written once in FP32."""
-    b = []
-    for m, _, dt in STACKS.values():
-        if dt not in TC_PARTS:
-            continue
-        F = (m + 2) ** 2
-        for C, H in layers:
-            T = _tiles(m, H, N)
-            Tp = (T + 127) // 128 * 128
-            b.append(F * (2.0 * TC_PARTS[dt] * (Tp * C + C * C) + 4.0 * T * C))
-    return sum(b) / len(b)
+        b = sum(fp32_layer_bytes(ctx, m, C, H) for m, _ in ctx.stacks("f32") for C, H in L)
+    else:
+        b = sum(tc_gemm_bytes(ctx, m, dt, C, H) for m, dt in ctx.stacks("tc") for C, H in L)
+    return meas / alg * b / per_step
 
 
 def sweep_flops_total():

@@ -131,6 +131,8 @@ int wino_direct_conv_f64(const void* x, const void* w, void* y64,
 /* Error statistics of an FP32 result against its FP64 reference, reduced on
  * the device in FP64 (warp shuffles): out4 (host, FP64) receives
  *   { sum |yhat - y|, sum |y|, max |yhat - y|, max |y| }.
+ * A NaN anywhere in yhat (or y) makes the sums and the matching maximum NaN
+ * (the maxima propagate NaN rather than skip it).
  * Synchronises `cuda_stream` because the result is a host array.          */
 int wino_error_stats(const void* yhat_f32, const void* y_f64, int64_t n,
                      double* out4, void* cuda_stream);
@@ -406,6 +408,22 @@ int wino_profile_read(const char* kernel, double* total_ms, int* launches);
 /* Number of kernels this library has launched in this process (all
  * devices); a diagnostic for counting launches inside a timed region.      */
 unsigned long long wino_kernel_launches(void);
+
+/* Measured arithmetic peak of one pipe of the current device, the
+ * denominator of the ALU-bound rooflines (the FP32 layer's contraction, the
+ * sweep, the FP64 reference).  The paper has no counterpart; it is a
+ * measurement aid.  One launch of blocks_per_sm x (SM count) CTAs of 256
+ * threads, each thread running 16 independent chains of `iters` fused
+ * multiply-adds on registers only:
+ *   WINO_PIPE_FP32    fma.rn.f32     (2 flops per lane and instruction)
+ *   WINO_PIPE_FP32X2  fma.rn.f32x2   (4 flops per lane and instruction)
+ *   WINO_PIPE_FP64    fma.rn.f64     (2 flops per lane and instruction)
+ * *tflops = flops / the launch's CUDA-event duration, *ms = that duration
+ * (host outputs).  Synchronises cuda_stream.  WINO_EINVAL for another kind,
+ * iters < 1, blocks_per_sm outside 1..8 or a NULL output.                 */
+enum { WINO_PIPE_FP32 = 0, WINO_PIPE_FP32X2 = 1, WINO_PIPE_FP64 = 2 };
+int wino_pipe_peak(int kind, int iters, int blocks_per_sm, double* tflops, double* ms,
+                   void* cuda_stream);
 
 /* Device-side failure detection.  Layer kernels that wait on hardware
  * completion (the tensor-core contraction's mbarrier, the FP32 layer's bulk

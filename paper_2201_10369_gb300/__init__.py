@@ -129,6 +129,8 @@ def _declare(L):
     L.wino_wait_probe.argtypes = [_i, ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p]
     L.wino_wait_probe.restype = _i
     L.wino_shutdown.restype = None
+    L.wino_pipe_peak.argtypes = [_i, _i, _i, _DP, _DP, _vp]
+    L.wino_pipe_peak.restype = _i
     for name in ("wino_make_matrices", "wino_conv1d", "wino_conv2d", "wino_set_workspace",
                  "wino_direct_conv_f64", "wino_error_stats", "wino_error_sweep"):
         getattr(L, name).restype = _i
@@ -183,7 +185,46 @@ def _ptr(t) -> int:
         raise ValueError("expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
+    import torch
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("tensor on cuda:%s, but the current device is cuda:%d"
+                         % (t.device.index, torch.cuda.current_device()))
     return t.data_ptr()
+
+
+def _want(name, t, dtype, shape=None, ndim=None):
+    """Checks a tensor argument's dtype and shape before any ABI call (the
+    library indexes device memory from the sizes alone, so a wrong dtype or
+    an undersized tensor would be read or written out of bounds)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s must be a torch tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError("%s must have %d dimensions, got shape %s" % (name, ndim, tuple(t.shape)))
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+
+
+def _check_layer(x, w, y, pts, m, r, pad, dim):
+    """Validates the arguments of a layer call (x, w, y FP32; shapes
+    x [N][C](H)[W], w [K][C](r)[r], y [N][K](Ho)[Wo]; m + r - 1 points)."""
+    import torch
+    if m < 1 or r < 1 or pad < 0:
+        raise ValueError("need m >= 1, r >= 1, pad >= 0")
+    if pts.ndim != 1 or pts.size != m + r - 1:
+        raise ValueError("need alpha = m + r - 1 = %d points, got %d" % (m + r - 1, pts.size))
+    _want("x", x, torch.float32, ndim=dim + 2)
+    N, C = x.shape[0], x.shape[1]
+    sp = tuple(x.shape[2:])
+    _want("w", w, torch.float32, ndim=dim + 2)
+    K = w.shape[0]
+    _want("w", w, torch.float32, shape=(K, C) + (r,) * dim)
+    out = tuple(v + 2 * pad - r + 1 for v in sp)
+    if min(out) < 1:
+        raise ValueError("kernel larger than the padded input")
+    _want("y", y, torch.float32, shape=(N, K) + out)
 
 
 def _stream(stream) -> int:
@@ -222,10 +263,11 @@ def _dtype(dtype) -> int:
 
 def wino_conv2d(x, w, y, points, m: int, r: int, pad: int = 1, dtype="f32", stream=None):
     """y[N][K][Ho][Wo] <- Winograd F(m x m, r x r) correlation of x with w."""
+    pts = _points(points)
+    _check_layer(x, w, y, pts, m, r, pad, 2)
     L = load()
     N, C, H, W = x.shape
     K = w.shape[0]
-    pts = _points(points)
     _check(L.wino_conv2d(_ptr(x), _ptr(w), _ptr(y), N, C, K, H, W, pad, pts.ctypes.data_as(_DP),
                          m, r, _dtype(dtype), _stream(stream)))
     return y
@@ -233,10 +275,11 @@ def wino_conv2d(x, w, y, points, m: int, r: int, pad: int = 1, dtype="f32", stre
 
 def wino_conv1d(x, w, y, points, m: int, r: int, pad: int = 1, dtype="f32", stream=None):
     """y[N][K][Lo] <- Winograd F(m, r) correlation of x[N][C][L] with w[K][C][r]."""
+    pts = _points(points)
+    _check_layer(x, w, y, pts, m, r, pad, 1)
     L = load()
     N, C, Ln = x.shape
     K = w.shape[0]
-    pts = _points(points)
     _check(L.wino_conv1d(_ptr(x), _ptr(w), _ptr(y), N, C, K, Ln, pad, pts.ctypes.data_as(_DP),
                          m, r, _dtype(dtype), _stream(stream)))
     return y
@@ -247,10 +290,11 @@ def wino_conv2d_f32_noalloc(x, w, y, points, m: int, r: int, pad: int = 1, strea
     cannot allocate (inside graph capture, under a framework that owns the
     memory pool).  Uses the library's fixed 16 MiB scratch array; see
     include/wino.h for the limits and the rule that overlapping calls race."""
+    pts = _points(points)
+    _check_layer(x, w, y, pts, m, r, pad, 2)
     L = load()
     N, C, H, W = x.shape
     K = w.shape[0]
-    pts = _points(points)
     _check(L.wino_conv2d_f32_noalloc(_ptr(x), _ptr(w), _ptr(y), N, C, K, H, W, pad,
                                      pts.ctypes.data_as(_DP), m, r, _stream(stream)))
     return y
@@ -272,13 +316,24 @@ def wino_set_workspace(buf=None, nbytes: int = 0):
 
 def wino_direct_conv_f64(x, w, y64, pad: int = 1, stream=None):
     """FP64 direct correlation (Eq. (1)); x, w FP32 CUDA tensors, y64 FP64."""
+    import torch
+    _want("x", x, torch.float32)
+    if x.dim() not in (3, 4):
+        raise ValueError("x must be [N][C][W] or [N][C][H][W]")
+    dim = x.dim() - 2
+    _want("w", w, torch.float32, ndim=x.dim())
+    r = w.shape[-1]
+    _want("w", w, torch.float32, shape=(w.shape[0], x.shape[1]) + (r,) * dim)
+    if pad < 0 or min(v + 2 * pad - r + 1 for v in x.shape[2:]) < 1:
+        raise ValueError("need pad >= 0 and a kernel no larger than the padded input")
+    _want("y64", y64, torch.float64,
+          shape=(x.shape[0], w.shape[0]) + tuple(v + 2 * pad - r + 1 for v in x.shape[2:]))
     L = load()
-    if x.dim() == 3:
+    if dim == 1:
         N, C, W = x.shape
-        H, dim, r = 1, 1, w.shape[2]
+        H = 1
     else:
         N, C, H, W = x.shape
-        dim, r = 2, w.shape[3]
     K = w.shape[0]
     _check(L.wino_direct_conv_f64(_ptr(x), _ptr(w), _ptr(y64), dim, N, C, K, H, W, pad, r,
                                   _stream(stream)))
@@ -287,6 +342,11 @@ def wino_direct_conv_f64(x, w, y64, pad: int = 1, stream=None):
 
 def wino_error_stats(yhat, y64, stream=None):
     """(sum|yhat-y|, sum|y|, max|yhat-y|, max|y|) reduced on the device."""
+    import torch
+    _want("yhat", yhat, torch.float32)
+    _want("y64", y64, torch.float64)
+    if yhat.numel() != y64.numel():
+        raise ValueError("yhat and y64 must hold the same number of elements")
     L = load()
     out = np.zeros(4)
     _check(L.wino_error_stats(_ptr(yhat), _ptr(y64), yhat.numel(), out.ctypes.data_as(_DP),
@@ -438,7 +498,17 @@ class Surrogate:
     def features(self, sizes, instances, stream=None):
         return instance_features(sizes, instances, stream)
 
+    @staticmethod
+    def _check_xy(X, y=None):
+        import torch
+        _want("X", X, torch.float32, ndim=2)
+        if X.shape[1] != 16:
+            raise ValueError("X must be [n][16] features")
+        if y is not None:
+            _want("y", y, torch.float32, shape=(X.shape[0],))
+
     def loss_grad(self, X, y, stream=None):
+        self._check_xy(X, y)
         g = np.zeros(MLP_PARAMS, dtype=np.float32)
         loss = ctypes.c_double(0.0)
         _check(self._L.wino_mlp_loss_grad(self._h, _ptr(X), _ptr(y), X.shape[0],
@@ -453,12 +523,14 @@ class Surrogate:
         self.set_params(p)
 
     def train(self, X, y, batch: int = 4096, epochs: int = 1, lr: float = 1e-3, stream=None):
+        self._check_xy(X, y)
         _check(self._L.wino_mlp_train(self._h, _ptr(X), _ptr(y), X.shape[0], batch, epochs, lr,
                                       _stream(stream)))
 
     def predict(self, X, stream=None):
         import torch
-        out = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        self._check_xy(X)
+        out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
         _check(self._L.wino_mlp_predict(self._h, _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
         return out
 
@@ -477,8 +549,11 @@ class Surrogate:
 def wino_topk_rows(vals, k: int, stream=None):
     """Indices (CUDA int32 [rows][k]) of the k smallest values of each row."""
     import torch
+    _want("vals", vals, torch.float32, ndim=2)
     rows, cols = vals.shape
-    idx = torch.empty((rows, k), dtype=torch.int32, device="cuda")
+    if not 1 <= k <= cols:
+        raise ValueError("need 1 <= k <= cols")
+    idx = torch.empty((rows, k), dtype=torch.int32, device=vals.device)
     _check(load().wino_topk_rows(_ptr(vals), rows, cols, k, _ptr(idx), _stream(stream)))
     return idx
 
@@ -803,6 +878,19 @@ def wino_wait_probe(polls: int) -> int:
     _check(load().wino_wait_probe(int(polls), ctypes.byref(ns),
                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return int(ns.value)
+
+
+WINO_PIPE_FP32, WINO_PIPE_FP32X2, WINO_PIPE_FP64 = 0, 1, 2
+PIPES = {"fp32": WINO_PIPE_FP32, "fp32x2": WINO_PIPE_FP32X2, "fp64": WINO_PIPE_FP64}
+
+
+def wino_pipe_peak(kind: str, iters: int, blocks_per_sm: int = 4, stream=None):
+    """(TFLOP/s, ms) of one launch of the library's FMA-throughput probe of
+    one pipe ('fp32', 'fp32x2' or 'fp64'); synchronises the stream."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().wino_pipe_peak(PIPES[kind], int(iters), int(blocks_per_sm), ctypes.byref(tf),
+                                 ctypes.byref(ms), _stream(stream)))
+    return tf.value, ms.value
 
 
 def wino_shutdown():

@@ -141,14 +141,8 @@ extern "C" int wino_conv2d_f32_noalloc(const void* x, const void* w, void* y, in
     set_error("x, w and y must be device pointers");
     return WINO_EINVAL;
   }
-  cudaDeviceProp prop;
-  int dev = 0;
-  WINO_CUDA_TRY(cudaGetDevice(&dev));
-  WINO_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
-  if (prop.major != 10 || prop.minor != 3) {
-    set_error("this library is built for sm_103 (GB300) only");
-    return WINO_EUNSUPPORTED;
-  }
+  // the device check is cached per device (no property query per call)
+  if (!wino_device_ok()) return WINO_EUNSUPPORTED;
   void* scratch = nullptr;
   int st = noalloc_scratch(&scratch);
   if (st != WINO_OK) return st;

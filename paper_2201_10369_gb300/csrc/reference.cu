@@ -107,13 +107,19 @@ struct Stats4 {
   double s_err, s_ref, m_err, m_ref;
 };
 
+// max that propagates NaN (fmax drops a NaN operand, which would let a NaN
+// output hide behind the largest finite error)
+__device__ __forceinline__ double nanmax(double a, double b) {
+  return (a != a) ? a : (b != b) ? b : fmax(a, b);
+}
+
 __device__ __forceinline__ Stats4 warp_reduce(Stats4 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     v.s_err += __shfl_down_sync(0xffffffffu, v.s_err, o);
     v.s_ref += __shfl_down_sync(0xffffffffu, v.s_ref, o);
-    v.m_err = fmax(v.m_err, __shfl_down_sync(0xffffffffu, v.m_err, o));
-    v.m_ref = fmax(v.m_ref, __shfl_down_sync(0xffffffffu, v.m_ref, o));
+    v.m_err = nanmax(v.m_err, __shfl_down_sync(0xffffffffu, v.m_err, o));
+    v.m_ref = nanmax(v.m_ref, __shfl_down_sync(0xffffffffu, v.m_ref, o));
   }
   return v;
 }
@@ -141,8 +147,8 @@ __global__ void k_error_stats_pass1(const float* __restrict__ yhat, const double
     const double e = fabs((double)yhat[i] - ref);
     v.s_err += e;
     v.s_ref += fabs(ref);
-    v.m_err = fmax(v.m_err, e);
-    v.m_ref = fmax(v.m_ref, fabs(ref));
+    v.m_err = nanmax(v.m_err, e);
+    v.m_ref = nanmax(v.m_ref, fabs(ref));
   }
   v = block_reduce(v);
   if (threadIdx.x == 0) partial[blockIdx.x] = v;
@@ -155,8 +161,8 @@ __global__ void k_error_stats_pass2(const Stats4* __restrict__ partial, int nb,
     const Stats4 p = partial[i];
     v.s_err += p.s_err;
     v.s_ref += p.s_ref;
-    v.m_err = fmax(v.m_err, p.m_err);
-    v.m_ref = fmax(v.m_ref, p.m_ref);
+    v.m_err = nanmax(v.m_err, p.m_err);
+    v.m_ref = nanmax(v.m_ref, p.m_ref);
   }
   v = block_reduce(v);
   if (threadIdx.x == 0) {

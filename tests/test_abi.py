@@ -122,3 +122,39 @@ def test_wait_probe_validation_on_host(wino):
     hdr = (pathlib.Path(__file__).resolve().parents[1] / "include" / "wino.h").read_text()
     m = re.search(r"#define WINO_WAIT_POLLS \(1 << (\d+)\)", hdr)
     assert m and 1 <= int(m.group(1)) <= 24
+
+
+def test_binding_validates_arguments_before_the_abi(lib):
+    """The Python wrappers check dtype, shapes and the point count before any
+    ABI call (the library indexes device memory from the sizes alone), so a
+    wrong argument raises ValueError and never reaches a kernel.  CPU
+    tensors: every check up to the device one runs here."""
+    import torch
+    pts4 = [0.0, 1.0, -1.0, math.inf]
+    x = torch.zeros((1, 8, 6, 6))
+    w = torch.zeros((16, 8, 3, 3))
+    y = torch.zeros((1, 16, 6, 6))
+    cases = [
+        (x.double(), w, y, pts4, "x must be torch.float32"),
+        (x, w.to(torch.bfloat16), y, pts4, "w must be torch.float32"),
+        (x, torch.zeros((16, 4, 3, 3)), y, pts4, "w must have shape"),
+        (x, w, torch.zeros((1, 16, 5, 6)), pts4, "y must have shape"),
+        (x, w, torch.zeros((1, 8, 6, 6)), pts4, "y must have shape"),
+        (x, w, y, pts4[:3], "need alpha"),
+        (x[0], w, y, pts4, "dimensions"),
+    ]
+    for xa, wa, ya, p, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            lib.wino_conv2d(xa, wa, ya, p, 2, 3, 1)
+    with pytest.raises(ValueError, match="need alpha"):
+        lib.wino_conv2d_f32_noalloc(x, w, y, pts4 + [2.0], 2, 3, 1)
+    with pytest.raises(ValueError, match="y must have shape"):
+        lib.wino_conv1d(torch.zeros((2, 8, 10)), torch.zeros((4, 8, 3)), torch.zeros((2, 4, 9)),
+                        pts4, 2, 3, 1)
+    with pytest.raises(ValueError, match="y64 must be torch.float64"):
+        lib.wino_direct_conv_f64(x, w, y, 1)
+    with pytest.raises(ValueError, match="same number"):
+        lib.wino_error_stats(y, torch.zeros(5, dtype=torch.float64))
+    # well-formed CPU tensors pass every check but the device one
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        lib.wino_conv2d(x, w, y, pts4, 2, 3, 1)

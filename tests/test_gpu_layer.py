@@ -197,6 +197,10 @@ def test_error_stats_vs_numpy(wino):
     want = (e.sum(), np.abs(y).sum(), e.max(), np.abs(y).max())
     for a, b in zip(got, want):
         assert a == pytest.approx(b, rel=1e-12)
+    # a NaN output is not hidden behind the largest finite error
+    yh[12345] = np.nan
+    got = wino.wino_error_stats(torch.from_numpy(yh).cuda(), torch.from_numpy(y).cuda())
+    assert np.isnan(got[0]) and np.isnan(got[2]) and got[3] == pytest.approx(want[3], rel=1e-12)
 
 
 def test_no_bounded_wait_gave_up(wino, monkeypatch):

@@ -3,13 +3,30 @@ split BF16x3 / split BF16x6 with per-frequency power-of-two scaling) against
 the oracle's emulation of the same rounding.
 
 Both sides round the same FP32 transform outputs to the same 16-bit
-operands and form exact products; only the FP32 accumulation order of the
-tensor cores differs from the oracle's sequential fmaf.  Bar: max |yGPU -
-yoracle| <= 2e-5 max |yoracle| (accumulation-order differences amplified by
-the output transform), and the relative L1 error against FP64 within 5% of
-the oracle's (split BF16x6: at most 5% above it -- its operands are exact to
-2^-24, so the accumulation order dominates its error, and the tensor cores'
-order may beat the oracle's sequential fmaf)."""
+operands and form exact products (16-bit x 16-bit products fit FP32).  They
+differ only in how the FP32 accumulator sums those products over the
+channels: the oracle adds them one after the other with fmaf, the tensor
+cores in their own order, with an adder whose rounding is not documented.
+The bar is derived from that (reading in the design notes):
+  - a sum of n exact terms p_i in FP32 errs by at most gamma_n(v) sum |p_i|,
+    gamma_n(v) = n v / (1 - n v), with v = 2^-24 for the oracle's
+    round-to-nearest and v = 2^-23 for the tensor cores (any rounding that
+    errs by at most one unit in the last place, truncation included);
+  - n = (products per channel) x C (+ 1 for split BF16x6, whose two
+    accumulators are added once at the end), and sum |p_i| <= 1.1 sum_c
+    |U_c| |V_c| (the parts of an operand sum in magnitude to at most
+    (1 + 2^-7) of it);
+  - the output transform A^T M A maps the difference of M through |A^T| .
+    |A| and rounds both sides' results, each by at most gamma_{2 alpha}(2^-24)
+    |A^T| |M| |A| <= gamma_{2 alpha} |A^T| S |A|, S = sum_c |U| |V|.
+So, per output: |y_gpu - y_oracle| <= (1.1 (gamma_n(2^-24) + gamma_n(2^-23))
++ 2 gamma_{2 alpha}(2^-24)) (|A^T| S |A|), with U, V and S computed here in
+FP64 from the FP64 matrices.  The relative L1 errors against FP64 then
+differ by at most sum(bound) / sum|y_fp64|.  Besides the derived bars: the
+BF16 / FP16 / split BF16x3 errors, dominated by the operand rounding both
+sides share, agree within 5%; and up to C = 128 the split BF16x6 error (its
+operands exact, so the accumulation dominates) is no more than 1.05x the
+sequential emulation's."""
 import math
 
 import numpy as np
@@ -22,6 +39,53 @@ pytestmark = pytest.mark.gpu
 PTS = {4: [0.0, -1 / 1.622, -1.622, 1.622, 1 / 1.622, math.inf],
        6: [0.0, -0.5, -2.0, 2.0, 0.5, -1.003, 1.003, math.inf],
        2: [0.0, -1.0, 1.0, math.inf]}
+
+
+PRODUCTS = {"bf16": 1, "fp16": 1, "split_bf16x3": 3, "split_bf16x6": 6}
+
+
+def _gamma(n, v):
+    return n * v / (1.0 - n * v)
+
+
+def _patches(x, m, pad):
+    """Input tiles d[n][ti][tj][c][alpha][alpha] (zero padding, ragged
+    tiles zero-filled), FP64."""
+    N, C, H, W = x.shape
+    a = m + 2
+    Ho, Wo = H + 2 * pad - 2, W + 2 * pad - 2
+    th, tw = -(-Ho // m), -(-Wo // m)
+    xp = np.zeros((N, C, th * m + 2, tw * m + 2))
+    xp[:, :, pad:pad + H, pad:pad + W] = x
+    d = np.empty((N, th, tw, C, a, a))
+    for i in range(th):
+        for j in range(tw):
+            d[:, i, j] = xp[:, :, i * m:i * m + a, j * m:j * m + a]
+    return d, th, tw
+
+
+def tc_magnitudes(orc, x, w, pts, m):
+    """|A^T| S |A| per output, S[f][t][k] = sum_c |U[f][t][c]| |V[f][c][k]|,
+    U = B^T d B and V = G g G^T in FP64 from the FP64 matrices; shaped like
+    y [N][K][Ho][Wo] (pad 1, r = 3)."""
+    AT, G, BT = orc.make_matrices(pts, m, 3)
+    N, C, H, W = x.shape
+    K = w.shape[0]
+    a = m + 2
+    d, th, tw = _patches(x.astype(np.float64), m, 1)
+    U = np.einsum("il,ntsclq,jq->ijntsc", BT, d, BT).reshape(a * a, N * th * tw, C)
+    V = np.einsum("ip,kcpq,jq->ijck", G, w.astype(np.float64), G).reshape(a * a, C, K)
+    S = np.matmul(np.abs(U), np.abs(V)).reshape(a, a, N, th, tw, K)
+    Y = np.einsum("ai,ijntsk,bj->nktasb", np.abs(AT), S, np.abs(AT))
+    return Y.reshape(N, K, th * m, tw * m)[:, :, :H, :W]
+
+
+def tc_parity_bound(orc, x, w, pts, m, dtype):
+    """Per-output bound on |y_gpu - y_oracle| (see the module docstring)."""
+    a = m + 2
+    n = PRODUCTS[dtype] * x.shape[1] + (1 if dtype == "split_bf16x6" else 0)
+    f = 1.1 * (_gamma(n, 2.0 ** -24) + _gamma(n, 2.0 ** -23)) + 2 * _gamma(2 * a, 2.0 ** -24)
+    return f * tc_magnitudes(orc, x, w, pts, m)
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp16", "split_bf16x3", "split_bf16x6"])
@@ -41,19 +105,20 @@ def test_tc_layer_vs_oracle_emulation(wino, orc, dtype, m, shape):
     yg = y.cpu().numpy()
     yo = orc.wino_layer(x, w, 2, 1, PTS[m], m, 3, dtype)
     assert np.all(np.isfinite(yg))
-    scale = np.abs(yo).max()
-    # the tensor cores accumulate in their own order: the difference grows
-    # with the contraction length (C = 300: 8e-5 of the scale measured)
-    assert np.abs(yg - yo).max() <= 2e-5 * max(1.0, C / 64) * scale
+    bound = tc_parity_bound(orc, x, w, PTS[m], m, dtype)
+    diff = np.abs(yg.astype(np.float64) - yo)
+    assert np.all(diff <= bound), float((diff / bound).max())
     ref = orc.direct_f64(x, w, 2, 1, 3)
-    eg = np.abs(yg - ref).sum() / np.abs(ref).sum()
-    eo = np.abs(yo.astype(np.float64) - ref).sum() / np.abs(ref).sum()
+    sref = np.abs(ref).sum()
+    eg = np.abs(yg - ref).sum() / sref
+    eo = np.abs(yo.astype(np.float64) - ref).sum() / sref
+    assert abs(eg - eo) <= bound.sum() / sref, (eg, eo, bound.sum() / sref)
     if dtype == "split_bf16x6":
         # operands exact to 2^-24: the accumulation is the dominant error
-        # term.  Up to C = 128 the tensor cores' is as good as sequential
-        # FP32 or better; over long contractions it is not (C = 300 at
-        # F(2x2,3x3): 1.5x measured)
-        assert eg <= (1.05 if C <= 128 else 2.0) * eo, (eg, eo)
+        # term, and over short contractions the tensor cores' is as good as
+        # sequential FP32
+        if C <= 128:
+            assert eg <= 1.05 * eo, (eg, eo)
     else:
         assert abs(eg / eo - 1) < 0.05, (eg, eo)
 

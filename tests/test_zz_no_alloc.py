@@ -2,10 +2,10 @@
 device memory (code running under CUDA graph capture, plug-ins whose host
 framework owns the memory pool).  It runs the same fused kernel as
 wino_conv2d with its scratch in a fixed array inside the library, so its
-output must equal wino_conv2d's bit for bit -- the tolerance the other layer
-tests use -- on consecutive calls that reuse that array with different
-shapes.  Collected last (file name) so a failure here leaves every other
-test already run."""
+output must equal the oracle's FP32 Winograd layer bit for bit -- the bar the
+other FP32 layer tests use -- and wino_conv2d's, on consecutive calls that
+reuse that array with different shapes.  Collected last (file name) so a
+failure here leaves every other test already run."""
 import ctypes
 import math
 
@@ -30,7 +30,7 @@ def _noalloc(wino, x, w, y, pts, m, pad):
     return st
 
 
-def test_noalloc_matches_conv2d_on_consecutive_calls(wino):
+def test_noalloc_matches_oracle_and_conv2d_on_consecutive_calls(wino, orc):
     import torch
     c = 1.622
     cases = [((2, 24, 64, 30, 21, 1), 4, [0.0, -1 / c, -c, c, 1 / c, math.inf]),
@@ -40,12 +40,14 @@ def test_noalloc_matches_conv2d_on_consecutive_calls(wino):
         x, w = inputs.layer_uniform(N, C, K, H, W, seed=N + C + K)
         xt, wt = torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda()
         shape = (N, K, H + 2 * pad - 2, W + 2 * pad - 2)
+        yo = orc.wino_layer(x, w, 2, pad, pts, m, 3)
         ref = torch.full(shape, float("nan"), device="cuda")
         wino.wino_conv2d(xt, wt, ref, pts, m, 3, pad)
         for _ in range(2):
             y = torch.full(shape, float("nan"), device="cuda")
             assert _noalloc(wino, xt, wt, y, pts, m, pad) == wino.WINO_OK, wino.wino_last_error()
             torch.cuda.synchronize()
+            assert np.array_equal(y.cpu().numpy(), yo)
             assert torch.equal(y, ref)
 
 
