@@ -466,6 +466,7 @@ def run_ours(args, rank, world, local_rank):
                 roofs[k] = r
     roofs["sweep_plan"] = plan_roofline(t_plan, args.steps, ctx)
     comparison = paper_comparison(wino, inputs, ex, cg, masks, sizes)
+    patterns = subset_tables(wino, inputs)
     orders = order_sweeps(wino, inputs, cg, sizes, masks, rank, pipe)
     plan_info = plan.info()
     plan.close()
@@ -532,6 +533,7 @@ def run_ours(args, rank, world, local_rank):
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk,
         "paper_comparison": comparison,
+        "subset_patterns": patterns,
         "sweep_orders": orders,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -675,6 +677,60 @@ def paper_comparison(wino, inputs, ex, cg, masks, sizes):
                             "err": float(e[i, k]),
                             "improvement_pct": 100.0 * (row["barabasz"] - e[i, k]) / row["barabasz"]}
     return out
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def _golden(name):
+    """Rows of a '|'-separated golden file of the paper's printed values."""
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([v.strip() for v in line.split("|")])
+    return rows
+
+
+def subset_tables(wino, inputs):
+    """Sec. 6.2 from this run's GPU sweep (untimed), c > 1 of the 4096-value
+    grid, 1000 trials: Tables 2-4 (per base and subset, the c of least error
+    and that error, beside the printed c) and Tables 5-6 (per base, the
+    measured pattern -- the subset of least error -- and its win fraction,
+    beside the printed pattern), through wino_subset_pattern."""
+    cg = inputs.c_grid()
+    cache = {}
+
+    def sweep(dim, m, d, masks):
+        key = (dim, m, d)
+        if key not in cache:
+            ms = np.array(sorted({b | s_ for b in (0x00, 0x20, 0x40, 0x60, 0x80) for s_ in range(16)
+                                  if bin(b | s_).count("1") == m}), dtype=np.uint8)
+            cache[key] = (ms, wino.wino_error_sweep(cg, [(dim, m, 3, d)], ms,
+                                                    inputs.SWEEP_TRIALS, seed=0)[0])
+        return cache[key]
+
+    t234 = {}
+    for lab, dim, m, d, mask, c, paper, _pin, cite in _golden("paper_subsets.txt"):
+        dim, m, d, mask = int(dim), int(m), float(d), int(mask, 16)
+        ms, err = sweep(dim, m, d, None)
+        cands = wino.wino_subset_pattern(err, ms, cg, (dim, m, 3, d), mask & 0xF0, 1.0, 20.0)
+        row = [x for x in cands if x["mask"] == mask][0]
+        t234[lab] = {"mask": "%#04x" % mask, "best_c": row["best_c"], "rel_err": row["best_err"],
+                     "printed_c": float(c), "printed_abs_err": float(paper), "cite": cite}
+    t56 = {}
+    for lab, dim, m, d, base, pat, cite in _golden("paper_patterns.txt"):
+        dim, m, d, base = int(dim), int(m), float(d), int(base, 16)
+        ms, err = sweep(dim, m, d, None)
+        cands = wino.wino_subset_pattern(err, ms, cg, (dim, m, 3, d), base, 1.0, 20.0)
+        t56[lab] = {"measured": "%#04x" % (cands[0]["mask"] & 0x0F),
+                    "win_frac": cands[0]["win_frac"], "best_c": cands[0]["best_c"],
+                    "printed": pat, "cite": cite,
+                    "candidates": {"%#04x" % (x["mask"] & 0x0F): x["best_err"] for x in cands}}
+    return {"tables_2_4": t234, "tables_5_6": t56,
+            "how": "GPU sweep of every base | subset mask, c > 1 of the 4096-value grid, 1000 "
+                   "trials; wino_subset_pattern per base"}
 
 
 def order_smem_ops(dim, m, r):

@@ -258,6 +258,48 @@ int wino_instance_matrices(const double* c_grid, int n_c, wino_size size,
                            unsigned char* singular, void* cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* Subset patterns (Sec. 6.2, Tables 2-6): fixed base points besides 0 and  */
+/* infinity joined to a subset of {-1/c, -c, c, 1/c}.                       */
+/* ---------------------------------------------------------------------- */
+
+/* One candidate subset of a base, ranked by the query below.              */
+typedef struct {
+  unsigned char mask;  /* the sweep mask: base bits | subset bits (0-3)     */
+  int best_k;          /* grid index of its least error in the window, -1
+                          when it has no finite error there                 */
+  double best_c;       /* c_grid[best_k] (NaN when best_k < 0)             */
+  double best_err;     /* that error (NaN when best_k < 0)                 */
+  double win_frac;     /* share of the window's c, among those where every
+                          candidate's error is finite, at which this
+                          candidate has the least error (ties to the
+                          smaller mask); 0 when there are none              */
+} wino_pattern_cand;
+
+/* The query behind Tables 2-6 of Sec. 6.2, over one size's sweep errors
+ * err[n_masks][n_c] (host; the [size] slice of wino_error_sweep's output for
+ * `size`, whose d fixes the d-group values).  A base is a set of d-group
+ * slots, base_mask (bits 4-7 only: e.g. d = 3 with bit 6 is the base point
+ * 3, with bit 5 the point -3; d = 2 with bit 7 is 1/2; d = 1 with bits 5 and
+ * 6 is the pair -1, 1; 0 is no base point besides 0 and infinity).  The
+ * candidates are the masks of `masks` whose bits 4-7 equal base_mask and
+ * that are valid for the size (popcount alpha - 2; bits 4 and 7 clear when
+ * |d| = 1).  Only grid points with c_lo <= c <= c_hi count (c > 1 covers
+ * every point set once: a subset at c is its mirror, -c <-> -1/c and
+ * c <-> 1/c, at 1/c).  Per candidate: its least finite error in the window
+ * (the first grid index on ties) and its win fraction.  cand_out (host,
+ * max_cand entries) receives the candidates ordered by best error, then
+ * mask, those with no finite error last; *n_cand = the number of
+ * candidates (entries beyond max_cand are not written).  The first entry is
+ * the base's pattern.  The paper states no procedure; this is the reading
+ * that reproduces its tables' layout.  Host code; needs no GPU.
+ * WINO_EINVAL for NULL arrays, n_masks or n_c < 1, base_mask bits 0-3 set
+ * or a bad size.                                                           */
+int wino_subset_pattern(const double* err, const unsigned char* masks, int n_masks,
+                        const double* c_grid, int n_c, wino_size size,
+                        unsigned char base_mask, double c_lo, double c_hi,
+                        wino_pattern_cand* cand_out, int max_cand, int* n_cand);
+
+/* ---------------------------------------------------------------------- */
 /* FP32 layer without allocation.                                           */
 /* ---------------------------------------------------------------------- */
 
@@ -390,6 +432,74 @@ int wino_mlp_predict(void* mlp, const float* X, int64_t n, float* out,
 int wino_topk_rows(const float* vals, int rows, int cols, int k, int* idx,
                    void* cuda_stream);
 void wino_mlp_destroy(void* mlp);
+
+/* Surrogate-guided search of a c grid.  For every (size, mask) pair valid
+ * under the rule of wino_error_sweep (a "row"):
+ *   1. the network `mlp` ranks every c of c_grid (predict kernel); its `top`
+ *      best predictions (top-k kernel) and `probe` random grid points
+ *      (SplitMix64 draws of the search's seed and run count) are evaluated
+ *      exactly in one planned launch;
+ *   2. the 2 refine + 1 grid points centred on the network's best verified
+ *      proposal are evaluated in a second planned launch (the error over c
+ *      is smooth at large scale but noisy between neighbours, Sec. 6.1);
+ *   3. a row whose network region (proposals and refinement) has a least
+ *      error above guard x the best random probe is swept exhaustively
+ *      (wino_error_sweep): the plain sweep is the fallback and the judge;
+ *   4. the row's result is the least error evaluated and its c.
+ * The paper has no surrogate; its observation that the error curve is
+ * roughly smooth (Sec. 6.1) motivates ranking a dense grid with a network
+ * and evaluating only the best candidates exactly.                         */
+typedef struct {
+  int top;       /* network proposals per row, 1 <= top <= n_c            */
+  int probe;     /* random grid points per row, >= 1                      */
+  int refine;    /* neighbours on each side of the refined point, >= 0     */
+  double guard;  /* fallback threshold factor, >= 1                        */
+} wino_guided_params;
+
+typedef struct {
+  int64_t evaluated;    /* instances evaluated (fallback rows count n_c)  */
+  int rows;             /* valid (size, mask) rows                        */
+  int fallback_rows;    /* rows swept exhaustively                        */
+  double phase_ms[4];   /* host wall time: rank, verify, refine, fallback */
+} wino_guided_stats;
+
+/* Builds a search over sizes x masks x c_grid (host arrays, copied; n_c <=
+ * 8192) with `trials` trials of `seed` (the sweep's trials and metric): the
+ * grid's features on the device and the two planned launches (their graphs
+ * captured once).  `mlp` (a wino_mlp_create handle) is borrowed and must
+ * outlive the search.  Allocates device memory owned by the search.        */
+int wino_guided_create(void* mlp, const wino_size* sizes, int n_sizes,
+                       const unsigned char* masks, int n_masks,
+                       const double* c_grid, int n_c, int trials,
+                       unsigned long long seed, const wino_guided_params* prm,
+                       void** search);
+/* One search with the network's present weights.  best_err and best_c are
+ * caller-owned host arrays [n_sizes][n_masks] (NaN where the mask is invalid
+ * for the size); stats may be NULL.  Every run draws new random probes.
+ * Synchronises cuda_stream.                                                */
+int wino_guided_run(void* search, double* best_err, double* best_c,
+                    wino_guided_stats* stats, void* cuda_stream);
+void wino_guided_destroy(void* search);
+
+/* The search without the network, for comparison: `budget` random grid
+ * points per valid (size, mask) row (SplitMix64 draws of `seed`) evaluated
+ * in one planned launch; best_err (host [n_sizes][n_masks], NaN where
+ * invalid) = the least error found per row.  Synchronises cuda_stream.    */
+int wino_random_search(const wino_size* sizes, int n_sizes, const unsigned char* masks,
+                       int n_masks, const double* c_grid, int n_c, int trials, int budget,
+                       unsigned long long seed, double* best_err, void* cuda_stream);
+
+/* The two-parameter sweep (Sec. 4: the group {-1/c, -c, c, 1/c} with a
+ * subset of {-1/d, -d, d, 1/d} for larger sizes): err_out (host,
+ * [n_d][n_masks][n_c]) = the sweep error of every mask at every (d, c) on
+ * the trials of size (dim, m, r) -- the same values as wino_error_sweep with
+ * sizes {dim, m, r, d_i} -- NaN where a mask is invalid for that d.  Runs as
+ * planned persistent launches of at most 64 d values each (the wide 2D
+ * sizes F(7x7,3x3), F(8x8,3x3) as wino_error_sweep calls).  d > 0.
+ * Synchronises cuda_stream.                                                */
+int wino_cd_sweep(int dim, int m, int r, const double* c_grid, int n_c, const double* d_grid,
+                  int n_d, const unsigned char* masks, int n_masks, int trials,
+                  unsigned long long seed, double* err_out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------- */
 /* Library state.                                                           */

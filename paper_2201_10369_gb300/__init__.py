@@ -38,6 +38,22 @@ class WinoSize(ctypes.Structure):
                 ("d", ctypes.c_double)]
 
 
+class WinoPatternCand(ctypes.Structure):
+    """One candidate subset of a subset-pattern query (Sec. 6.2)."""
+    _fields_ = [("mask", ctypes.c_ubyte), ("best_k", ctypes.c_int), ("best_c", ctypes.c_double),
+                ("best_err", ctypes.c_double), ("win_frac", ctypes.c_double)]
+
+
+class WinoGuidedParams(ctypes.Structure):
+    _fields_ = [("top", ctypes.c_int), ("probe", ctypes.c_int), ("refine", ctypes.c_int),
+                ("guard", ctypes.c_double)]
+
+
+class WinoGuidedStats(ctypes.Structure):
+    _fields_ = [("evaluated", ctypes.c_int64), ("rows", ctypes.c_int),
+                ("fallback_rows", ctypes.c_int), ("phase_ms", ctypes.c_double * 4)]
+
+
 class WinoInstance(ctypes.Structure):
     """One planned-sweep instance: size index, subset mask, parameter c."""
     _fields_ = [("size", ctypes.c_int), ("mask", ctypes.c_ubyte), ("c", ctypes.c_double)]
@@ -129,6 +145,25 @@ def _declare(L):
     L.wino_wait_probe.argtypes = [_i, ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p]
     L.wino_wait_probe.restype = _i
     L.wino_shutdown.restype = None
+    L.wino_subset_pattern.argtypes = [_DP, ctypes.POINTER(ctypes.c_ubyte), _i, _DP, _i, WinoSize,
+                                      ctypes.c_ubyte, _d, _d, ctypes.POINTER(WinoPatternCand), _i,
+                                      ctypes.POINTER(_i)]
+    L.wino_subset_pattern.restype = _i
+    _UB = ctypes.POINTER(ctypes.c_ubyte)
+    L.wino_guided_create.argtypes = [_vp, ctypes.POINTER(WinoSize), _i, _UB, _i, _DP, _i, _i,
+                                     ctypes.c_ulonglong, ctypes.POINTER(WinoGuidedParams),
+                                     ctypes.POINTER(_vp)]
+    L.wino_guided_create.restype = _i
+    L.wino_guided_run.argtypes = [_vp, _DP, _DP, ctypes.POINTER(WinoGuidedStats), _vp]
+    L.wino_guided_run.restype = _i
+    L.wino_guided_destroy.argtypes = [_vp]
+    L.wino_guided_destroy.restype = None
+    L.wino_random_search.argtypes = [ctypes.POINTER(WinoSize), _i, _UB, _i, _DP, _i, _i, _i,
+                                     ctypes.c_ulonglong, _DP, _vp]
+    L.wino_random_search.restype = _i
+    L.wino_cd_sweep.argtypes = [_i, _i, _i, _DP, _i, _DP, _i, _UB, _i, _i, ctypes.c_ulonglong,
+                                _DP, _vp]
+    L.wino_cd_sweep.restype = _i
     L.wino_pipe_peak.argtypes = [_i, _i, _i, _DP, _DP, _vp]
     L.wino_pipe_peak.restype = _i
     for name in ("wino_make_matrices", "wino_conv1d", "wino_conv2d", "wino_set_workspace",
@@ -375,6 +410,28 @@ def wino_error_sweep(c_grid, sizes, subsets, trials: int, seed: int = 0, stream=
     return err
 
 
+def wino_subset_pattern(err, masks, c_grid, size, base_mask: int, c_lo: float = 1.0,
+                        c_hi: float = float("inf")):
+    """The subset-pattern query (Sec. 6.2, Tables 2-6) over one size's sweep
+    errors err[n_masks][n_c]: the candidate subsets of `base_mask` ranked by
+    least error in the c window, as dicts {mask, best_k, best_c, best_err,
+    win_frac}; the first is the base's pattern."""
+    e = np.ascontiguousarray(err, dtype=np.float64)
+    mk = np.ascontiguousarray(masks, dtype=np.uint8)
+    cg = np.ascontiguousarray(c_grid, dtype=np.float64)
+    if e.shape != (mk.size, cg.size):
+        raise ValueError("err must be [n_masks][n_c]")
+    dim, m, r, d = size
+    out = (WinoPatternCand * 16)()
+    n = _i(0)
+    _check(load().wino_subset_pattern(e.ctypes.data_as(_DP), mk.ctypes.data_as(ctypes.POINTER(
+        ctypes.c_ubyte)), mk.size, cg.ctypes.data_as(_DP), cg.size, WinoSize(dim, m, r, d),
+        int(base_mask), float(c_lo), float(c_hi), out, 16, ctypes.byref(n)))
+    return [{"mask": int(o.mask), "best_k": int(o.best_k), "best_c": float(o.best_c),
+             "best_err": float(o.best_err), "win_frac": float(o.win_frac)}
+            for o in out[:min(n.value, 16)]]
+
+
 def wino_instance_matrices(c_grid, size, mask: int, stream=None):
     """Device-built FP64 matrices of the sweep instances (size, mask, c_k):
     (AT[n][m][alpha], G[n][alpha][r], BT[n][alpha][alpha], singular[n])."""
@@ -617,131 +674,62 @@ def surrogate_training_set(sizes, masks, n: int, trials: int, seed: int = 0, c_l
 
 
 class GuidedSearch:
-    """Surrogate-guided search of a c grid for every valid (size, mask) row.
-
-    Built once: the grid's features (device), the rows, and two planned
-    sweeps whose graphs are captured once.  Each run():
-      1. the network ranks every c of every row (predict kernel) and the
-         `top` best predictions per row (top-k kernel) plus `probe` random
-         grid points per row are evaluated exactly in one graph launch;
-      2. the `2 refine + 1` grid points around each row's best verified c
-         are evaluated in a second launch (the error curve is smooth at
-         large scale but noisy between neighbouring c, Sec. 6.1);
-      3. a row whose proposals' best is worse than `guard` x its probe's
-         best (the network failed there) is searched exhaustively.
-    """
+    """Surrogate-guided search of a c grid for every valid (size, mask) row
+    (wino_guided_create / wino_guided_run; the method is described in
+    include/wino.h): the network's `top` proposals and `probe` random grid
+    points verified in one planned launch, the neighbours of the network's
+    best refined in a second, and rows where the network's region loses to
+    `guard` x the random probe swept exhaustively."""
 
     def __init__(self, model, sizes, masks, c_grid, trials: int, seed: int = 0, top: int = 64,
                  probe: int = 64, refine: int = 32, guard: float = 1.01):
-        import torch
         L = load()
-        self.model, self.sizes, self.trials, self.seed = model, list(sizes), trials, seed
-        self.top, self.probe, self.refine, self.guard = top, probe, refine, guard
+        self._L = L
+        self.model, self.sizes = model, list(sizes)
         self.cg = np.ascontiguousarray(c_grid, dtype=np.float64)
-        self.masks = [int(mk) for mk in masks]
-        self.rows = [(s, mk) for s in range(len(sizes)) for mk in valid_masks(sizes[s], self.masks)]
-        rs = np.array([s for s, _ in self.rows], dtype=np.int32)
-        rm = np.array([mk for _, mk in self.rows], dtype=np.uint8)
-        self.rs, self.rm = rs, rm
-        self.X = torch.empty((len(self.rows) * self.cg.size, 16), dtype=torch.float32,
-                             device="cuda")
-        _check(L.wino_mlp_grid_features(_sizes(sizes), len(sizes),
-                                        rs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                                        rm.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
-                                        len(self.rows), self.cg.ctypes.data_as(_DP), self.cg.size,
-                                        _ptr(self.X), _stream(None)))
-        nr = len(self.rows)
-        c0 = float(self.cg[self.cg.size // 3])
-        self.verify = SweepPlan(sizes, instance_array(np.repeat(rs, top + probe),
-                                                      np.repeat(rm, top + probe), c0),
-                                trials, seed=seed, mode=WINO_SWEEP_PERSISTENT)
-        self.local = SweepPlan(sizes, instance_array(np.repeat(rs, 2 * refine + 1),
-                                                     np.repeat(rm, 2 * refine + 1), c0),
-                               trials, seed=seed, mode=WINO_SWEEP_PERSISTENT)
-        self.rng = np.random.default_rng(seed + 1)
-        self.nr = nr
+        self.masks = np.ascontiguousarray([int(mk) for mk in masks], dtype=np.uint8)
+        prm = WinoGuidedParams(int(top), int(probe), int(refine), float(guard))
+        h = ctypes.c_void_p()
+        _check(L.wino_guided_create(model._h, _sizes(sizes), len(sizes),
+                                    self.masks.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                    self.masks.size, self.cg.ctypes.data_as(_DP), self.cg.size,
+                                    int(trials), int(seed), ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h
 
-    def _run_plan(self, plan, sel):
-        c = self.cg[sel].ravel()
-        _check(plan._L.wino_sweep_plan_set_c(plan._h, c.ctypes.data_as(_DP), c.size))
-        err = plan.run().reshape(sel.shape)
-        return np.where(np.isfinite(err), err, np.inf)
-
-    def run(self):
-        import time
-        t0 = time.perf_counter()
-        nr, nc = self.nr, self.cg.size
-        pred = self.model.predict(self.X).reshape(nr, nc)
-        idx = wino_topk_rows(pred, self.top).cpu().numpy()
-        t1 = time.perf_counter()
-        probe = self.rng.integers(0, nc, (nr, self.probe))
-        sel = np.concatenate([idx, probe], axis=1)
-        ev = self._run_plan(self.verify, sel)
-        t2 = time.perf_counter()
-        r_idx = np.arange(nr)
-        vt = ev[:, :self.top].min(axis=1)
-        vp = ev[:, self.top:].min(axis=1)
-        bi = sel[r_idx, np.argmin(ev, axis=1)]
-        # local refinement around each row's best verified grid point
-        off = np.arange(-self.refine, self.refine + 1)
-        lsel = np.clip(bi[:, None] + off[None, :], 0, nc - 1)
-        le = self._run_plan(self.local, lsel)
-        lb = np.argmin(le, axis=1)
-        use_l = le[r_idx, lb] < ev[r_idx, np.argmin(ev, axis=1)]
-        best_e = np.where(use_l, le[r_idx, lb], ev.min(axis=1))
-        best_i = np.where(use_l, lsel[r_idx, lb], bi)
-        evaluated = sel.size + lsel.size
-        t3 = time.perf_counter()
-        # rows where the network's proposals lost to the random probe: exhaustive
-        fallback = np.nonzero(vt > self.guard * vp)[0]
-        by_size = {}
-        for r in fallback:
-            by_size.setdefault(int(self.rs[r]), []).append(r)
-        for s, rlist in by_size.items():
-            e = wino_error_sweep(self.cg, [self.sizes[s]], [int(self.rm[r]) for r in rlist],
-                                 self.trials, self.seed)[0]
-            e = np.where(np.isfinite(e), e, np.inf)
-            for j, r in enumerate(rlist):
-                k = int(np.argmin(e[j]))
-                best_e[r], best_i[r] = e[j, k], k
-            evaluated += len(rlist) * nc
-        t4 = time.perf_counter()
-        best = np.full((len(self.sizes), len(self.masks)), np.nan)
-        best_c = np.full_like(best, np.nan)
-        for r, (s, mk) in enumerate(self.rows):
-            q = self.masks.index(mk)
-            best[s, q], best_c[s, q] = best_e[r], self.cg[best_i[r]]
-        return {"best_err": best, "best_c": best_c, "evaluated": int(evaluated),
-                "fallback_rows": int(fallback.size), "rows": nr,
-                "phase_ms": {"rank": 1e3 * (t1 - t0), "verify": 1e3 * (t2 - t1),
-                             "refine": 1e3 * (t3 - t2), "fallback": 1e3 * (t4 - t3)}}
+    def run(self, stream=None):
+        shape = (len(self.sizes), self.masks.size)
+        best, best_c = np.empty(shape), np.empty(shape)
+        st = WinoGuidedStats()
+        _check(self._L.wino_guided_run(self._h, best.ctypes.data_as(_DP),
+                                       best_c.ctypes.data_as(_DP), ctypes.byref(st),
+                                       _stream(stream)))
+        ph = list(st.phase_ms)
+        return {"best_err": best, "best_c": best_c, "evaluated": int(st.evaluated),
+                "fallback_rows": int(st.fallback_rows), "rows": int(st.rows),
+                "phase_ms": {"rank": ph[0], "verify": ph[1], "refine": ph[2], "fallback": ph[3]}}
 
     def close(self):
-        self.verify.close()
-        self.local.close()
+        if getattr(self, "_h", None):
+            self._L.wino_guided_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
-def random_search(sizes, masks, c_grid, trials: int, budget: int, seed: int = 0):
-    """The search without the network, at a given per-row budget: `budget`
-    random grid points per valid (size, mask) row, evaluated in one planned
-    launch.  Returns best_err [n_sizes][n_masks]."""
+def random_search(sizes, masks, c_grid, trials: int, budget: int, seed: int = 0, stream=None):
+    """The search without the network, at a given per-row budget
+    (wino_random_search): best_err [n_sizes][n_masks]."""
     cg = np.ascontiguousarray(c_grid, dtype=np.float64)
-    masks = [int(mk) for mk in masks]
-    rows = [(s, mk) for s in range(len(sizes)) for mk in valid_masks(sizes[s], masks)]
-    rng = np.random.default_rng(seed + 2)
-    sel = rng.integers(0, cg.size, (len(rows), budget))
-    rs = np.repeat(np.array([s for s, _ in rows], dtype=np.int32), budget)
-    rm = np.repeat(np.array([mk for _, mk in rows], dtype=np.uint8), budget)
-    plan = SweepPlan(sizes, instance_array(rs, rm, cg[sel].ravel()), trials, seed=seed,
-                     mode=WINO_SWEEP_PERSISTENT)
-    try:
-        err = plan.run().reshape(len(rows), budget)
-    finally:
-        plan.close()
-    err = np.where(np.isfinite(err), err, np.inf)
-    best = np.full((len(sizes), len(masks)), np.nan)
-    for r, (s, mk) in enumerate(rows):
-        best[s, masks.index(mk)] = err[r].min()
+    mk = np.ascontiguousarray([int(v) for v in masks], dtype=np.uint8)
+    best = np.empty((len(sizes), mk.size))
+    _check(load().wino_random_search(_sizes(sizes), len(sizes),
+                                     mk.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), mk.size,
+                                     cg.ctypes.data_as(_DP), cg.size, int(trials), int(budget),
+                                     int(seed), best.ctypes.data_as(_DP), _stream(stream)))
     return best
 
 
@@ -775,45 +763,19 @@ def wino_pointset_error(size, point_sets, trials: int, seed: int = 0, stream=Non
     return err
 
 
-# Sizes the sweep runs with one warp per instance only (their per-lane tile
-# does not fit the registers): no planned persistent form.
-WIDE_SWEEP_SIZES = {(2, 7, 3), (2, 8, 3)}
-
-
 def cd_sweep(dim: int, m: int, c_grid, d_grid, masks, trials: int, seed: int = 0, r: int = 3,
-             mode: int = WINO_SWEEP_PERSISTENT) -> np.ndarray:
-    """The two-parameter sweep (Sec. 4: the c-group {-1/c, -c, c, 1/c} with a
-    subset of the d-group {-1/d, -d, d, 1/d} for larger sizes): the errors of
-    every valid mask at every (d, c), err[n_d][n_masks][n_c], NaN where a
-    mask is invalid for that d.  Runs as planned persistent launches of at
-    most 64 d values each (one plan size per d), or for the wide 2D sizes
-    F(7x7,3x3), F(8x8,3x3) as wino_error_sweep calls of 64 sizes (one per d);
-    the same trials as wino_error_sweep for size (dim, m, r)."""
+             stream=None) -> np.ndarray:
+    """The two-parameter sweep (wino_cd_sweep; Sec. 4: the c-group with a
+    subset of the d-group for larger sizes): err[n_d][n_masks][n_c], NaN
+    where a mask is invalid for that d."""
     cg = np.ascontiguousarray(c_grid, dtype=np.float64)
-    dg = [float(d) for d in d_grid]
-    masks = [int(mk) for mk in masks]
-    err = np.full((len(dg), len(masks), cg.size), np.nan)
-    for d0 in range(0, len(dg), 64):
-        sizes = [(dim, m, r, d) for d in dg[d0:d0 + 64]]
-        if (dim, m, r) in WIDE_SWEEP_SIZES:
-            err[d0:d0 + len(sizes)] = wino_error_sweep(cg, sizes, masks, trials, seed=seed)
-            continue
-        si, mi, ks = [], [], []
-        for s, size in enumerate(sizes):
-            for mk in valid_masks(size, masks):
-                si.append(np.full(cg.size, s, np.int32))
-                mi.append(np.full(cg.size, mk, np.uint8))
-                ks.append((s, masks.index(mk)))
-        if not ks:
-            continue
-        inst = instance_array(np.concatenate(si), np.concatenate(mi), np.tile(cg, len(ks)))
-        plan = SweepPlan(sizes, inst, trials, seed=seed, mode=mode)
-        try:
-            e = plan.run().reshape(len(ks), cg.size)
-        finally:
-            plan.close()
-        for row, (s, q) in enumerate(ks):
-            err[d0 + s, q] = e[row]
+    dg = np.ascontiguousarray(d_grid, dtype=np.float64)
+    mk = np.ascontiguousarray([int(v) for v in masks], dtype=np.uint8)
+    err = np.empty((dg.size, mk.size, cg.size))
+    _check(load().wino_cd_sweep(int(dim), int(m), int(r), cg.ctypes.data_as(_DP), cg.size,
+                                dg.ctypes.data_as(_DP), dg.size,
+                                mk.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), mk.size,
+                                int(trials), int(seed), err.ctypes.data_as(_DP), _stream(stream)))
     return err
 
 

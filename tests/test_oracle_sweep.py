@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_errors.txt")
+GOLDEN_SUBSETS = os.path.join(os.path.dirname(__file__), "golden", "paper_subsets.txt")
 
 
 def test_splitmix64_published_outputs(orc):
@@ -94,9 +95,9 @@ def test_sweep_threads_deterministic(orc):
     assert np.array_equal(e1, e4, equal_nan=True)
 
 
-def _golden_rows():
+def _golden_rows(path=GOLDEN):
     rows = []
-    with open(GOLDEN) as f:
+    with open(path) as f:
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
@@ -124,7 +125,8 @@ def _mean_abs_y(orc, dim, m, trials, seed):
     return tot / n
 
 
-@pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r["label"])
+@pytest.mark.parametrize("row", _golden_rows() + _golden_rows(GOLDEN_SUBSETS),
+                         ids=lambda r: r["label"])
 def test_paper_printed_errors(orc, row):
     """Our FP32-vs-FP64 error, in the per-element absolute reading, against
     the paper's printed value (Huffman order there, plain order here)."""
