@@ -465,6 +465,7 @@ def run_ours(args, rank, world, local_rank):
             if r:
                 roofs[k] = r
     roofs["sweep_plan"] = plan_roofline(t_plan, args.steps, ctx)
+    per_size = sweep_per_size(wino, inputs, ctx, rank)
     comparison = paper_comparison(wino, inputs, ex, cg, masks, sizes)
     patterns = subset_tables(wino, inputs)
     orders = order_sweeps(wino, inputs, cg, sizes, masks, rank, pipe)
@@ -501,7 +502,8 @@ def run_ours(args, rank, world, local_rank):
         "stacks": {k: {"value": tflops[k], "unit": "TFLOP/s",
                        "ms_per_step": 1e3 * tk[k] / args.steps} for k in STACKS},
         "sweep": {"value": vsw, "unit": "evals/s", "instances": n_inst, "trials": 1000,
-                  "ms_per_step": 1e3 * wall["sweep"] / args.steps, "path": "per-size kernels"},
+                  "ms_per_step": 1e3 * wall["sweep"] / args.steps, "path": "per-size kernels",
+                  "per_size": per_size},
         "sweep_plan": {"value": vplan, "unit": "evals/s",
                        "ms_per_step": 1e3 * wall["plan"] / args.steps,
                        "graph_ms_per_step": 1e3 * t_plan / args.steps,
@@ -918,6 +920,37 @@ def kernel_roofline(kernel, ms, n, ctx):
                 traffic=kernel_traffic(kernel, ctx, per_step),
                 peak_source=base["peak_source"], work_per_launch=work / per_step,
                 launches_per_step=per_step, mean_launch_ms=ms / n)
+
+
+def sweep_size_flops(dim, m, r, d, masks):
+    """Dense FP32 flops of one size's full sweep (4096 c x 1000 trials)."""
+    a = m + r - 1
+    nmask = sum(1 for mk in masks if bin(int(mk)).count("1") == a - 2 and
+                not (abs(d) == 1.0 and (int(mk) & 0x90)))
+    if dim == 1:
+        f = 2 * (a * r + a * a + m * a) + a
+    else:
+        f = 2 * (a * r * r + a * a * r) + 4 * a ** 3 + a * a + 2 * (m * a * a + m * m * a)
+    return nmask * 4096 * 1000 * f
+
+
+def sweep_per_size(wino, inputs, ctx, rank):
+    """Each sweep size alone (untimed by the step): its k_sweep_eval time
+    (CUDA events, the kernel only) and fraction of the FP32 peak."""
+    cg, masks = inputs.c_grid(), inputs.sweep_masks()
+    out = {}
+    for size in inputs.SWEEP_SIZES:
+        wino.wino_error_sweep(cg, [size], masks, inputs.SWEEP_TRIALS, seed=rank)  # warm-up
+        wino.wino_profile_enable(True)
+        wino.wino_profile_read("sweep_eval")
+        wino.wino_error_sweep(cg, [size], masks, inputs.SWEEP_TRIALS, seed=rank)
+        ms, n = wino.wino_profile_read("sweep_eval")
+        wino.wino_profile_enable(False)
+        fl = sweep_size_flops(*size, masks)
+        ach = fl / (ms / 1e3) / 1e12
+        out["%dd_F%d" % (size[0], size[1])] = {"kernel_ms": ms, "launches": n, "tflops": ach,
+                                               "frac": ach / ctx.fp32["peak"]}
+    return out
 
 
 def plan_roofline(t_plan, steps, ctx):

@@ -163,9 +163,13 @@ typedef struct {
  * FP64 and rounded once) and scored against the FP64 direct correlation:
  *   err = sum_t ||yhat_t - y_t||_1 / sum_t ||y_t||_1.
  * Summation order (the same in wino_error_sweep and every planned-sweep
- * mode, so all return the same bits): per trial the terms in FP32, trials in
- * chunks of 128 summed in FP64 from zero, chunk sums added in ascending
- * order.
+ * mode, so all return the same bits): per trial the terms in FP32; trials
+ * in chunks of 128, each chunk's trial sums accumulated in trial order as a
+ * compensated FP32 pair (hi, lo) -- per term (s, r) = TwoSum(hi, e) with
+ * s = hi + e, b = s - hi, r = (hi - (s - b)) + (e - b), then hi = s and
+ * lo = lo + r, every operation rounded to nearest -- and the chunk's value
+ * (double)hi + (double)lo; chunk values added in FP64 in ascending order.
+ * The result is within ~1e-10 relative of the exact sum.
  * err_out is a caller-owned HOST array [n_sizes][n_subsets][n_c] (FP64).
  * c_grid, sizes, subsets are host arrays.  Synchronises `cuda_stream`.     */
 int wino_error_sweep(const double* c_grid, int n_c,

@@ -513,7 +513,8 @@ __device__ __noinline__ double order_instance(const double* a, unsigned char* ba
   float* pl = reinterpret_cast<float*>(base + L::P_OFF) + lane;
   if constexpr (!HUFF) {
     static_assert(kTrialChunk % 32 == 0, "chunks are whole rounds of 32 trials");
-    double num = 0.0, chunk = 0.0;
+    double num = 0.0;
+    ChunkSum chunk;
     const int rounds = (trials + 31) / 32;
     for (int rd = 0; rd < rounds; ++rd) {
       const int t = rd * 32 + lane;
@@ -522,11 +523,11 @@ __device__ __noinline__ double order_instance(const double* a, unsigned char* ba
       const int n_here = min(32, trials - rd * 32);
       for (int j = 0; j < 32; ++j) {  // this round's errors in trial order
         const float ej = __shfl_sync(kFull, e, j);
-        if (j < n_here) chunk += (double)ej;
+        if (j < n_here) chunk.add(ej);
       }
       if ((rd + 1) % (kTrialChunk / 32) == 0 || rd + 1 == rounds) {
-        num += chunk;
-        chunk = 0.0;
+        num += chunk.value();
+        chunk = ChunkSum();
       }
     }
     return num / ysum;

@@ -97,9 +97,10 @@ def _ranks(best, ex, rows):
 @pytest.mark.slow
 def test_guided_search_gain(wino):
     """What the network gains.  Trained on sweep labels, the guided search
-    evaluates at most 25% of the 4096-c grid (193 grid points per row plus
-    4096 for each row whose proposals lose to the random probe -- about one
-    row in seven here), and the error it finds per
+    evaluates at most 15% of the 4096-c grid (193 grid points per row, 4.7%,
+    plus 4096 for each row whose refined proposals lose to the random probe
+    -- one row in fifteen measured, so at most one row in ten is allowed),
+    and the error it finds per
     (size, mask) row ranks among the best of the exhaustive sweep's 4096
     values of that row: median rank <= 2, 90th percentile <= 32 (0.8% of the
     grid).  A random search given the same per-row budget -- the method
@@ -122,7 +123,7 @@ def test_guided_search_gain(wino):
     ex = np.where(np.isinf(ex), np.nan, ex)
     rows = np.any(np.isfinite(ex), axis=2)
     exb = np.nanmin(np.where(rows[:, :, None], ex, 1.0), axis=2)
-    assert res["evaluated"] <= 0.25 * rows.sum() * cg.size, res["fallback_rows"]
+    assert res["evaluated"] <= 0.15 * rows.sum() * cg.size, res["fallback_rows"]
     assert np.median(res["best_err"][rows] / exb[rows]) <= 1.01
     rk = _ranks(res["best_err"], ex, rows)
     assert np.median(rk) <= 2 and np.percentile(rk, 90) <= 32, (np.median(rk), np.percentile(rk, 90))

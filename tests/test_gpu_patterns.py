@@ -98,9 +98,14 @@ def reproduces(r, cands):
 
 
 def test_patterns_vs_paper(wino):
+    """14 of the 16 printed entries reproduce (both "No pattern" entries
+    among them: the best subset wins about 0.37 of the c > 1 window).  The
+    base 1/2 F(3,3) entries, {-c, c} in both tables, measure {-1/c, c} by a
+    near-tie (its win fraction 0.46 in 1D, 0.20 in 2D); the bar leaves
+    room for one more near-tie to flip."""
     rows = golden_patterns()
     meas = measured_patterns(wino)
     ok = [reproduces(r, meas[r["label"]]) for r in rows]
     print({r["label"]: ("%#04x" % (meas[r["label"]][0]["mask"] & 15),
                         round(meas[r["label"]][0]["win_frac"], 2), o) for r, o in zip(rows, ok)})
-    assert sum(ok) >= 12, [r["label"] for r, o in zip(rows, ok) if not o]
+    assert sum(ok) >= 13, [r["label"] for r, o in zip(rows, ok) if not o]
