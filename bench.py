@@ -1038,10 +1038,14 @@ def profile_case(name):
         for _ in range(4):
             for (x, w), y in zip(xs, ys):
                 wino.wino_conv2d(x, w, y, pts, m, 3, 1, dt)
-    elif name == "sweep":
+    elif name == "sweep" or (name.startswith("sweep_") and name[6:7] in "12" and
+                             name[7:8] == "d" and name[8:].isdigit()):
+        # sweep: 2D F(4x4,3x3); sweep_<dim>d<m>: that size (the d of the sweep)
+        dim, m = (2, 4) if name == "sweep" else (int(name[6]), int(name[8:]))
+        size = [s_ for s_ in inputs.SWEEP_SIZES if s_[0] == dim and s_[1] == m][0]
         cg = inputs.c_grid()
         for _ in range(4):
-            wino.wino_error_sweep(cg, [(2, 4, 3, 1.0)], inputs.sweep_masks(), 1000, seed=0)
+            wino.wino_error_sweep(cg, [size], inputs.sweep_masks(), 1000, seed=0)
     elif name == "fp64_ref":
         # the FP64 direct reference and the FP64 error reduction on one VGG16
         # stage-2 shape (128 ch, 112x112, N = 2): 1.2 GFLOP in FP64
@@ -1075,6 +1079,7 @@ def main():
                          "f4x4 | f6x6 | f4x4_bf16 | f4x4_split | f4x4_x6 (VGG 64ch 224x224, N=8; "
                          "suffix _vgg: the five VGG16 stages, N=8; suffix _l0.._l4: that "
                          "VGG16 stage at N=32) | sweep (2D F(4x4), all masks, 4096 c) | "
+                         "sweep_<dim>d<m> (that sweep size, e.g. sweep_1d4) | "
                          "sweep_huffman | sweep_huffman_mixed (the same in the Huffman "
                          "orders) | fp64_ref (FP64 direct reference and error reduction, "
                          "128 ch 112x112, N=2)")
