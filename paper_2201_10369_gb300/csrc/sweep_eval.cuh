@@ -198,8 +198,7 @@ __device__ __forceinline__ double chunk_error_ev(const Ev& ev, const float* __re
   constexpr int REC = Ev::REC;
   ChunkSum num;
   const float4* r4 = reinterpret_cast<const float4*>(rec);
-  for (int t = t0; t < t1; ++t) {
-    float buf[REC];
+  auto load = [&](int t, float (&buf)[REC]) {
 #pragma unroll
     for (int q = 0; q < REC / 4; ++q) {
       const float4 v = __ldg(r4 + (int64_t)t * (REC / 4) + q);
@@ -208,6 +207,23 @@ __device__ __forceinline__ double chunk_error_ev(const Ev& ev, const float* __re
       buf[4 * q + 2] = v.z;
       buf[4 * q + 3] = v.w;
     }
+  };
+  int t = t0;
+  if constexpr (Ev::PAIRS) {
+    // short tiles: two trials per iteration, two independent evaluations
+    // in flight; their errors still join the sum in trial order
+    for (; t + 1 < t1; t += 2) {
+      float b0[REC], b1[REC];
+      load(t, b0);
+      load(t + 1, b1);
+      const float e0 = ev(b0), e1 = ev(b1);
+      num.add(e0);
+      num.add(e1);
+    }
+  }
+  for (; t < t1; ++t) {
+    float buf[REC];
+    load(t, buf);
     num.add(ev(buf));
   }
   return num.value();
@@ -242,6 +258,7 @@ __device__ __forceinline__ void lane_eval_ev(const Ev& ev, bool ok, const float*
 template <int DIM, int M, int R>
 struct PlainEval {
   static constexpr int REC = SweepShape<DIM, M, R>::REC;
+  static constexpr bool PAIRS = DIM == 1;
   const Mats<M, R>& Mx;
   __device__ __forceinline__ float operator()(const float* buf) const {
     return DIM == 1 ? tile_err_1d<M, R>(Mx, buf) : tile_err_2d<M, R>(Mx, buf);
