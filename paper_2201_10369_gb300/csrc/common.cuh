@@ -68,6 +68,37 @@ __device__ __forceinline__ void filter_transform_one(const float* __restrict__ g
     }
 }
 
+// V = G g G^T of one (c, k) kernel with compile-time sizes, in the FP32
+// layer's order (W = G g, l ascending; then V = W G^T, q ascending; every sum
+// from zero with fmaf), so the values equal the FP32 filter transform's.
+template <int MM>
+__device__ __forceinline__ void filter_fixed(const float* g9, const LayerMats& M,
+                                             float (&v)[(MM + 2) * (MM + 2)]) {
+  constexpr int A = MM + 2, R = 3;
+  float gl[R * R];
+#pragma unroll
+  for (int i = 0; i < R * R; ++i) gl[i] = g9[i];
+  float Wk[A][R];
+#pragma unroll
+  for (int i = 0; i < A; ++i)
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int l = 0; l < R; ++l) acc = fmaf(M.G[i * R + l], gl[l * R + q], acc);
+      Wk[i][q] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < A; ++i)
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < R; ++q) acc = fmaf(Wk[i][q], M.G[j * R + q], acc);
+      v[i * A + j] = acc;
+    }
+}
+
 // Per-device int in device memory, zero until a kernel's bounded wait gives
 // up (the kernel then stores 1 and abandons its tile); wino_wait_error
 // reads and clears it.

@@ -553,24 +553,49 @@ __global__ void __launch_bounds__(256) k_input_transform_blk(const float* __rest
   for (int e = threadIdx.x; e < n4; e += blockDim.x) dst[e] = src[e];
 }
 
-// Filter transform into Vb: one thread per (channel, output channel) over
-// the padded channel range, output channels fastest.
+// Filter transform into Vb.  One CTA per 32 output channels x 32 input
+// channels (of the padded range): the 32 x 32 kernels are staged in shared
+// memory first -- for each output channel its 32 input channels' taps are
+// 288 contiguous floats of w, read coalesced -- with rows padded to 289
+// floats, so that the compute pass, one thread per (input, output channel)
+// with output channels across the lanes, reads them without bank conflicts
+// and writes each frequency's 32 outputs as one contiguous run of Vb.
+// (Reading w straight from global memory with output channels across the
+// lanes touched 32 lines per load.)  Launch: grid (ceil(K / 32),
+// ceil(nch CC / 32)), 256 threads.
+constexpr int kFtK = 32, kFtC = 32, kFtRow = kFtC * 9 + 1;
+template <int MM>
 __global__ void __launch_bounds__(256) k_filter_transform_blk(const float* __restrict__ w,
                                                               float* __restrict__ Vb, int C,
                                                               int K, const LayerMats M,
                                                               const SplitGeom sg) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)sg.nch * sg.CC * K) return;
-  const int k = (int)(idx % K), c = (int)(idx / K);
-  const int kb = k / sg.KB, kl = k - kb * sg.KB;
-  const int ch = c / sg.CC, cc = c - ch * sg.CC;
-  float* out = Vb + ((int64_t)kb * sg.nch + ch) * sg.F_ * sg.VPL + cc * sg.KB + kl;
-  if (c >= C) {
-    for (int f = 0; f < sg.F_; ++f) out[(int64_t)f * sg.VPL] = 0.0f;
-    return;
+  constexpr int F = (MM + 2) * (MM + 2);
+  __shared__ float ws[kFtK * kFtRow];
+  const int k0 = blockIdx.x * kFtK, c0 = blockIdx.y * kFtC;
+  const int cpad = sg.nch * sg.CC;
+  for (int e = threadIdx.x; e < kFtK * kFtC * 9; e += blockDim.x) {
+    const int kk = e / (kFtC * 9), r = e - kk * (kFtC * 9);
+    const int k = k0 + kk, c = c0 + r / 9;
+    ws[kk * kFtRow + r] = (k < K && c < C) ? __ldg(w + ((int64_t)k * C + c0) * 9 + r) : 0.0f;
   }
-  filter_transform_one(w + ((int64_t)k * C + c) * M.r * M.r, 2, M,
-                       [&](int f, float v) { out[(int64_t)f * sg.VPL] = v; });
+  __syncthreads();
+  for (int e = threadIdx.x; e < kFtK * kFtC; e += blockDim.x) {
+    const int kk = e % kFtK, cl = e / kFtK;
+    const int k = k0 + kk, c = c0 + cl;
+    if (k >= K || c >= cpad) continue;
+    const int kb = k / sg.KB, kl = k - kb * sg.KB;
+    const int ch = c / sg.CC, cc = c - ch * sg.CC;
+    float* out = Vb + ((int64_t)kb * sg.nch + ch) * F * sg.VPL + cc * sg.KB + kl;
+    float v[F];
+    if (c < C) {
+      filter_fixed<MM>(ws + kk * kFtRow + cl * 9, M, v);
+    } else {
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[f] = 0.0f;
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) out[(int64_t)f * sg.VPL] = v[f];
+  }
 }
 
 // NS stages of (U chunk, V chunk) in shared memory; MINB CTAs per SM.
@@ -1102,10 +1127,10 @@ template <int MM>
 static bool launch_split_transforms(const float* x, const float* w, const LayerGeom& g,
                                     const LayerMats& M, const SplitGeom& sg, float* Ub, float* Vb,
                                     cudaStream_t st) {
-  const int64_t nfl = (int64_t)sg.nch * sg.CC * g.K;
+  const int fy = (sg.nch * sg.CC + kFtC - 1) / kFtC;
   const size_t csm = (size_t)g.F * sg.UPL * sizeof(float);
   constexpr int kMaxCsm = 96 * 1024;
-  if (sg.nch > 65535 || (nfl + 255) / 256 > 0x7fffffffLL || csm > (size_t)kMaxCsm) return false;
+  if (sg.nch > 65535 || fy > 65535 || csm > (size_t)kMaxCsm) return false;
   static bool attr_set[16] = {false};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -1117,7 +1142,8 @@ static bool launch_split_transforms(const float* x, const float* w, const LayerG
   }
   {
     ProfScope ps(kKFilter, st);
-    k_filter_transform_blk<<<(unsigned)((nfl + 255) / 256), 256, 0, st>>>(w, Vb, g.C, g.K, M, sg);
+    k_filter_transform_blk<MM><<<dim3((unsigned)((g.K + kFtK - 1) / kFtK), (unsigned)fy), 256, 0,
+                                 st>>>(w, Vb, g.C, g.K, M, sg);
   }
   {
     ProfScope ps(kKInput, st);
