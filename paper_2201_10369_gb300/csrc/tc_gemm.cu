@@ -212,136 +212,148 @@ __global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ 
 }
 
 // Input transform (FP32, the FP32 layer's order) -> operand parts
-// U0/U1/U2 [f][t][c], scaled; columns c >= C are zero (rows t >= T:
-// k_quant_zero_tail).
-//
-// One CTA = TQ consecutive tiles of one tile row x one 64-channel chunk.
-// First the CTA copies the input band those tiles read -- alpha rows x
-// (TQ m + 2) columns x 64 channels, zero outside the image and past C --
-// into shared memory with coalesced row loads (16 columns x 2 channels per
-// warp instruction).  The band is stored channel-fastest, [row][column][64],
-// channel c of column col at c ^ 2 (col & 15): the loads' stores spread over
-// all 32 banks, and so do the patch reads below.  Then one thread per
-// (tile, channel), warps = 32 channels of one tile, computes B^T d B from
-// the band in the FP32 layer's order, scales, splits and stores each
-// frequency's 16-bit value straight to the operand image: the 32 lanes of a
-// warp write 64 contiguous bytes of one (frequency, tile) row (the
-// 128-byte swizzle permutes whole 16-byte pieces within an aligned group
-// of four), so no output staging is needed.  (The previous form read each
-// patch from global memory per thread, its warps touching eight lines per
-// load, and staged the results: 41-48% of HBM.)
-template <int MM, int TQ>
-struct QuantBand {
-  static constexpr int A = MM + 2, F = A * A, BW = TQ * MM + 2;
-  static constexpr int NCB = (BW + 15) / 16;    // column blocks of 16
-  static constexpr int NT = TQ * 64;            // threads
-  static constexpr size_t SMEM = (size_t)A * BW * 64 * sizeof(float);
-};
+// U0/U1/U2 [f][t][c], scaled; rows t >= T and columns c >= C are zero.
+// One block = kQT = 4 tiles x 64 channels; a thread transforms two adjacent
+// channels of one tile (tiles fastest: neighbouring patches share input
+// rows).  The 16-bit results are staged in shared memory as 32-bit channel
+// pairs -- rows of kQRow = 32 pairs, pair p of tile tl's row at word
+// p ^ 8 tl, so the 32 stores of a warp (4 tiles x 8 pairs) hit 32 distinct
+// banks with no padding -- and leave as whole 128-byte rows of 64 channels
+// (one cache line per (f, tile) and part).  (Rows padded to 40 words
+// instead held one F(6x6) split-BF16x6 block per SM, not two.)
+// (Splitting the transform's rows over 2-4 blocks, for staging within 36 KB
+// and five blocks per SM, measured 8-15% slower per stack: every block
+// loads the whole patch, and the patch loads are what this kernel waits on.
+// Issuing both channels' patch loads before either transform measured the
+// same for the split forms and 3% slower for BF16: 122 registers instead
+// of 80.)
+constexpr int kQT = 4, kQC = 64, kQP = kQC / 2, kQRow = kQP;
+// staging word of channel pair p in tile tl's row (bank-conflict swizzle)
+__device__ __forceinline__ int qswz(int p, int tl) { return p ^ (tl << 3); }
+constexpr int kQuantThreads = kQT * kQP;
+// largest staging: three parts of F = 64 frequencies (m = 6)
+constexpr int kQuantSmemMax = 3 * 64 * kQT * kQRow * 4;
 
-__device__ __forceinline__ int qband_swz(int c, int col) { return c ^ ((col & 15) << 1); }
-// tiles per CTA by m: 512, 256 and 128 threads; bands of 18, 28 and 29 KB
-constexpr int kQuantTQ2 = 8, kQuantTQ4 = 4, kQuantTQ6 = 2;
-
-template <int MM, int TQ>
-__global__ void __launch_bounds__(QuantBand<MM, TQ>::NT) k_quant_input_band(
-    const float* __restrict__ x, const LayerGeom g, const LayerMats Mx, const TcScales S, int Cp,
-    int64_t Tp, int nseg, uint16_t* __restrict__ U0, uint16_t* __restrict__ U1,
-    uint16_t* __restrict__ U2, int mode) {
-  using Q = QuantBand<MM, TQ>;
-  constexpr int A = Q::A, BW = Q::BW;
-  extern __shared__ __align__(16) float band[];  // [A][BW][64], channels swizzled
-  const int seg = blockIdx.x;
-  const int per_img = g.th * nseg;
-  const int n = seg / per_img;
-  const int rem = seg - n * per_img;
-  const int ti = rem / nseg, tj0 = (rem - ti * nseg) * TQ;
-  const int c0 = blockIdx.y * 64;
-  const int h0 = ti * MM - g.pad, w0 = tj0 * MM - g.pad;
-  const int64_t HW = (int64_t)g.H * g.W;
-  const float* xn = x + (int64_t)n * g.C * HW;
-  // the band: unit = (row i, channel pair, column block); lanes 16 columns x 2 channels
-  for (int e = threadIdx.x; e < A * 32 * Q::NCB * 32; e += Q::NT) {
-    const int l = e & 31, unit = e >> 5;
-    const int cb = unit % Q::NCB, cq = (unit / Q::NCB) % 32, i = unit / (Q::NCB * 32);
-    const int col = cb * 16 + (l & 15), c = 2 * cq + (l >> 4);
-    if (col >= BW) continue;
-    const int hh = h0 + i, ww = w0 + col, cg = c0 + c;
-    const bool ok = (unsigned)hh < (unsigned)g.H && (unsigned)ww < (unsigned)g.W && cg < g.C;
-    band[(i * BW + col) * 64 + qband_swz(c, col)] =
-        ok ? __ldg(xn + (int64_t)cg * HW + (int64_t)hh * g.W + ww) : 0.0f;
-  }
-  __syncthreads();
-  const int tl = threadIdx.x >> 6, c = threadIdx.x & 63;
-  const int tj = tj0 + tl;
-  if (tj >= g.tw) return;
-  const int64_t t = ((int64_t)n * g.th + ti) * g.tw + tj;
+// B^T d B of the tile patch of channel c (zeros when the tile or the channel
+// is out of range), rows i in [I0, I1) of the result only: frequency f =
+// i alpha + j at out(f, v).  Each value is computed exactly as by the whole
+// transform (the row restriction only skips rows).
+template <int MM, int I0, int I1, class Out>
+__device__ __forceinline__ void quant_patch(const float* __restrict__ x, const LayerGeom& g,
+                                            const LayerMats& Mx, int64_t t, int c, Out out) {
+  constexpr int A = MM + 2;
   float d[A][A];
+  const bool live = t < g.T && c < g.C;
+  if (live) {
+    const int tpi = g.th * g.tw;
+    const int n = (int)(t / tpi);
+    const int rem = (int)(t - (int64_t)n * tpi);
+    const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
+    const int h0 = ti * MM - g.pad, w0 = tj * MM - g.pad;
+    const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
 #pragma unroll
-  for (int i = 0; i < A; ++i)
+    for (int i = 0; i < A; ++i)
 #pragma unroll
-    for (int j = 0; j < A; ++j) {
-      const int col = MM * tl + j;
-      d[i][j] = band[(i * BW + col) * 64 + qband_swz(c, col)];
-    }
-  const int parts = tc_parts(mode);
-  const int64_t ntb = Tp / kTcM;
-  const int nch = Cp / kTcKc;
-  // tc_u_index is linear in the frequency: one base and one stride
-  const int64_t obase = tc_u_index(0, t, c0 + c, ntb, nch);
-  const int64_t fstride = ntb * nch * (int64_t)(kTcM * kTcKc);
-  uint16_t* u0 = U0 + obase;
-  uint16_t* u1 = U1 + obase;
-  uint16_t* u2 = U2 + obase;
-  // one frequency row at a time: the column pass's row i (B^T d), then its
-  // alpha outputs (. B); every value in the order of the whole transform
+      for (int j = 0; j < A; ++j) {
+        const int hh = h0 + i, ww = w0 + j;
+        d[i][j] = ((unsigned)hh < (unsigned)g.H && (unsigned)ww < (unsigned)g.W)
+                      ? __ldg(xc + (int64_t)hh * g.W + ww)
+                      : 0.0f;
+      }
+  } else {
 #pragma unroll
-  for (int i = 0; i < A; ++i) {
-    float tmi[A];
+    for (int i = 0; i < A; ++i)
+#pragma unroll
+      for (int j = 0; j < A; ++j) d[i][j] = 0.0f;
+  }
+  float tm[I1 - I0][A];
+#pragma unroll
+  for (int i = I0; i < I1; ++i)
 #pragma unroll
     for (int l = 0; l < A; ++l) {
       float acc = 0.0f;
 #pragma unroll
       for (int q = 0; q < A; ++q) acc = fmaf(Mx.BT[i * A + q], d[q][l], acc);
-      tmi[l] = acc;
+      tm[i - I0][l] = acc;
     }
+#pragma unroll
+  for (int i = I0; i < I1; ++i)
 #pragma unroll
     for (int j = 0; j < A; ++j) {
       float acc = 0.0f;
 #pragma unroll
-      for (int l = 0; l < A; ++l) acc = fmaf(tmi[l], Mx.BT[j * A + l], acc);
-      const int f = i * A + j;
-      uint16_t q[3];
-      split_parts(acc * S.sU[f], mode, q);
-      u0[f * fstride] = q[0];
-      if (parts > 1) u1[f * fstride] = q[1];
-      if (parts > 2) u2[f * fstride] = q[2];
+      for (int l = 0; l < A; ++l) acc = fmaf(tm[i - I0][l], Mx.BT[j * A + l], acc);
+      out(i * A + j, live ? acc : 0.0f);
     }
-  }
 }
 
-// Zero rows t in [T, Tp) of every (frequency, chunk) block of the U parts
-// (the contraction's padding tiles): one 16-byte store per thread.
-__global__ void __launch_bounds__(256) k_quant_zero_tail(int F, int64_t T, int64_t Tp, int Cp,
-                                                         int parts, uint16_t* __restrict__ U0,
-                                                         uint16_t* __restrict__ U1,
-                                                         uint16_t* __restrict__ U2) {
-  const int64_t rows = Tp - T;
-  const int nch = Cp / kTcKc;
-  const int64_t n = (int64_t)F * rows * nch * 8;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const int piece = (int)(e % 8);
-  const int64_t row = e / 8;
-  const int ch = (int)(row % nch);
-  const int64_t t = T + (row / nch) % rows;
-  const int f = (int)(row / ((int64_t)nch * rows));
-  // the row (f, t) of chunk ch: 64 contiguous elements (whole row, so the
-  // swizzle of its pieces does not matter)
-  const int64_t ntb = Tp / kTcM;
-  const int64_t o = ((((int64_t)f * ntb + t / kTcM) * nch + ch) * kTcM + t % kTcM) * kTcKc +
-                    piece * 8;
-  uint16_t* const dst[3] = {U0, U1, U2};
-  for (int pp = 0; pp < parts; ++pp) *reinterpret_cast<uint4*>(dst[pp] + o) = make_uint4(0, 0, 0, 0);
+// Rows [I0, I1) of two adjacent channels' transforms, scaled, split and
+// staged as 32-bit channel pairs (channel c in the low half).
+template <int MM, int I0, int I1>
+__device__ __forceinline__ void quant_pair_rows(const float* __restrict__ x, const LayerGeom& g,
+                                                const LayerMats& Mx, const TcScales& S,
+                                                int64_t t, int c, int tl, int cp, int mode,
+                                                int parts, uint32_t* qs, int kPart) {
+  constexpr int A = MM + 2, NR = (I1 - I0) * A;
+  float ua[NR];
+  quant_patch<MM, I0, I1>(x, g, Mx, t, c, [&](int f, float v) { ua[f - I0 * A] = v; });
+  quant_patch<MM, I0, I1>(x, g, Mx, t, c + 1, [&](int f, float v) {
+    uint16_t qa[3], qb[3];
+    split_parts(ua[f - I0 * A] * S.sU[f], mode, qa);
+    split_parts(v * S.sU[f], mode, qb);
+    const int o = (f * kQT + tl) * kQRow + qswz(cp, tl);
+    qs[o] = (uint32_t)qa[0] | ((uint32_t)qb[0] << 16);
+    if (parts > 1) qs[kPart + o] = (uint32_t)qa[1] | ((uint32_t)qb[1] << 16);
+    if (parts > 2) qs[2 * kPart + o] = (uint32_t)qa[2] | ((uint32_t)qb[2] << 16);
+  });
+}
+
+template <int MM>
+__global__ void __launch_bounds__(kQuantThreads) k_quant_input_tiled(
+    const float* __restrict__ x, const LayerGeom g, const LayerMats Mx, const TcScales S, int Cp,
+    int64_t Tp, uint16_t* __restrict__ U0, uint16_t* __restrict__ U1, uint16_t* __restrict__ U2,
+    int mode) {
+  constexpr int A = MM + 2, F = A * A;
+  extern __shared__ __align__(16) uint32_t qs[];  // [parts][F][kQT][kQRow] channel pairs
+  constexpr int kPart = F * kQT * kQRow;          // one part's staging, in words
+  const int tl = threadIdx.x % kQT, cp = threadIdx.x / kQT;
+  const int64_t t = (int64_t)blockIdx.x * kQT + tl;
+  const int c = blockIdx.y * kQC + 2 * cp;
+  const int parts = tc_parts(mode);
+  if constexpr (A <= 6) {
+    // both channels' values of a frequency meet in registers: one 32-bit
+    // store per (f, part)
+    quant_pair_rows<MM, 0, A>(x, g, Mx, S, t, c, tl, cp, mode, parts, qs, kPart);
+  } else {
+    // alpha = 8: holding one channel's 64 values while transforming the
+    // other costs too many registers (and transforming in row halves costs
+    // a second pass over the patches), so each channel goes straight to its
+    // 16-bit half of the same words
+    uint16_t* qh = reinterpret_cast<uint16_t*>(qs);
+    for (int h = 0; h < 2; ++h)
+      quant_patch<MM, 0, A>(x, g, Mx, t, c + h, [&](int f, float v) {
+        uint16_t q[3];
+        split_parts(v * S.sU[f], mode, q);
+        const int o = 2 * ((f * kQT + tl) * kQRow + qswz(cp, tl)) + h;
+        qh[o] = q[0];
+        if (parts > 1) qh[2 * kPart + o] = q[1];
+        if (parts > 2) qh[4 * kPart + o] = q[2];
+      });
+  }
+  __syncthreads();
+  // rows (f, tile) of 64 channels = 8 x 16-byte stores, consecutive threads
+  // on consecutive segments of a row (one 128-byte line of the blocked image)
+  const int64_t tb = (int64_t)blockIdx.x * kQT;
+  const int c0 = blockIdx.y * kQC;
+  uint16_t* const dsts[3] = {U0, U1, U2};
+  for (int e = threadIdx.x; e < F * kQT * 8; e += kQuantThreads) {
+    const int seg = e % 8, row = e / 8;  // row = f * kQT + tile
+    const int f = row / kQT, tr = row % kQT;
+    const int64_t dst = tc_u_index(f, tb + tr, c0 + seg * 8, Tp / kTcM, Cp / kTcKc);
+    for (int pp = 0; pp < parts; ++pp)
+      *reinterpret_cast<uint4*>(dsts[pp] + dst) =
+          *reinterpret_cast<const uint4*>(qs + pp * kPart + row * kQRow + qswz(seg * 4, tr));
+  }
 }
 
 // Output transform A^T M A with compile-time sizes, M [F][K][T]: one thread
@@ -754,40 +766,33 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
       k_filter_quant<6><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
                                             NB);
     }
-    // input transform: tile-row bands (QuantBand), then the padding tiles
-    auto band = [&](auto kern, int tq, size_t smem) -> int {
-      const int nseg = (g.tw + tq - 1) / tq;
-      const int64_t nblk = (int64_t)g.N * g.th * nseg;
-      if (nblk > 0x7fffffffLL || Cp / kTcKc > 65535) {
-        set_error("layer too large for the quantising transform's grid");
-        return WINO_EINVAL;
-      }
-      static bool qattr[16] = {false};
-      int qdev = 0;
-      WINO_CUDA_TRY(cudaGetDevice(&qdev));
-      if (qdev < 16 && !qattr[qdev]) {
-        WINO_CUDA_TRY(
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        qattr[qdev] = true;
-      }
-      kern<<<dim3((unsigned)nblk, (unsigned)(Cp / kTcKc)), tq * 64, smem, st>>>(
-          x, g, M, S, Cp, Tp, nseg, Up[0], Up[1], Up[2], mode);
-      return WINO_OK;
-    };
-    int qrc;
-    if (M.m == 2)
-      qrc = band(k_quant_input_band<2, kQuantTQ2>, kQuantTQ2, QuantBand<2, kQuantTQ2>::SMEM);
-    else if (M.m == 4)
-      qrc = band(k_quant_input_band<4, kQuantTQ4>, kQuantTQ4, QuantBand<4, kQuantTQ4>::SMEM);
-    else
-      qrc = band(k_quant_input_band<6, kQuantTQ6>, kQuantTQ6, QuantBand<6, kQuantTQ6>::SMEM);
-    if (qrc != WINO_OK) return qrc;
-    if (Tp > g.T) {
-      const int64_t nz = (int64_t)g.F * (Tp - g.T) * (Cp / kTcKc) * 8;
-      k_quant_zero_tail<<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(g.F, g.T, Tp, Cp, parts,
-                                                                      Up[0], Up[1], Up[2]);
-      note_launches(1);
+    const dim3 gq((unsigned)(Tp / kQT), (unsigned)(Cp / kQC));
+    size_t qsm = (size_t)parts * g.F * kQT * kQRow * sizeof(uint32_t);
+    // the patch loads reuse overlapping input rows through L1, which shares
+    // the SM's storage with these blocks' staging: the two-part F(4x4) form
+    // (37 KB) runs best at four blocks per SM (six measured 4% slower)
+    if (parts == 2 && M.m == 4 && qsm < 46 * 1024) qsm = 46 * 1024;
+    static bool qattr[16] = {false};
+    int qdev = 0;
+    WINO_CUDA_TRY(cudaGetDevice(&qdev));
+    if (qdev < 16 && !qattr[qdev]) {
+      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
+      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
+      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<6>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
+      qattr[qdev] = true;
     }
+    if (M.m == 2)
+      k_quant_input_tiled<2><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                         mode);
+    else if (M.m == 4)
+      k_quant_input_tiled<4><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                         mode);
+    else
+      k_quant_input_tiled<6><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                         mode);
     note_launches(3);
   }
   TcGemmArgs P;
