@@ -67,7 +67,7 @@ def lib():
             L.orc_wino_layer.argtypes = [fp, fp, fp] + [ctypes.c_int] * 7 + [dp] + [ctypes.c_int] * 3
             L.orc_wino_layer.restype = ctypes.c_int
             L.orc_wino_layer_tiles.argtypes = [fp, fp] + [ctypes.c_int] * 7 + [dp] + \
-                [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int64), fp]
+                [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int64), fp, ctypes.c_int]
             L.orc_wino_layer_tiles.restype = ctypes.c_int
             L.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             L.orc_splitmix64.restype = ctypes.c_uint64
@@ -207,9 +207,9 @@ def wino_layer(x, w, dim: int, pad: int, points, m: int, r: int, lowp: str = "f3
     return y
 
 
-def wino_layer_tiles(x, w, dim: int, pad: int, points, m: int, r: int, sel):
-    """Outputs of selected (tile, k) pairs of the FP32 layer: array
-    [n_sel][m] (1D) or [n_sel][m][m] (2D), uncropped."""
+def wino_layer_tiles(x, w, dim: int, pad: int, points, m: int, r: int, sel, lowp: str = "f32"):
+    """Outputs of selected (tile, k) pairs of the layer (wino_layer's
+    `lowp` modes): array [n_sel][m] (1D) or [n_sel][m][m] (2D), uncropped."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     w = np.ascontiguousarray(w, dtype=np.float32)
     pts = np.ascontiguousarray(points, dtype=np.float64)
@@ -223,7 +223,8 @@ def wino_layer_tiles(x, w, dim: int, pad: int, points, m: int, r: int, sel):
     out = np.zeros((sel.shape[0],) + ((m,) if dim == 1 else (m, m)), dtype=np.float32)
     st = lib().orc_wino_layer_tiles(_fp(x), _fp(w), dim, N, C, K, H, W, pad, _dp(pts), m, r,
                                     sel.shape[0],
-                                    sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _fp(out))
+                                    sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _fp(out),
+                                    LOWP[lowp])
     if st == -2:
         raise SingularPoints("coinciding finite points")
     if st < 0:

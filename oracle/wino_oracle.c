@@ -312,6 +312,51 @@ static float pow2_normaliser(double mx) {
   return (float)ldexp(1.0, -(e - 1));
 }
 
+/* One product of the contraction over channels, in the precision form
+ * `lowp` (0 FP32, 1 BF16, 2 FP16, 3 split BF16 x3, 4 split BF16 x6): u, v
+ * the FP32 transform outputs, sU, sV the frequency's power-of-two scales;
+ * accumulates into *acc (and, x6, the five small products into *acc_lo). */
+static void mac_lowp(int lowp, float u, float v, float sU, float sV, float* acc,
+                     float* acc_lo) {
+  if (lowp == 0) {
+    *acc = fmaf(u, v, *acc);
+  } else if (lowp == 1 || lowp == 2) {
+    float uq = round_mode(u * sU, lowp), vq = round_mode(v * sV, lowp);
+    *acc = fmaf(uq, vq, *acc);
+  } else if (lowp == 3) {
+    float us = u * sU, vs = v * sV;
+    float uh = orc_round_bf16(us), vh = orc_round_bf16(vs);
+    float ul = orc_round_bf16(us - uh), vl = orc_round_bf16(vs - vh);
+    *acc = fmaf(uh, vh, *acc);
+    *acc = fmaf(uh, vl, *acc);
+    *acc = fmaf(ul, vh, *acc);
+  } else {
+    /* three-part split: hi, mid = RN(a - hi), lo = RN((a - hi) - mid);
+       the differences are exact in FP32 */
+    float us = u * sU, vs = v * sV;
+    float uh = orc_round_bf16(us), vh = orc_round_bf16(vs);
+    float ur = us - uh, vr = vs - vh;
+    float um = orc_round_bf16(ur), vm = orc_round_bf16(vr);
+    float ul = orc_round_bf16(ur - um), vl = orc_round_bf16(vr - vm);
+    /* hh in one accumulator, the five smaller products (below 2^-7 of hh)
+       in a second one, added at the end */
+    *acc = fmaf(uh, vh, *acc);
+    *acc_lo = fmaf(uh, vm, *acc_lo);
+    *acc_lo = fmaf(um, vh, *acc_lo);
+    *acc_lo = fmaf(uh, vl, *acc_lo);
+    *acc_lo = fmaf(ul, vh, *acc_lo);
+    *acc_lo = fmaf(um, vm, *acc_lo);
+  }
+}
+
+/* The contraction's value M[f] from its accumulators: x6 adds the small
+ * products' accumulator, and the scales come off (exact: powers of two). */
+static float finish_lowp(int lowp, float acc, float acc_lo, float sU, float sV) {
+  if (lowp == 4) acc = acc + acc_lo;
+  if (lowp != 0) acc = acc / (sU * sV);
+  return acc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* FP32 Winograd layer.                                                      */
 /* ------------------------------------------------------------------------ */
@@ -444,41 +489,10 @@ int orc_wino_layer(const float* x, const float* w, float* y, int dim,
     for (int k = 0; k < K; ++k) {
       for (int f = 0; f < F; ++f) {
         float acc = 0.0f, acc_lo = 0.0f;  /* acc_lo: split x6's small products */
-        for (int c = 0; c < C; ++c) {
-          float u = U[((size_t)f * T + t) * C + c];
-          float v = V[((size_t)f * C + c) * K + k];
-          if (lowp == 0) {
-            acc = fmaf(u, v, acc);
-          } else if (lowp == 1 || lowp == 2) {
-            float uq = round_mode(u * sU[f], lowp), vq = round_mode(v * sV[f], lowp);
-            acc = fmaf(uq, vq, acc);
-          } else if (lowp == 3) {
-            float us = u * sU[f], vs = v * sV[f];
-            float uh = orc_round_bf16(us), vh = orc_round_bf16(vs);
-            float ul = orc_round_bf16(us - uh), vl = orc_round_bf16(vs - vh);
-            acc = fmaf(uh, vh, acc);
-            acc = fmaf(uh, vl, acc);
-            acc = fmaf(ul, vh, acc);
-          } else {
-            /* three-part split: hi, mid = RN(a - hi), lo = RN((a - hi) - mid);
-               the differences are exact in FP32 */
-            float us = u * sU[f], vs = v * sV[f];
-            float uh = orc_round_bf16(us), vh = orc_round_bf16(vs);
-            float ur = us - uh, vr = vs - vh;
-            float um = orc_round_bf16(ur), vm = orc_round_bf16(vr);
-            float ul = orc_round_bf16(ur - um), vl = orc_round_bf16(vr - vm);
-            /* hh in one accumulator, the five smaller products (below
-               2^-7 of hh) in a second one, added at the end */
-            acc = fmaf(uh, vh, acc);
-            acc_lo = fmaf(uh, vm, acc_lo);
-            acc_lo = fmaf(um, vh, acc_lo);
-            acc_lo = fmaf(uh, vl, acc_lo);
-            acc_lo = fmaf(ul, vh, acc_lo);
-            acc_lo = fmaf(um, vm, acc_lo);
-          }
-        }
-        if (lowp == 4) acc = acc + acc_lo;
-        if (lowp != 0) acc = acc / (sU[f] * sV[f]); /* exact: powers of two */
+        for (int c = 0; c < C; ++c)
+          mac_lowp(lowp, U[((size_t)f * T + t) * C + c], V[((size_t)f * C + c) * K + k], sU[f],
+                   sV[f], &acc, &acc_lo);
+        acc = finish_lowp(lowp, acc, acc_lo, sU[f], sV[f]);
         Mf[f] = acc;
       }
       if (dim == 1) {
@@ -1114,7 +1128,7 @@ static void input_one(int dim, int A, const float* BT, const float* d, float* ou
 
 int orc_wino_layer_tiles(const float* x, const float* w, int dim, int N, int C, int K, int H,
                          int W, int pad, const double* points, int m, int r, int n_sel,
-                         const int64_t* sel, float* out) {
+                         const int64_t* sel, float* out, int lowp) {
   const int A = m + r - 1;
   double ATd[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Gd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
   double BTd[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
@@ -1136,13 +1150,37 @@ int orc_wino_layer_tiles(const float* x, const float* w, int dim, int N, int C, 
   const int no = (dim == 1) ? m : m * m;
   float d[ORC_MAX_ALPHA * ORC_MAX_ALPHA], U[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
   float Vf[ORC_MAX_ALPHA * ORC_MAX_ALPHA], Mf[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  /* precision form: the scales of orc_wino_layer -- U's from the B^T row
+     norms, V's from max |V[f]| over every (c, k) of the layer */
+  float sU[ORC_MAX_ALPHA * ORC_MAX_ALPHA], sV[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+  for (int f = 0; f < F; ++f) { sU[f] = 1.0f; sV[f] = 1.0f; }
+  if (lowp != 0) {
+    double rown[ORC_MAX_ALPHA], vmax[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
+    for (int i = 0; i < A; ++i) {
+      double sr = 0.0;
+      for (int l = 0; l < A; ++l) sr += fabs((double)BT[i * A + l]);
+      rown[i] = sr;
+    }
+    for (int f = 0; f < F; ++f) vmax[f] = 0.0;
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < C; ++c) {
+        filter_one(dim, A, r, G, w + ((size_t)k * C + c) * rw, Vf);
+        for (int f = 0; f < F; ++f)
+          if (fabs((double)Vf[f]) > vmax[f]) vmax[f] = fabs((double)Vf[f]);
+      }
+    for (int f = 0; f < F; ++f) {
+      sU[f] = pow2_normaliser((dim == 1) ? rown[f] : rown[f / A] * rown[f % A]);
+      sV[f] = pow2_normaliser(vmax[f]);
+    }
+  }
+  float Ml[ORC_MAX_ALPHA * ORC_MAX_ALPHA];
   for (int s = 0; s < n_sel; ++s) {
     const int64_t t = sel[2 * s];
     const int k = (int)sel[2 * s + 1];
     const int n = (int)(t / ((int64_t)th * tw));
     const int ti = (int)((t / tw) % th), tj = (int)(t % tw);
     if (n < 0 || n >= N || k < 0 || k >= K) return -1;
-    for (int f = 0; f < F; ++f) Mf[f] = 0.0f;
+    for (int f = 0; f < F; ++f) Mf[f] = Ml[f] = 0.0f;
     for (int c = 0; c < C; ++c) {
       const int pr = (dim == 1) ? 1 : A;
       for (int i = 0; i < pr; ++i)
@@ -1155,8 +1193,9 @@ int orc_wino_layer_tiles(const float* x, const float* w, int dim, int N, int C, 
         }
       input_one(dim, A, BT, d, U);
       filter_one(dim, A, r, G, w + ((size_t)k * C + c) * rw, Vf);
-      for (int f = 0; f < F; ++f) Mf[f] = fmaf(U[f], Vf[f], Mf[f]);
+      for (int f = 0; f < F; ++f) mac_lowp(lowp, U[f], Vf[f], sU[f], sV[f], &Mf[f], &Ml[f]);
     }
+    for (int f = 0; f < F; ++f) Mf[f] = finish_lowp(lowp, Mf[f], Ml[f], sU[f], sV[f]);
     float* o = out + (size_t)s * no;
     if (dim == 1) {
       for (int j = 0; j < m; ++j) {

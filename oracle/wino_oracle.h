@@ -64,14 +64,15 @@ int orc_wino_layer(const float* x, const float* w, float* y, int dim,
                    int N, int C, int K, int H, int W, int pad,
                    const double* points, int m, int r, int lowp);
 
-/* The same FP32 layer evaluated only for selected (tile, k) pairs:
+/* The same layer evaluated only for selected (tile, k) pairs:
  * sel[2s] = linear tile index (n, tile row, tile column), sel[2s+1] = k;
  * out[s] receives the tile's m (1D) or m*m (2D) outputs, including those a
- * ragged tile crops.  FP32 contraction only.  Pinned by: equals
- * orc_wino_layer bit for bit on every tile of small layers.               */
+ * ragged tile crops; `lowp` is orc_wino_layer's (the scales are the whole
+ * layer's).  Pinned by: equals orc_wino_layer bit for bit on every tile of
+ * small layers, in every lowp mode.                                        */
 int orc_wino_layer_tiles(const float* x, const float* w, int dim, int N, int C, int K,
                          int H, int W, int pad, const double* points, int m, int r,
-                         int n_sel, const int64_t* sel, float* out);
+                         int n_sel, const int64_t* sel, float* out, int lowp);
 
 /* SplitMix64 (Steele, Lea, Flood 2014): the n-th output of the generator
  * whose state starts at `seed`.  Pinned by published output values.        */

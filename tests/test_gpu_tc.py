@@ -156,3 +156,61 @@ def test_tc_error_ordering_matches_precision(wino, orc):
         torch.cuda.synchronize()
         err[dt] = np.abs(y.cpu().numpy() - ref).sum() / np.abs(ref).sum()
     assert err["bf16"] > err["fp16"] > err["split_bf16x3"] > err["f32"] >= err["split_bf16x6"]
+
+
+def _sample_bound(orc, x, w, pts, m, sel, dtype):
+    """The per-output bound of the module docstring for sampled (tile, k)
+    pairs of a full layer: [n_sel][m][m]."""
+    AT, G, BT = orc.make_matrices(pts, m, 3)
+    N, C, H, W = x.shape
+    a = m + 2
+    th, tw = -(-H // m), -(-W // m)
+    n_terms = PRODUCTS[dtype] * C + (1 if dtype == "split_bf16x6" else 0)
+    fac = (1.1 * (_gamma(n_terms, 2.0 ** -24) + _gamma(n_terms, 2.0 ** -23))
+           + 2 * _gamma(2 * a, 2.0 ** -24))
+    out = np.empty((len(sel), m, m))
+    for s, (t, k) in enumerate(sel):
+        n, ti, tj = t // (th * tw), (t // tw) % th, t % tw
+        d = np.zeros((C, a, a))
+        h0, w0 = ti * m - 1, tj * m - 1
+        hs, ws = max(h0, 0), max(w0, 0)
+        he, we = min(h0 + a, H), min(w0 + a, W)
+        d[:, hs - h0:he - h0, ws - w0:we - w0] = x[n, :, hs:he, ws:we]
+        U = np.einsum("il,clq,jq->cij", BT, d, BT)
+        V = np.einsum("ip,cpq,jq->cij", G, w[k].astype(np.float64), G)
+        S = (np.abs(U) * np.abs(V)).sum(axis=0)
+        out[s] = fac * (np.abs(AT) @ S @ np.abs(AT).T)
+    return out
+
+
+@pytest.mark.parametrize("layer", [0, 3])
+def test_tc_vgg_full_size_sampled(wino, orc, layer):
+    """The bench's configuration (VGG16 stage, N = 32, the bench's points)
+    for every tensor-core dtype and both tile sizes: 256 random (tile, k)
+    outputs recomputed by the oracle's emulation of the same rounding agree
+    within the derived per-output bound."""
+    import torch
+    C, H = inputs.VGG16_LAYERS[layer]
+    x, w = inputs.vgg_layer_host(C, H, N=inputs.VGG_BATCH, seed=5 + layer)
+    xt, wt = torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda()
+    y = torch.empty((inputs.VGG_BATCH, C, H, H), device="cuda")
+    for m in (4, 6):
+        th = -(-H // m)
+        T = inputs.VGG_BATCH * th * th
+        rng = np.random.default_rng(100 * layer + m)
+        sel = np.stack([rng.integers(0, T, 256), rng.integers(0, C, 256)], axis=1)
+        for dtype in PRODUCTS:
+            y.fill_(float("nan"))
+            wino.wino_conv2d(xt, wt, y, PTS[m], m, 3, 1, dtype)
+            torch.cuda.synchronize()
+            yh = y.cpu().numpy()
+            out = orc.wino_layer_tiles(x, w, 2, 1, PTS[m], m, 3, sel, dtype)
+            bound = _sample_bound(orc, x, w, PTS[m], m, sel, dtype)
+            for s, (t, k) in enumerate(sel):
+                nn, ti, tj = t // (th * th), (t // th) % th, t % th
+                for a in range(m):
+                    for b in range(m):
+                        p, q = ti * m + a, tj * m + b
+                        if p < H and q < H:
+                            diff = abs(float(yh[nn, k, p, q]) - float(out[s, a, b]))
+                            assert diff <= bound[s, a, b], (m, dtype, t, k, a, b, diff)

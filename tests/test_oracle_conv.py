@@ -227,9 +227,11 @@ def test_split_bf16x6_error_not_above_fp32(orc, C, H, m):
 
 
 @pytest.mark.parametrize("dim,m", [(2, 2), (2, 4), (2, 6), (1, 4)])
-def test_layer_tiles_equals_layer(orc, dim, m):
+@pytest.mark.parametrize("lowp", ["f32", "bf16", "fp16", "split_bf16x3", "split_bf16x6"])
+def test_layer_tiles_equals_layer(orc, dim, m, lowp):
     """The per-tile oracle entry reproduces the full layer bit for bit on
-    every (tile, k) of a small ragged layer."""
+    every (tile, k) of a small ragged layer, in every precision mode (the
+    per-tile scales are the whole layer's)."""
     rng = np.random.default_rng(20 + m)
     c = 1.7
     pts = [0.0, -1 / c, -c, c, 1 / c, -1.0, 1.0][: m + 1] + [math.inf]
@@ -239,12 +241,12 @@ def test_layer_tiles_equals_layer(orc, dim, m):
     else:
         x = rng.uniform(-1, 1, (2, 3, 19)).astype(np.float32)
         w = rng.uniform(-1, 1, (4, 3, 3)).astype(np.float32)
-    y = orc.wino_layer(x, w, dim, 1, pts, m, 3)
+    y = orc.wino_layer(x, w, dim, 1, pts, m, 3, lowp)
     Ho = 1 if dim == 1 else y.shape[2]
     Wo = y.shape[-1]
     th, tw = (1 if dim == 1 else -(-Ho // m)), -(-Wo // m)
     sel = [(t, k) for t in range(2 * th * tw) for k in range(4)]
-    out = orc.wino_layer_tiles(x, w, dim, 1, pts, m, 3, sel)
+    out = orc.wino_layer_tiles(x, w, dim, 1, pts, m, 3, sel, lowp)
     for (t, k), o in zip(sel, out):
         n, ti, tj = t // (th * tw), (t // tw) % th, t % tw
         if dim == 1:
