@@ -976,6 +976,13 @@ NCU_TRAFFIC = {
     # k_tc_gemm split-BF16x6, C = K = 64, 224x224, N = 8: three 16-bit parts
     # of U and V read, M written (FP32)
     "tc_gemm": (538.43e6, 36 * (2 * 3 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
+    # k_input_transform_blk F(4x4), C = 64, 224x224, N = 8: x read, U written
+    "input_transform": (285.9e6, 334.0e6),
+    # k_quant_input_tiled split-BF16x6 F(4x4), C = 64, 224x224, N = 8: x read,
+    # three 16-bit parts of U written (the filter kernels' bytes are small)
+    "tc_transform": (389.7e6, 449.6e6),
+    # k_output_transform_r3 F(4x4), K = 64, 224x224, N = 8: M read, y written
+    "output_transform": (300.7e6, 334.0e6),
 }
 
 
@@ -988,8 +995,16 @@ def kernel_traffic(kernel, ctx, per_step):
     L = ctx.layers
     if kernel == "fused_layer":
         b = sum(fp32_layer_bytes(ctx, m, C, H) for m, _ in ctx.stacks("f32") for C, H in L)
-    else:
+    elif kernel == "tc_gemm":
         b = sum(tc_gemm_bytes(ctx, m, dt, C, H) for m, dt in ctx.stacks("tc") for C, H in L)
+    elif kernel == "input_transform":
+        b = sum(4.0 * (ctx.N * C * H * H + (m + 2) ** 2 * C * _tiles(m, H, ctx.N))
+                for m, _ in ctx.stacks("f32") for C, H in L)
+    elif kernel == "tc_transform":
+        b = sum(tc_transform_bytes(ctx, m, dt, C, H) for m, dt in ctx.stacks("tc") for C, H in L)
+    else:  # output_transform
+        b = sum(4.0 * ((m + 2) ** 2 * _tiles(m, H, ctx.N) * C + ctx.N * C * H * H)
+                for m, dt in ctx.stacks("tc") for C, H in L)
     return meas / alg * b / per_step
 
 
