@@ -350,7 +350,7 @@ enum {
   WINO_SWEEP_AUTO = 0,         /* time the modes below once, keep the best */
   WINO_SWEEP_PERSISTENT = 1,   /* one persistent launch, LPT work queue    */
   WINO_SWEEP_PERSISTENT3 = 2,  /* same, 3 CTAs/SM (register-capped)        */
-  WINO_SWEEP_PER_SIZE = 3      /* one launch per size                      */
+  WINO_SWEEP_PER_SIZE = 3      /* one launch per size, sizes on 3 streams  */
 };
 
 /* Builds a plan evaluating every instance with `trials` trials of `seed`

@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "../../include/wino.h"
@@ -223,6 +224,36 @@ static MaskList valid_masks(const SweepSize& s, const unsigned char* subsets, in
   return L;
 }
 
+// Auxiliary streams of the per-size sweep (per device, created on first
+// use): the sizes' evaluation launches are spread over them so that one
+// size's last, partly filled wave overlaps the next size's work; the
+// caller's stream forks to them after the trial records and joins them
+// before the results are copied.
+constexpr int kSweepStreams = 3;
+static int sweep_streams(cudaStream_t** aux, cudaEvent_t** ev) {
+  static cudaStream_t streams[16][kSweepStreams];
+  static cudaEvent_t events[16][kSweepStreams + 1];
+  static bool made[16] = {false};
+  static std::mutex mu;
+  int dev = 0;
+  WINO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 16) {
+    set_error("device index out of range");
+    return WINO_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!made[dev]) {
+    for (int i = 0; i < kSweepStreams; ++i)
+      WINO_CUDA_TRY(cudaStreamCreateWithFlags(&streams[dev][i], cudaStreamNonBlocking));
+    for (int i = 0; i <= kSweepStreams; ++i)
+      WINO_CUDA_TRY(cudaEventCreateWithFlags(&events[dev][i], cudaEventDisableTiming));
+    made[dev] = true;
+  }
+  *aux = streams[dev];
+  *ev = events[dev];
+  return WINO_OK;
+}
+
 int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_sizes,
                 const unsigned char* subsets, int n_subsets, int trials, unsigned long long seed,
                 int order, double* err_out, cudaStream_t st) {
@@ -245,6 +276,26 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   std::vector<int> split(n_sizes, 1);
   const int nblk = (n_c + 31) / 32;
   const int n_chunks = trial_chunks(trials);
+  // sizes to auxiliary streams, longest first to the least loaded (the
+  // sizes of one stream run in order, so they can share a chunk buffer)
+  std::vector<int> lane(n_sizes, 0), by_cost(n_sizes);
+  {
+    std::vector<double> cost(n_sizes), load(kSweepStreams, 0.0);
+    for (int s = 0; s < n_sizes; ++s) {
+      by_cost[s] = s;
+      cost[s] = sweep_trial_flops(sizes[s].dim, sizes[s].m, sizes[s].r) *
+                valid_masks(sizes[s], subsets, n_subsets).n;
+    }
+    std::stable_sort(by_cost.begin(), by_cost.end(),
+                     [&](int a, int b2) { return cost[a] > cost[b2]; });
+    for (int s : by_cost) {
+      int l = 0;
+      for (int i = 1; i < kSweepStreams; ++i)
+        if (load[i] < load[l]) l = i;
+      lane[s] = l;
+      load[l] += cost[s];
+    }
+  }
   size_t n_part = 0;
   for (int s = 0; s < n_sizes; ++s) {
     ml[s] = valid_masks(sizes[s], subsets, n_subsets);
@@ -266,7 +317,7 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
   off_err = (off_err + 255) & ~(size_t)255;
   size_t off_chunk = off_err + n_err * sizeof(double);
   off_chunk = (off_chunk + 255) & ~(size_t)255;
-  const size_t total = off_chunk + n_part * sizeof(double);
+  const size_t total = off_chunk + (size_t)kSweepStreams * n_part * sizeof(double);
   void* base = nullptr;
   int rc = scratch_get(kScratchSweep, total, &base);
   if (rc != WINO_OK) return rc;
@@ -284,37 +335,53 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
                        sizes[s].m, sizes[s].r, trials, seed, st);
     if (rc != WINO_OK) return rc;
   }
-  for (int s = 0; s < n_sizes; ++s) {
-    if (ml[s].n == 0) continue;
-    const int64_t n_out = (int64_t)n_subsets * n_c;
-    const int ch_per = (n_chunks + split[s] - 1) / split[s];
-    const int sp = (n_chunks + ch_per - 1) / ch_per;  // groups actually holding chunks
-    const int64_t warps = (int64_t)ml[s].n * nblk * (split[s] > 1 ? sp : 1);
-    const int warps_per_block = 4;
-    const unsigned grid = (unsigned)((warps + warps_per_block - 1) / warps_per_block);
-    double* es = err + (size_t)s * n_out;
-    // the Huffman orders, and the wide sizes in any order: one warp per
-    // instance (sweep_order.cuh)
-    if (order != 0 || sweep_wide(sizes[s].dim, sizes[s].m, sizes[s].r)) {
-      ProfScope ps(order != 0 ? kKSweepOrder : kKSweepEval, st);
-      rc = order_sweep_launch(order, sizes[s], rec + rec_off[s], trials, cg, n_c, ml[s],
-                              ysum + s, es, st);
-      if (rc != WINO_OK) return rc;
-      continue;
-    }
-    EvalFn fn = eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r);
-    {
-      ProfScope ps(kKSweepEval, st);
-      fn<<<grid, 32 * warps_per_block, 0, st>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
-                                                 ml[s], ysum + s, es, split[s] > 1 ? sp : 1,
-                                                 ch_per, chunk, n_out);
+  cudaStream_t* aux = nullptr;
+  cudaEvent_t* ev = nullptr;
+  rc = sweep_streams(&aux, &ev);
+  if (rc != WINO_OK) return rc;
+  {
+    // profiled as one phase, fork to join (its launches overlap)
+    ProfScope ps(order != 0 ? kKSweepOrder : kKSweepEval, st);
+    WINO_CUDA_TRY(cudaEventRecord(ev[kSweepStreams], st));
+    for (int i = 0; i < kSweepStreams; ++i)
+      WINO_CUDA_TRY(cudaStreamWaitEvent(aux[i], ev[kSweepStreams], 0));
+    for (int s : by_cost) {
+      if (ml[s].n == 0) continue;
+      const cudaStream_t st_s = aux[lane[s]];
+      double* chunk_s = chunk + (size_t)lane[s] * n_part;
+      const int64_t n_out = (int64_t)n_subsets * n_c;
+      const int ch_per = (n_chunks + split[s] - 1) / split[s];
+      const int sp = (n_chunks + ch_per - 1) / ch_per;  // groups actually holding chunks
+      const int64_t warps = (int64_t)ml[s].n * nblk * (split[s] > 1 ? sp : 1);
+      const int warps_per_block = 4;
+      const unsigned grid = (unsigned)((warps + warps_per_block - 1) / warps_per_block);
+      double* es = err + (size_t)s * n_out;
+      // the Huffman orders, and the wide sizes in any order: one warp per
+      // instance (sweep_order.cuh)
+      if (order != 0 || sweep_wide(sizes[s].dim, sizes[s].m, sizes[s].r)) {
+        rc = order_sweep_launch(order, sizes[s], rec + rec_off[s], trials, cg, n_c, ml[s],
+                                ysum + s, es, st_s);
+        if (rc != WINO_OK) break;
+        continue;
+      }
+      EvalFn fn = eval_kernel(sizes[s].dim, sizes[s].m, sizes[s].r);
+      fn<<<grid, 32 * warps_per_block, 0, st_s>>>(rec + rec_off[s], trials, cg, n_c, sizes[s].d,
+                                                   ml[s], ysum + s, es, split[s] > 1 ? sp : 1,
+                                                   ch_per, chunk_s, n_out);
       note_launches(1);
+      if (split[s] > 1) {
+        rc = sweep_combine(chunk_s, n_chunks, n_out, n_out, nullptr, ysum + s, es, st_s);
+        if (rc != WINO_OK) break;
+      }
     }
-    if (split[s] > 1) {
-      rc = sweep_combine(chunk, n_chunks, n_out, n_out, nullptr, ysum + s, es, st);
-      if (rc != WINO_OK) return rc;
+    // join (also after a failed launch): the caller's stream waits for every
+    // auxiliary stream
+    for (int i = 0; i < kSweepStreams; ++i) {
+      WINO_CUDA_TRY(cudaEventRecord(ev[i], aux[i]));
+      WINO_CUDA_TRY(cudaStreamWaitEvent(st, ev[i], 0));
     }
   }
+  if (rc != WINO_OK) return rc;
   WINO_CUDA_TRY(cudaGetLastError());
   WINO_CUDA_TRY(
       cudaMemcpyAsync(err_out, err, n_err * sizeof(double), cudaMemcpyDeviceToHost, st));

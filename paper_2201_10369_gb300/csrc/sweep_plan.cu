@@ -21,7 +21,11 @@
 //   WINO_SWEEP_PERSISTENT   persistent kernel, 2 CTAs x 4 warps per SM
 //   WINO_SWEEP_PERSISTENT3  persistent kernel limited to 168 registers,
 //                           3 CTAs x 4 warps per SM
-//   WINO_SWEEP_PER_SIZE     one grid launch per size over its items
+//   WINO_SWEEP_PER_SIZE     one grid launch per size over its items, the
+//                           sizes spread over three streams (forked from
+//                           and joined back to the plan's stream by
+//                           events), so one size's last wave overlaps
+//                           the next size's launch
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -188,6 +192,12 @@ struct SweepPlan {
   std::vector<int64_t> rec_off;
   int grid = 0;
   cudaStream_t st = nullptr;
+  // per-size mode: the streams the sizes run on, each size's stream, and
+  // the fork (kPlanLanes) and join events
+  static constexpr int kPlanLanes = 3;
+  cudaStream_t lane_st[kPlanLanes] = {};
+  cudaEvent_t lane_ev[kPlanLanes + 1] = {};
+  std::vector<int> lane;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
 };
@@ -197,6 +207,10 @@ static void plan_free(SweepPlan* p) {
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->st) cudaStreamDestroy(p->st);
+  for (int i = 0; i < SweepPlan::kPlanLanes; ++i)
+    if (p->lane_st[i]) cudaStreamDestroy(p->lane_st[i]);
+  for (int i = 0; i <= SweepPlan::kPlanLanes; ++i)
+    if (p->lane_ev[i]) cudaEventDestroy(p->lane_ev[i]);
   if (p->dbuf) cudaFree(p->dbuf);
   if (p->err_h) cudaFreeHost(p->err_h);
   if (p->status_h) cudaFreeHost(p->status_h);
@@ -221,11 +235,20 @@ static int plan_enqueue(SweepPlan* p, int mode, cudaStream_t st) {
   if (!p->items.empty()) {
     ProfScope ps(kKSweepEval, st);
     if (mode == WINO_SWEEP_PER_SIZE) {
+      constexpr int L = SweepPlan::kPlanLanes;
+      WINO_CUDA_TRY(cudaEventRecord(p->lane_ev[L], st));
+      for (int i = 0; i < L; ++i) WINO_CUDA_TRY(cudaStreamWaitEvent(p->lane_st[i], p->lane_ev[L], 0));
       for (int s = 0; s < p->n_sizes; ++s) {
         if (p->size_count[s] == 0) continue;
         ItemsFn fn = items_kernel(p->kind[s]);
-        fn<<<(p->size_count[s] + 3) / 4, 128, 0, st>>>(p->P, p->size_first[s], p->size_count[s]);
+        fn<<<(p->size_count[s] + 3) / 4, 128, 0, p->lane_st[p->lane[s]]>>>(
+            p->P, p->size_first[s], p->size_count[s]);
         note_launches(1);
+      }
+      WINO_CUDA_TRY(cudaGetLastError());
+      for (int i = 0; i < L; ++i) {
+        WINO_CUDA_TRY(cudaEventRecord(p->lane_ev[i], p->lane_st[i]));
+        WINO_CUDA_TRY(cudaStreamWaitEvent(st, p->lane_ev[i], 0));
       }
     } else if (mode == WINO_SWEEP_PERSISTENT3) {
       k_sweep_persistent<3><<<p->grid, 128, 0, st>>>(p->P);
@@ -436,6 +459,26 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
     p->size_count[p->items[i].size]++;
   }
   const int64_t n_sorted = (int64_t)p->order.size();
+  // per-size mode: sizes to streams, costliest first to the least loaded
+  {
+    std::vector<double> cost(n_sizes), load(SweepPlan::kPlanLanes, 0.0);
+    std::vector<int> by_cost(n_sizes);
+    for (int s = 0; s < n_sizes; ++s) {
+      by_cost[s] = s;
+      cost[s] = sweep_trial_flops(p->sizes[s].dim, p->sizes[s].m, p->sizes[s].r) *
+                p->size_count[s];
+    }
+    std::stable_sort(by_cost.begin(), by_cost.end(),
+                     [&](int x, int y) { return cost[x] > cost[y]; });
+    p->lane.assign(n_sizes, 0);
+    for (int s : by_cost) {
+      int l = 0;
+      for (int k = 1; k < SweepPlan::kPlanLanes; ++k)
+        if (load[k] < load[l]) l = k;
+      p->lane[s] = l;
+      load[l] += cost[s];
+    }
+  }
 
   // device buffers: records | partials | ysum | rec_off | kind | dval | c |
   // mask | err | items | counter | status | deadline
@@ -519,6 +562,10 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   if (e == cudaSuccess)
     e = cudaHostAlloc((void**)&p->deadline_h, sizeof(unsigned long long), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking);
+  for (int i = 0; i < SweepPlan::kPlanLanes && e == cudaSuccess; ++i)
+    e = cudaStreamCreateWithFlags(&p->lane_st[i], cudaStreamNonBlocking);
+  for (int i = 0; i <= SweepPlan::kPlanLanes && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&p->lane_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     rc = cuda_fail(e, "sweep plan setup");
     plan_free(p);
