@@ -308,9 +308,9 @@ static int plan_capture(SweepPlan* p) {
   return WINO_OK;
 }
 
-// Autotuner: times each mode on the plan itself (eagerly, best of 2 after a
-// warm-up) and keeps the fastest; results are cached per plan signature for
-// the life of the process.
+// Autotuner: captures each mode and times its graph replays on the plan
+// itself (best of 2 after a warm-up), keeps the fastest; results are cached
+// per plan signature for the life of the process.
 static std::mutex g_tune_mu;
 static std::map<std::string, int> g_tune_cache;
 
@@ -338,12 +338,13 @@ static int plan_autotune(SweepPlan* p) {
   float best = 1e30f;
   int best_mode = WINO_SWEEP_PERSISTENT;
   for (int mi = 0; mi < 3; ++mi) {
-    p->grid = plan_grid(modes[mi]);
+    p->mode = modes[mi];
+    int rc = plan_capture(p);
+    if (rc != WINO_OK) return rc;
     float t_best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       WINO_CUDA_TRY(cudaEventRecord(a, p->st));
-      int rc = plan_enqueue(p, modes[mi], p->st);
-      if (rc != WINO_OK) return rc;
+      WINO_CUDA_TRY(cudaGraphLaunch(p->exec, p->st));
       WINO_CUDA_TRY(cudaEventRecord(b, p->st));
       WINO_CUDA_TRY(cudaEventSynchronize(b));
       float ms = 0.0f;

@@ -25,7 +25,7 @@
 //
 // Pipeline: filter transform (FP32) -> per-frequency max |V| -> V rounded
 // into the blocked image of [F][K][Cp] (K-major B operand); input transform
-// (FP32) rounded into the blocked image of [F][Tp][Cp] (K-major A operand);
+// (FP32) rounded into the blocked image of [F][Tp][Cp] (MN-major A operand);
 // k_tc_gemm; the general output transform.
 // k_tc_gemm: one CTA = one frequency x 128 tiles (MMA M) x NB output
 // channels (MMA N <= 256), contraction over Cp in chunks of 64 channels
@@ -47,6 +47,7 @@
 #include "../../include/wino.h"
 #include "async_copy.cuh"
 #include "common.cuh"
+#include "packed.cuh"
 
 namespace wino {
 
@@ -56,16 +57,23 @@ constexpr int kTcKc = 64;    // channels per chunk: one 128-byte row per operand
 // Operand parts in HBM are the shared-memory images the contraction copies
 // whole (one bulk copy per operand part and chunk): U per (frequency,
 // 128-tile block, 64-channel chunk) one 16 KB block, V per (frequency,
-// NB-channel k block, chunk) one NB x 128-byte block.  Row r of a block (a
-// tile, an output channel) is 128 bytes at r x 128, its 16-byte piece j (8
-// channels) at position j ^ (r & 7): the 128-byte swizzle the MMA's K-major
-// operand descriptors name.  Element index of (f, tile t, channel c) in a U
-// part, and of (f, output channel k, c) in a V part:
+// NB-channel k block, chunk) one NB x 128-byte block.
+// U is the MMA's A operand in MN-major form (tiles contiguous): the block is
+// 16 atoms of 1024 bytes, atom (g, a) at (2 g + a) x 1024 holding channels
+// 8 g .. 8 g + 7 (rows r = c % 8, 128 bytes each) of tiles 64 a .. 64 a + 63;
+// the 16-byte piece j (8 tiles) of row r sits at position j ^ r (the
+// 128-byte swizzle).  Atoms along the tiles are 1024 bytes apart (the
+// descriptor's leading byte offset), groups of 8 channels 2048 bytes (its
+// stride byte offset).  V is the B operand in K-major form: row r of a block
+// (an output channel) is 128 bytes at r x 128, its piece j (8 channels) at
+// position j ^ (r & 7).  Element index of (f, tile t, channel c) in a U part,
+// and of (f, output channel k, c) in a V part:
 __host__ __device__ __forceinline__ int64_t tc_u_index(int f, int64_t t, int c, int64_t ntb,
                                                        int nch) {
   const int64_t blk = ((int64_t)f * ntb + t / kTcM) * nch + c / kTcKc;
-  const int r = (int)(t % kTcM), j = (c % kTcKc) / 8;
-  return blk * (kTcM * kTcKc) + r * kTcKc + ((j ^ (r & 7)) * 8) + (c % 8);
+  const int tl = (int)(t % kTcM), cl = c % kTcKc;
+  const int r = cl % 8, j = (tl % 64) / 8;
+  return blk * (kTcM * kTcKc) + (((cl / 8) * 2 + tl / 64) * 8 + r) * 64 + ((j ^ r) * 8) + (tl % 8);
 }
 __host__ __device__ __forceinline__ int64_t tc_v_index(int f, int k, int c, int NB, int nkb,
                                                        int nch) {
@@ -212,148 +220,298 @@ __global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ 
 }
 
 // Input transform (FP32, the FP32 layer's order) -> operand parts
-// U0/U1/U2 [f][t][c], scaled; rows t >= T and columns c >= C are zero.
-// One block = kQT = 4 tiles x 64 channels; a thread transforms two adjacent
-// channels of one tile (tiles fastest: neighbouring patches share input
-// rows).  The 16-bit results are staged in shared memory as 32-bit channel
-// pairs -- rows of kQRow = 32 pairs, pair p of tile tl's row at word
-// p ^ 8 tl, so the 32 stores of a warp (4 tiles x 8 pairs) hit 32 distinct
-// banks with no padding -- and leave as whole 128-byte rows of 64 channels
-// (one cache line per (f, tile) and part).  (Rows padded to 40 words
-// instead held one F(6x6) split-BF16x6 block per SM, not two.)
-// (Splitting the transform's rows over 2-4 blocks, for staging within 36 KB
-// and five blocks per SM, measured 8-15% slower per stack: every block
-// loads the whole patch, and the patch loads are what this kernel waits on.
-// Issuing both channels' patch loads before either transform measured the
-// same for the split forms and 3% slower for BF16: 122 registers instead
-// of 80.)
-constexpr int kQT = 4, kQC = 64, kQP = kQC / 2, kQRow = kQP;
-// staging word of channel pair p in tile tl's row (bank-conflict swizzle)
-__device__ __forceinline__ int qswz(int p, int tl) { return p ^ (tl << 3); }
-constexpr int kQuantThreads = kQT * kQP;
-// largest staging: three parts of F = 64 frequencies (m = 6)
-constexpr int kQuantSmemMax = 3 * 64 * kQT * kQRow * 4;
+// U0/U1/U2, scaled, in the MN-major image of tc_u_index; rows t >= T and
+// channels c >= C are zero.  A warp takes one channel of 64 consecutive
+// tiles (F(2x2), F(4x4): two adjacent tiles per lane) or 32 (F(6x6): one per
+// lane), so that its patch loads run along the input rows (F(4x4): a lane's
+// two patches are one 16-byte-aligned run of ten columns per row, loaded as
+// two 16-byte vectors and two scalars) and its results for one frequency
+// and part are one contiguous run of the image: 128 bytes (a whole line,
+// two tiles' 16-bit values in each 32-bit store) or 64 bytes.  Nothing is
+// staged in shared memory.  Launch: grid (Tp / 64, Cp / 8) blocks of 256
+// threads for F(2x2) and F(4x4), (Tp / 64, Cp / 4) for F(6x6).
+constexpr int kQuantThreads = 256;
 
-// B^T d B of the tile patch of channel c (zeros when the tile or the channel
-// is out of range), rows i in [I0, I1) of the result only: frequency f =
-// i alpha + j at out(f, v).  Each value is computed exactly as by the whole
-// transform (the row restriction only skips rows).
-template <int MM, int I0, int I1, class Out>
-__device__ __forceinline__ void quant_patch(const float* __restrict__ x, const LayerGeom& g,
-                                            const LayerMats& Mx, int64_t t, int c, Out out) {
-  constexpr int A = MM + 2;
-  float d[A][A];
-  const bool live = t < g.T && c < g.C;
-  if (live) {
-    const int tpi = g.th * g.tw;
-    const int n = (int)(t / tpi);
-    const int rem = (int)(t - (int64_t)n * tpi);
-    const int ti = rem / g.tw, tj = rem - (rem / g.tw) * g.tw;
-    const int h0 = ti * MM - g.pad, w0 = tj * MM - g.pad;
-    const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
+// B^T d B of one patch, FP32 in the layer's order (column transforms B^T d,
+// then the rows times B; every sum from zero with fmaf, inner index
+// ascending), frequency f = i alpha + j at out(f, v).  The column
+// transforms overwrite d, one column at a time.
+template <int A, class Out>
+__device__ __forceinline__ void bt_d_b(float (&d)[A][A], const LayerMats& Mx, Out out) {
 #pragma unroll
-    for (int i = 0; i < A; ++i)
+  for (int l = 0; l < A; ++l) {
+    float col[A];
 #pragma unroll
-      for (int j = 0; j < A; ++j) {
-        const int hh = h0 + i, ww = w0 + j;
-        d[i][j] = ((unsigned)hh < (unsigned)g.H && (unsigned)ww < (unsigned)g.W)
-                      ? __ldg(xc + (int64_t)hh * g.W + ww)
-                      : 0.0f;
-      }
-  } else {
-#pragma unroll
-    for (int i = 0; i < A; ++i)
-#pragma unroll
-      for (int j = 0; j < A; ++j) d[i][j] = 0.0f;
-  }
-  float tm[I1 - I0][A];
-#pragma unroll
-  for (int i = I0; i < I1; ++i)
-#pragma unroll
-    for (int l = 0; l < A; ++l) {
+    for (int i = 0; i < A; ++i) {
       float acc = 0.0f;
 #pragma unroll
       for (int q = 0; q < A; ++q) acc = fmaf(Mx.BT[i * A + q], d[q][l], acc);
-      tm[i - I0][l] = acc;
+      col[i] = acc;
     }
 #pragma unroll
-  for (int i = I0; i < I1; ++i)
+    for (int i = 0; i < A; ++i) d[i][l] = col[i];
+  }
+#pragma unroll
+  for (int i = 0; i < A; ++i)
 #pragma unroll
     for (int j = 0; j < A; ++j) {
       float acc = 0.0f;
 #pragma unroll
-      for (int l = 0; l < A; ++l) acc = fmaf(tm[i - I0][l], Mx.BT[j * A + l], acc);
-      out(i * A + j, live ? acc : 0.0f);
+      for (int l = 0; l < A; ++l) acc = fmaf(d[i][l], Mx.BT[j * A + l], acc);
+      out(i * A + j, acc);
     }
 }
 
-// Rows [I0, I1) of two adjacent channels' transforms, scaled, split and
-// staged as 32-bit channel pairs (channel c in the low half).
-template <int MM, int I0, int I1>
-__device__ __forceinline__ void quant_pair_rows(const float* __restrict__ x, const LayerGeom& g,
-                                                const LayerMats& Mx, const TcScales& S,
-                                                int64_t t, int c, int tl, int cp, int mode,
-                                                int parts, uint32_t* qs, int kPart) {
-  constexpr int A = MM + 2, NR = (I1 - I0) * A;
-  float ua[NR];
-  quant_patch<MM, I0, I1>(x, g, Mx, t, c, [&](int f, float v) { ua[f - I0 * A] = v; });
-  quant_patch<MM, I0, I1>(x, g, Mx, t, c + 1, [&](int f, float v) {
-    uint16_t qa[3], qb[3];
-    split_parts(ua[f - I0 * A] * S.sU[f], mode, qa);
-    split_parts(v * S.sU[f], mode, qb);
-    const int o = (f * kQT + tl) * kQRow + qswz(cp, tl);
-    qs[o] = (uint32_t)qa[0] | ((uint32_t)qb[0] << 16);
-    if (parts > 1) qs[kPart + o] = (uint32_t)qa[1] | ((uint32_t)qb[1] << 16);
-    if (parts > 2) qs[2 * kPart + o] = (uint32_t)qa[2] | ((uint32_t)qb[2] << 16);
-  });
+// The alpha x alpha input patch of tile t, channel c: zero outside the
+// image, and all zero for t >= T or c >= C.
+template <int MM>
+__device__ __forceinline__ void load_patch(const float* __restrict__ x, const LayerGeom& g,
+                                           int64_t t, int c, float (&d)[MM + 2][MM + 2]) {
+  constexpr int A = MM + 2;
+#pragma unroll
+  for (int i = 0; i < A; ++i)
+#pragma unroll
+    for (int j = 0; j < A; ++j) d[i][j] = 0.0f;
+  if (t >= g.T || c >= g.C) return;
+  const int tpi = g.th * g.tw;
+  const int n = (int)(t / tpi);
+  const int rem = (int)(t - (int64_t)n * tpi);
+  const int ti = rem / g.tw, tj = rem - ti * g.tw;
+  const int h0 = ti * MM - g.pad, w0 = tj * MM - g.pad;
+  const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
+  // F(6x6) inside the row (pad 1, even W, 8-byte aligned rows): three
+  // 8-byte vectors and two scalars per row
+  const bool vec2 = MM == 6 && g.pad == 1 && (g.W & 1) == 0 && (((uintptr_t)x) & 7) == 0 &&
+                    w0 + A - 2 < g.W;
+#pragma unroll
+  for (int i = 0; i < A; ++i) {
+    const int hh = h0 + i;
+    if ((unsigned)hh >= (unsigned)g.H) continue;
+    const float* row = xc + (int64_t)hh * g.W;
+    if (vec2) {
+      const float2* r2 = reinterpret_cast<const float2*>(row + w0 + 1);
+#pragma unroll
+      for (int v = 0; v < (A - 2) / 2; ++v) {
+        const float2 p = __ldg(r2 + v);
+        d[i][1 + 2 * v] = p.x;
+        d[i][2 + 2 * v] = p.y;
+      }
+      if (w0 >= 0) d[i][0] = __ldg(row + w0);
+      if (w0 + A - 1 < g.W) d[i][A - 1] = __ldg(row + w0 + A - 1);
+    } else {
+#pragma unroll
+      for (int j = 0; j < A; ++j) {
+        const int ww = w0 + j;
+        if ((unsigned)ww < (unsigned)g.W) d[i][j] = __ldg(row + ww);
+      }
+    }
+  }
+}
+
+// 32 bytes of x (8 floats, 32-byte aligned) in one load.
+__device__ __forceinline__ void ldg8(const float* p, float (&v)[8]) {
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                 "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+
+// F(4x4) tile pairs, W a multiple of 8 and x 32-byte aligned: a tile row
+// has an even number of tiles (and T is even), so the lane's two tiles t, t
+// + 1 (t even) share a tile row and start at an even tj.  Per input row the
+// lane loads columns 4 tj .. 4 tj + 7 as one 32-byte vector (the warp: one
+// contiguous run); column 4 tj - 1 is column 7 of lane q - 1 and column
+// 4 tj + 8 column 0 of lane q + 1 whenever those columns are inside the row
+// (the neighbours hold the adjacent tiles of the same tile row), else zero
+// padding, and the warp's first and last lanes load them.  Called by every
+// lane of the warp, lane q with t = t_w + 2q.
+__device__ __forceinline__ void load_pair_f4_v8(const float* __restrict__ x, const LayerGeom& g,
+                                                int64_t t, int c, int lane,
+                                                unsigned long long (&d)[6][6]) {
+  const bool live = t < g.T && c < g.C;
+  int n = 0, ti = 0, tj = 0;
+  if (live) {
+    const int tpi = g.th * g.tw;
+    n = (int)(t / tpi);
+    const int rem = (int)(t - (int64_t)n * tpi);
+    ti = rem / g.tw;
+    tj = rem - ti * g.tw;
+  }
+  const int h0 = ti * 4 - 1, c0 = tj * 4;
+  const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
+  const bool has_l = live && c0 > 0, has_r = live && c0 + 8 < g.W;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int hh = h0 + i;
+    const bool in = live && (unsigned)hh < (unsigned)g.H;
+    float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    const float* row = xc + (int64_t)hh * g.W + c0;
+    if (in) ldg8(row, v);
+    float e0 = __shfl_up_sync(0xffffffffu, v[7], 1);
+    float e9 = __shfl_down_sync(0xffffffffu, v[0], 1);
+    if (!(in && has_l))
+      e0 = 0.0f;
+    else if (lane == 0)
+      e0 = __ldg(row - 1);
+    if (!(in && has_r))
+      e9 = 0.0f;
+    else if (lane == 31)
+      e9 = __ldg(row + 8);
+    d[i][0] = pack2(e0, v[3]);
+    d[i][1] = pack2(v[0], v[4]);
+    d[i][2] = pack2(v[1], v[5]);
+    d[i][3] = pack2(v[2], v[6]);
+    d[i][4] = pack2(v[3], v[7]);
+    d[i][5] = pack2(v[4], e9);
+  }
+}
+
+// F(4x4) tile pairs in one tile row, W a multiple of 4 and x 16-byte
+// aligned: columns 4 tj - 1 .. 4 tj + 8 per row (tile t takes 0-5, tile t + 1
+// takes 4-9) as two 16-byte vectors and two scalars; 4 tj .. 4 tj + 7 lie
+// inside the row (tile tj + 1 exists).  False (nothing loaded) when the
+// pair does not qualify.
+__device__ __forceinline__ bool load_pair_f4_v4(const float* __restrict__ x, const LayerGeom& g,
+                                                int64_t t, int c,
+                                                unsigned long long (&d)[6][6]) {
+  if (!(t + 1 < g.T && c < g.C && g.pad == 1 && (g.W & 3) == 0 && (((uintptr_t)x) & 15) == 0))
+    return false;
+  const int tpi = g.th * g.tw;
+  const int n = (int)(t / tpi);
+  const int rem = (int)(t - (int64_t)n * tpi);
+  const int ti = rem / g.tw, tj = rem - ti * g.tw;
+  if (tj + 1 >= g.tw) return false;  // the pair spans two tile rows
+  const int h0 = ti * 4 - 1, c0 = tj * 4;
+  const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int hh = h0 + i;
+    float e0 = 0.0f, e9 = 0.0f;
+    float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), v1 = v0;
+    if ((unsigned)hh < (unsigned)g.H) {
+      const float* row = xc + (int64_t)hh * g.W + c0;
+      v0 = __ldg(reinterpret_cast<const float4*>(row));
+      v1 = __ldg(reinterpret_cast<const float4*>(row + 4));
+      if (c0 > 0) e0 = __ldg(row - 1);
+      if (c0 + 8 < g.W) e9 = __ldg(row + 8);
+    }
+    d[i][0] = pack2(e0, v0.w);
+    d[i][1] = pack2(v0.x, v1.x);
+    d[i][2] = pack2(v0.y, v1.y);
+    d[i][3] = pack2(v0.z, v1.z);
+    d[i][4] = pack2(v0.w, v1.w);
+    d[i][5] = pack2(v1.x, e9);
+  }
+  return true;
+}
+
+// The patches of tiles t and t + 1 (channel c) as FP32 pairs, tile t in the
+// low half.  Called by every lane of the warp, lane q with t = t_w + 2q.
+template <int MM>
+__device__ __forceinline__ void load_patch_pair(const float* __restrict__ x, const LayerGeom& g,
+                                                int64_t t, int c, int lane,
+                                                unsigned long long (&d)[MM + 2][MM + 2]) {
+  constexpr int A = MM + 2;
+  if constexpr (MM == 4) {
+    if (g.pad == 1 && (g.W & 7) == 0 && (((uintptr_t)x) & 31) == 0) {
+      load_pair_f4_v8(x, g, t, c, lane, d);
+      return;
+    }
+    if (load_pair_f4_v4(x, g, t, c, d)) return;
+  }
+  float p0[A][A], p1[A][A];
+  load_patch<MM>(x, g, t, c, p0);
+  load_patch<MM>(x, g, t + 1, c, p1);
+#pragma unroll
+  for (int i = 0; i < A; ++i)
+#pragma unroll
+    for (int j = 0; j < A; ++j) d[i][j] = pack2(p0[i][j], p1[i][j]);
 }
 
 template <int MM>
-__global__ void __launch_bounds__(kQuantThreads) k_quant_input_tiled(
+__global__ void __launch_bounds__(kQuantThreads) k_quant_input_mn(
     const float* __restrict__ x, const LayerGeom g, const LayerMats Mx, const TcScales S, int Cp,
     int64_t Tp, uint16_t* __restrict__ U0, uint16_t* __restrict__ U1, uint16_t* __restrict__ U2,
     int mode) {
   constexpr int A = MM + 2, F = A * A;
-  extern __shared__ __align__(16) uint32_t qs[];  // [parts][F][kQT][kQRow] channel pairs
-  constexpr int kPart = F * kQT * kQRow;          // one part's staging, in words
-  const int tl = threadIdx.x % kQT, cp = threadIdx.x / kQT;
-  const int64_t t = (int64_t)blockIdx.x * kQT + tl;
-  const int c = blockIdx.y * kQC + 2 * cp;
-  const int parts = tc_parts(mode);
-  if constexpr (A <= 6) {
-    // both channels' values of a frequency meet in registers: one 32-bit
-    // store per (f, part)
-    quant_pair_rows<MM, 0, A>(x, g, Mx, S, t, c, tl, cp, mode, parts, qs, kPart);
+  constexpr int TPL = A <= 6 ? 2 : 1;    // tiles per lane
+  constexpr int WT = 64 / (32 * TPL);    // warps per 64 tiles
+  constexpr int WC = (kQuantThreads / 32) / WT;  // channels per block
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * 64 + (warp % WT) * (32 * TPL) + lane * TPL;
+  const int c = blockIdx.y * WC + warp / WT;
+  const int64_t ntb = Tp / kTcM;
+  const int nch = Cp / kTcKc;
+  // element index of (f, t, c) = base + f * fstride
+  const int64_t base = tc_u_index(0, t, c, ntb, nch);
+  const int64_t fstride = ntb * nch * (int64_t)(kTcM * kTcKc);
+  const bool fp16 = mode == 2;
+  if constexpr (TPL == 2) {
+    // two tiles per lane as FP32 pairs: B^T d B in fma.rn.f32x2 (each half
+    // the scalar transform's fmaf sequence, so the same bits), the scale in
+    // mul.rn.f32x2, the split in paired conversions; each 32-bit store
+    // holds both tiles' 16-bit values (tile t, even, at the lower address)
+    unsigned long long d[A][A];
+    load_patch_pair<MM>(x, g, t, c, lane, d);
+#pragma unroll
+    for (int l = 0; l < A; ++l) {
+      unsigned long long col[A];
+#pragma unroll
+      for (int i = 0; i < A; ++i) {
+        unsigned long long acc = 0ull;
+#pragma unroll
+        for (int q = 0; q < A; ++q) acc = fma2(pack_dup(Mx.BT[i * A + q]), d[q][l], acc);
+        col[i] = acc;
+      }
+#pragma unroll
+      for (int i = 0; i < A; ++i) d[i][l] = col[i];
+    }
+    // running pointers to frequency f (f ascending below)
+    uint32_t* W0 = reinterpret_cast<uint32_t*>(U0 + base);
+    uint32_t* W1 = reinterpret_cast<uint32_t*>(U1 + base);
+    uint32_t* W2 = reinterpret_cast<uint32_t*>(U2 + base);
+    const int64_t fs = fstride / 2;
+#pragma unroll
+    for (int i = 0; i < A; ++i)
+#pragma unroll
+      for (int j = 0; j < A; ++j) {
+        unsigned long long acc = 0ull;
+#pragma unroll
+        for (int l = 0; l < A; ++l) acc = fma2(d[i][l], pack_dup(Mx.BT[j * A + l]), acc);
+        const int f = i * A + j;
+        const unsigned long long v = mul2(acc, pack_dup(S.sU[f]));
+        const uint32_t hi = cvt16x2(v, fp16);
+        *W0 = hi;
+        if (mode == 3 || mode == 4) {
+          const unsigned long long r1 = sub2(v, widen16x2(hi, fp16));  // exact
+          const uint32_t mid = cvt16x2(r1, fp16);
+          *W1 = mid;
+          if (mode == 4) *W2 = cvt16x2(sub2(r1, widen16x2(mid, fp16)), fp16);
+        }
+        W0 += fs;
+        W1 += fs;
+        W2 += fs;
+      }
   } else {
-    // alpha = 8: holding one channel's 64 values while transforming the
-    // other costs too many registers (and transforming in row halves costs
-    // a second pass over the patches), so each channel goes straight to its
-    // 16-bit half of the same words
-    uint16_t* qh = reinterpret_cast<uint16_t*>(qs);
-    for (int h = 0; h < 2; ++h)
-      quant_patch<MM, 0, A>(x, g, Mx, t, c + h, [&](int f, float v) {
-        uint16_t q[3];
-        split_parts(v * S.sU[f], mode, q);
-        const int o = 2 * ((f * kQT + tl) * kQRow + qswz(cp, tl)) + h;
-        qh[o] = q[0];
-        if (parts > 1) qh[2 * kPart + o] = q[1];
-        if (parts > 2) qh[4 * kPart + o] = q[2];
-      });
+    float d[A][A];
+    load_patch<MM>(x, g, t, c, d);
+    // running pointers to frequency f (bt_d_b emits f ascending)
+    uint16_t* D0 = U0 + base;
+    uint16_t* D1 = U1 + base;
+    uint16_t* D2 = U2 + base;
+    const int parts = tc_parts(mode);
+    bt_d_b<A>(d, Mx, [&](int f, float v) {
+      uint16_t q[3];
+      split_parts(v * S.sU[f], mode, q);
+      *D0 = q[0];
+      if (parts > 1) *D1 = q[1];
+      if (parts > 2) *D2 = q[2];
+      D0 += fstride;
+      D1 += fstride;
+      D2 += fstride;
+    });
   }
-  __syncthreads();
-  // rows (f, tile) of 64 channels = 8 x 16-byte stores, consecutive threads
-  // on consecutive segments of a row (one 128-byte line of the blocked image)
-  const int64_t tb = (int64_t)blockIdx.x * kQT;
-  const int c0 = blockIdx.y * kQC;
-  uint16_t* const dsts[3] = {U0, U1, U2};
-  for (int e = threadIdx.x; e < F * kQT * 8; e += kQuantThreads) {
-    const int seg = e % 8, row = e / 8;  // row = f * kQT + tile
-    const int f = row / kQT, tr = row % kQT;
-    const int64_t dst = tc_u_index(f, tb + tr, c0 + seg * 8, Tp / kTcM, Cp / kTcKc);
-    for (int pp = 0; pp < parts; ++pp)
-      *reinterpret_cast<uint4*>(dsts[pp] + dst) =
-          *reinterpret_cast<const uint4*>(qs + pp * kPart + row * kQRow + qswz(seg * 4, tr));
-  }
+  (void)F;
 }
 
 // Output transform A^T M A with compile-time sizes, M [F][K][T]: one thread
@@ -439,12 +597,25 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// The same for an MN-major operand (the A images, tc_u_index): 1024-byte
+// atoms of 8 rows (channels) x 128 bytes (64 tiles), leading byte offset =
+// 1024 bytes between the atoms along M, stride byte offset = 2048 bytes
+// between groups of 8 rows along K.
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(1024u >> 4) << 16;
+  d |= (uint64_t)(2048u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A and B format
-// (bits 7-9, 10-12: 0 = F16, 1 = BF16), both K-major (bits 15, 16 = 0),
-// N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+// (bits 7-9, 10-12: 0 = F16, 1 = BF16), A MN-major (bit 15 = 1), B K-major
+// (bit 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28).
 __host__ __device__ __forceinline__ uint32_t f16_idesc(int fmt, int M, int N) {
-  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | (1u << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
@@ -571,7 +742,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
         const uint32_t acc = (ch > 0 || kk > 0) ? 1u : 0u;
         uint64_t ad[3], bd[3];
         for (int pp = 0; pp < parts; ++pp) {
-          ad[pp] = sw128_desc(smem_addr(As + pp * a_bytes) + kk * 32);
+          ad[pp] = sw128_desc_mn(smem_addr(As + pp * a_bytes) + kk * 4096);
           bd[pp] = sw128_desc(smem_addr(Bs + pp * b_bytes) + kk * 32);
         }
         mma_f16(tmem, ad[0], bd[0], idesc, acc);
@@ -766,33 +937,16 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
       k_filter_quant<6><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
                                             NB);
     }
-    const dim3 gq((unsigned)(Tp / kQT), (unsigned)(Cp / kQC));
-    size_t qsm = (size_t)parts * g.F * kQT * kQRow * sizeof(uint32_t);
-    // the patch loads reuse overlapping input rows through L1, which shares
-    // the SM's storage with these blocks' staging: the two-part F(4x4) form
-    // (37 KB) runs best at four blocks per SM (six measured 4% slower)
-    if (parts == 2 && M.m == 4 && qsm < 46 * 1024) qsm = 46 * 1024;
-    static bool qattr[16] = {false};
-    int qdev = 0;
-    WINO_CUDA_TRY(cudaGetDevice(&qdev));
-    if (qdev < 16 && !qattr[qdev]) {
-      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
-      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<4>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
-      WINO_CUDA_TRY(cudaFuncSetAttribute(k_quant_input_tiled<6>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQuantSmemMax));
-      qattr[qdev] = true;
-    }
+    const dim3 gq((unsigned)(Tp / 64), (unsigned)(Cp / (M.m == 6 ? 4 : 8)));
     if (M.m == 2)
-      k_quant_input_tiled<2><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                         mode);
+      k_quant_input_mn<2><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                        mode);
     else if (M.m == 4)
-      k_quant_input_tiled<4><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                         mode);
+      k_quant_input_mn<4><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                        mode);
     else
-      k_quant_input_tiled<6><<<gq, kQuantThreads, qsm, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                         mode);
+      k_quant_input_mn<6><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                        mode);
     note_launches(3);
   }
   TcGemmArgs P;
