@@ -6,11 +6,11 @@
 // by decreasing cost (trials x dense flops per trial: longest first, so the
 // last items to start are the cheapest).  A persistent grid of warps pulls
 // items from an atomic counter; each item dispatches to the size's
-// compile-time evaluator (sweep_eval.cuh).  A plan too small to fill the
-// GPU (fewer groups of 32 than four rounds of resident warps) gives each
-// group several items, one per range of trial chunks; their partial sums
-// are combined in fixed order afterwards, so the errors are the same bits
-// either way.  A device-side deadline
+// compile-time evaluator (sweep_eval.cuh).  A size with too few groups of
+// 32 to fill the GPU on its own (fewer than four rounds of resident warps)
+// gives each of its groups several items, one per range of trial chunks;
+// their partial sums are combined in fixed order afterwards, per size, so
+// the errors are the same bits either way.  A device-side deadline
 // (%globaltimer) lets the kernel stop taking work and report WINO_ETIMEOUT
 // instead of running unbounded; there is no spin-wait anywhere.  The graph
 // holds the counter/status resets, the trial records of every size
@@ -64,10 +64,11 @@ struct PlanDev {
   const double* dval;      // per size
   const double* ysum;      // per size
   double* err;             // per sorted instance
-  double* part;            // chunk partials [chunk][sorted instance] when split
+  double* part;            // chunk partials [chunk][sorted instance] of split sizes
   int64_t n_sorted;
   int trials;
-  int split;               // 1: items cover all chunks and write err directly
+  int n_chunks;            // trial chunks of `trials`
+  int split;               // 1: no size is split, every item writes err directly
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -81,7 +82,8 @@ __device__ __noinline__ void eval_item_as(const PlanDev& P, const WorkItem& w, i
   const int i = w.first + lane;
   const bool active = lane < w.count;
   const int ii = active ? i : w.first;
-  const bool partial = P.split > 1;
+  // an item covering only some trial chunks leaves partial sums
+  const bool partial = w.c0 != 0 || w.c1 != P.n_chunks;
   lane_eval<D, MM, RR>(P.rec + P.rec_off[w.size], P.trials, P.inst_mask[ii], P.inst_c[ii],
                        P.dval[w.size], w.c0, w.c1, P.ysum[w.size], partial,
                        partial ? P.part + i : P.err + i, P.n_sorted, active);
@@ -177,6 +179,8 @@ struct SweepPlan {
   std::vector<char> invalid;       // per caller instance: mask invalid for its size
   std::vector<WorkItem> items;     // LPT order
   std::vector<int> size_first, size_count;  // items of each size (per-size mode)
+  std::vector<int64_t> inst_first, inst_count;  // sorted instances of each size
+  std::vector<char> size_split;             // size's items cover chunk ranges
   // device
   void* dbuf = nullptr;
   PlanDev P{};
@@ -259,9 +263,11 @@ static int plan_enqueue(SweepPlan* p, int mode, cudaStream_t st) {
     }
   }
   WINO_CUDA_TRY(cudaGetLastError());
-  if (p->P.split > 1) {
-    int rc = sweep_combine(p->P.part, trial_chunks(p->trials), p->P.n_sorted, p->P.n_sorted,
-                           p->size_of, p->ysum, p->P.err, st);
+  for (int s = 0; s < p->n_sizes; ++s) {
+    if (!p->size_split[s] || p->inst_count[s] == 0) continue;
+    const int64_t f = p->inst_first[s];
+    int rc = sweep_combine(p->P.part + f, p->P.n_chunks, p->P.n_sorted, p->inst_count[s],
+                           p->size_of + f, p->ysum, p->P.err + f, st);
     if (rc != WINO_OK) return rc;
   }
   WINO_CUDA_TRY(cudaMemcpyAsync(p->err_h, p->P.err, sizeof(double) * (size_t)p->n_inst,
@@ -417,19 +423,28 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   }
   p->size_first.assign(n_sizes, 0);
   p->size_count.assign(n_sizes, 0);
-  // a plan of few instances spreads each group's trial chunks over several
-  // items so that the launch still fills the GPU
+  // a size with too few groups of 32 instances to fill the GPU on its own
+  // (per-size mode runs each size as one launch) spreads each group's trial
+  // chunks over several items; their partial sums are combined in fixed
+  // order afterwards, so the errors are the same bits either way
   const int n_chunks = trial_chunks(trials);
-  int64_t base_items = 0;
-  for (int s = 0; s < n_sizes; ++s) base_items += ((int64_t)by_size[s].size() + 31) / 32;
-  int split = 1;
-  if (base_items > 0 && base_items < sweep_target_warps())
-    split = (int)std::min<int64_t>(n_chunks, (sweep_target_warps() + base_items - 1) / base_items);
-  const int ch_per = (n_chunks + split - 1) / split;
-  const int groups = (n_chunks + ch_per - 1) / ch_per;
+  p->inst_first.assign(n_sizes, 0);
+  p->inst_count.assign(n_sizes, 0);
+  p->size_split.assign(n_sizes, 0);
+  bool any_split = false;
   std::vector<std::pair<double, WorkItem>> tmp;
   for (int s = 0; s < n_sizes; ++s) {
     const double flops = sweep_trial_flops(p->sizes[s].dim, p->sizes[s].m, p->sizes[s].r);
+    const int64_t items = ((int64_t)by_size[s].size() + 31) / 32;
+    int split = 1;
+    if (items > 0 && items < sweep_target_warps())
+      split = (int)std::min<int64_t>(n_chunks, (sweep_target_warps() + items - 1) / items);
+    const int ch_per = (n_chunks + split - 1) / split;
+    const int groups = (n_chunks + ch_per - 1) / ch_per;
+    p->size_split[s] = groups > 1;
+    any_split = any_split || groups > 1;
+    p->inst_first[s] = (int64_t)p->order.size();
+    p->inst_count[s] = (int64_t)by_size[s].size();
     for (size_t j = 0; j < by_size[s].size(); j += 32) {
       const int first = (int)p->order.size();
       const int count = (int)std::min<size_t>(32, by_size[s].size() - j);
@@ -522,7 +537,7 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   const size_t o_isz = o;
   o = al(o + (size_t)std::max<int64_t>(n_sorted, 1));
   const size_t o_chunk = o;
-  if (groups > 1) o = al(o + (size_t)n_chunks * n_sorted * 8);
+  if (any_split) o = al(o + (size_t)n_chunks * n_sorted * 8);
   const size_t o_ctr = o;
   o = al(o + 64);
   if (cudaMalloc(&p->dbuf, o) != cudaSuccess) {
@@ -590,7 +605,8 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   P.part = (double*)(b + o_chunk);
   P.n_sorted = n_sorted;
   P.trials = trials;
-  P.split = groups;
+  P.n_chunks = n_chunks;
+  P.split = any_split ? 2 : 1;
 
   if (mode == WINO_SWEEP_AUTO) {
     rc = plan_autotune(p);
