@@ -975,12 +975,12 @@ NCU_TRAFFIC = {
                     + 32 * 512 * 28 * 28 * 4),
     # k_tc_gemm split-BF16x6, C = K = 64, 224x224, N = 8: three 16-bit parts
     # of U and V read, M written (FP32)
-    "tc_gemm": (538.43e6, 36 * (2 * 3 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
+    "tc_gemm": (535.54e6, 36 * (2 * 3 * (25216 * 64 + 64 * 64) + 4 * 25088 * 64)),
     # k_input_transform_blk F(4x4), C = 64, 224x224, N = 8: x read, U written
     "input_transform": (285.9e6, 334.0e6),
-    # k_quant_input_mn BF16 F(4x4), C = 64, 224x224, N = 8: x read, U written
-    # (one 16-bit part; the filter kernels' bytes are small)
-    "tc_transform": (172.20e6, 8 * 64 * 224 * 224 * 4 + 36 * 25088 * 64 * 2),
+    # k_quant_input_mn split-BF16x6 F(4x4), C = 64, 224x224, N = 8: x read,
+    # three 16-bit parts of U written (the filter kernels' bytes are small)
+    "tc_transform": (390.28e6, 8 * 64 * 224 * 224 * 4 + 3 * 36 * 25088 * 64 * 2),
     # k_output_transform_r3 F(4x4), K = 64, 224x224, N = 8: M read, y written
     "output_transform": (300.7e6, 334.0e6),
 }
