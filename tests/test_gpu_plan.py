@@ -98,3 +98,35 @@ def test_chunk_split_is_bit_identical(wino):
         small.close()
     key = {(int(q["mask"]), float(q["c"])): e for q, e in zip(inst, want)}
     assert np.array_equal(got, np.array([key[(int(q["mask"]), float(q["c"]))] for q in sub]))
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_mixed_split_and_whole_sizes(wino, mode):
+    """Chunks are split per size: in one plan a size with more groups of 32
+    than four rounds of resident warps runs whole trials per lane while a
+    small size spreads its chunks over several items, and only the small
+    size's partial sums are combined.  Each instance must give the bits it
+    gives in a plan of its size alone (a whole plan for the large size, a
+    split one for the small size), in every execution mode."""
+    big_size, small_size = (1, 2, 3, 1.0), (2, 6, 3, 1.0)
+    rng = np.random.default_rng(33)
+    mb = np.array(wino.valid_masks(big_size, inputs.sweep_masks()), dtype=np.uint8)
+    ms = np.array(wino.valid_masks(small_size, inputs.sweep_masks()), dtype=np.uint8)
+    nb, ns = 32 * 152 * 8 * 4 + 77, 900
+    cb = np.exp(rng.uniform(np.log(0.05), np.log(20), nb))
+    cs = np.exp(rng.uniform(np.log(0.05), np.log(20), ns))
+    inst_b = wino.instance_array(np.zeros(nb, np.int32), mb[rng.integers(mb.size, size=nb)], cb)
+    inst_s = wino.instance_array(np.zeros(ns, np.int32), ms[rng.integers(ms.size, size=ns)], cs)
+    both = wino.instance_array(np.concatenate([np.zeros(ns, np.int32), np.ones(nb, np.int32)]),
+                               np.concatenate([inst_s["mask"], inst_b["mask"]]),
+                               np.concatenate([cs, cb]))
+    plans = [wino.SweepPlan([big_size], inst_b, 300, seed=8, mode=1),
+             wino.SweepPlan([small_size], inst_s, 300, seed=8, mode=1),
+             wino.SweepPlan([small_size, big_size], both, 300, seed=8, mode=mode)]
+    try:
+        want_b, want_s, got = (p.run() for p in plans)
+    finally:
+        for p in plans:
+            p.close()
+    assert np.array_equal(got[:ns], want_s, equal_nan=True)
+    assert np.array_equal(got[ns:], want_b, equal_nan=True)
