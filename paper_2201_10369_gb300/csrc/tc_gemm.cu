@@ -30,11 +30,14 @@
 // k_tc_gemm: one CTA = one frequency x 128 tiles (MMA M) x NB output
 // channels (MMA N <= 256), contraction over Cp in chunks of 64 channels
 // (one 128-byte swizzle row per operand row).  The quantising kernels write
-// the operands as the SWIZZLE_128B K-major shared-memory images of these
-// chunks, so one thread moves each chunk with one bulk copy per operand
-// part (mbarrier-counted), issues tcgen05.mma (K = 16 per instruction) and
-// commits to a second mbarrier; every wait is bounded and records an error
-// instead of hanging.
+// the operands as the SWIZZLE_128B shared-memory images of these chunks (A
+// MN-major, B K-major), so one thread moves each chunk with one bulk copy
+// per operand part (mbarrier-counted), issues tcgen05.mma (K = 16 per
+// instruction) and commits to a second mbarrier; every wait is bounded and
+// records an error instead of hanging.  k_tc_gemm_ws, the warp-specialised
+// persistent form (a producer, an MMA issuer and epilogue warps over a ring
+// of stages and two TMEM accumulator buffers), takes the split x6 layers and
+// the others whose contraction has four or more chunks.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -800,6 +803,232 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(const TcGemmArgs P) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised persistent form of the contraction.
+// ---------------------------------------------------------------------------
+// One CTA per SM loops over work units (frequency f, 128-tile block, NB-
+// channel k block), the k blocks of one (f, tile block) adjacent so that
+// its U blocks are re-read from L2.  Roles:
+//   warp 0, lane 0  producer: per (unit, 64-channel chunk) one bulk copy per
+//                   operand part of A and of B into an NS-stage ring, each
+//                   fill counted in bytes on full[s];
+//   warp 1, lane 0  MMA issuer: per unit, waits until the epilogue has
+//                   drained the unit's TMEM accumulator buffer (two
+//                   buffers, alternating), then per chunk waits full[s],
+//                   issues the MMAs and commits to empty[s]; after the
+//                   unit's last chunk it commits to tfull[buffer];
+//   warps 2-5       epilogue: wait tfull[buffer], read their 32 TMEM lanes
+//                   (tiles) of the buffer, write M = (D (+ D')) / (sU sV)
+//                   and arrive on tempty[buffer].
+// So the epilogue of unit i overlaps the MMAs of unit i + 1 and the copies
+// of the chunks after it.  The products per 16-channel step and their
+// accumulators are those of k_tc_gemm, so M is the same.  Every wait is
+// bounded; a role whose wait gave up records the error and stops, and the
+// CTA drains its copies and MMAs before TMEM is freed.  Launch: one CTA of
+// 192 threads per SM (shared memory and TMEM keep it alone), NS ring stages.
+constexpr int kTwsThreads = 192;
+constexpr int kTwsMaxNS = 8;
+// The layer uses this form for the split x6 form, and for the others when
+// the contraction has at least this many 64-channel chunks (C >= 256): on
+// the VGG16 stages it took stages 3-5 from 134 / 99 / 34 to 117 / 77 / 32 us
+// (BF16 F(4x4), with the output transform), while with one or two chunks per
+// unit the one- and two-part forms ran 2-8% behind k_tc_gemm (also with
+// eight epilogue warps instead of four); the split x6 stacks are fastest
+// with this form on every stage.
+constexpr int kTwsMinChunks = 4;
+
+__device__ __forceinline__ void mbar_init_n(uint32_t bar, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(n));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kTwsThreads, 1) k_tc_gemm_ws(const TcGemmArgs P, int NS,
+                                                              int F) {
+  extern __shared__ __align__(1024) unsigned char wsm_raw[];
+  unsigned char* wsm = wsm_raw + ((1024u - (smem_addr(wsm_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t full[kTwsMaxNS], empty[kTwsMaxNS], tfull[2], tempty[2], done;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int s_issued, s_consumed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int parts = tc_parts(P.mode);
+  const int NB = P.NB;
+  const int nch = P.Cp / kTcKc, nkb = P.K / NB;
+  const int64_t ntb = P.Tp / kTcM;
+  const int64_t n_units = (int64_t)F * ntb * nkb;
+  const uint32_t a_bytes = kTcM * 128, b_bytes = (uint32_t)NB * 128;
+  const uint32_t stage_bytes = (uint32_t)parts * (a_bytes + b_bytes);
+  const uint32_t ncols = (uint32_t)max(32, parts == 3 ? 2 * NB : NB);  // one buffer
+  const uint32_t ring = smem_addr(wsm);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_addr(&tmem_holder)),
+                 "r"(2 * ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init1(smem_addr(&full[s]));
+      mbar_init1(smem_addr(&empty[s]));
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init1(smem_addr(&tfull[b]));
+      mbar_init_n(smem_addr(&tempty[b]), 4);
+    }
+    mbar_init1(smem_addr(&done));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_issued = 0;
+    s_consumed = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+
+  bool ok = true;
+  if (warp == 0 && lane == 0) {
+    // producer
+    int it = 0;
+    for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int kb = (int)(u % nkb);
+      const int64_t r = u / nkb;
+      const int64_t tb = r % ntb;
+      const int f = (int)(r / ntb);
+      for (int ch = 0; ch < nch; ++ch, ++it) {
+        const int s = it % NS;
+        if (it >= NS && !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)((it / NS - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const uint32_t dst = ring + (uint32_t)s * stage_bytes, bar = smem_addr(&full[s]);
+        mbar_expect_tx(bar, stage_bytes);
+        const int64_t ua = (((int64_t)f * ntb + tb) * nch + ch) * (int64_t)(kTcM * kTcKc);
+        const int64_t vb = (((int64_t)f * nkb + kb) * nch + ch) * ((int64_t)NB * kTcKc);
+        for (int pp = 0; pp < parts; ++pp) {
+          bulk_g2s(dst + pp * a_bytes, P.U[pp] + ua, a_bytes, bar);
+          bulk_g2s(dst + parts * a_bytes + pp * b_bytes, P.V[pp] + vb, b_bytes, bar);
+        }
+      }
+    }
+    s_issued = it;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = f16_idesc(P.mode == 2 ? 0 : 1, kTcM, NB);
+    int it = 0, lu = 0;
+    for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++lu) {
+      const int b = lu & 1;
+      if (lu >= 2 && !mbar_wait_bounded(smem_addr(&tempty[b]), (uint32_t)((lu / 2 - 1) & 1))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t td = tmem + (uint32_t)b * ncols, td2 = td + (uint32_t)NB;
+      for (int ch = 0; ch < nch; ++ch, ++it) {
+        const int s = it % NS;
+        if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)((it / NS) & 1))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t As = ring + (uint32_t)s * stage_bytes, Bs = As + parts * a_bytes;
+#pragma unroll
+        for (int kk = 0; kk < kTcKc / 16; ++kk) {
+          const uint32_t acc = (ch > 0 || kk > 0) ? 1u : 0u;
+          uint64_t ad[3], bd[3];
+          for (int pp = 0; pp < parts; ++pp) {
+            ad[pp] = sw128_desc_mn(As + pp * a_bytes + kk * 4096);
+            bd[pp] = sw128_desc(Bs + pp * b_bytes + kk * 32);
+          }
+          mma_f16(td, ad[0], bd[0], idesc, acc);
+          if (parts == 2) {
+            mma_f16(td, ad[0], bd[1], idesc, 1u);
+            mma_f16(td, ad[1], bd[0], idesc, 1u);
+          } else if (parts == 3) {
+            mma_f16(td2, ad[0], bd[1], idesc, acc);
+            mma_f16(td2, ad[1], bd[0], idesc, 1u);
+            mma_f16(td2, ad[0], bd[2], idesc, 1u);
+            mma_f16(td2, ad[2], bd[0], idesc, 1u);
+            mma_f16(td2, ad[1], bd[1], idesc, 1u);
+          }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_addr(&empty[s]))
+            : "memory");
+      }
+      if (!ok) break;
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              smem_addr(&tfull[b]))
+          : "memory");
+    }
+    s_consumed = it;
+    // arrives once every MMA issued above has completed
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_addr(&done))
+        : "memory");
+  } else if (warp >= 2) {
+    // epilogue: TMEM lanes 32 (warp % 4) .. are this warp's tiles
+    const int lg = warp & 3;
+    int lu = 0;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++lu) {
+      const int b = lu & 1;
+      const bool got = mbar_wait_bounded(smem_addr(&tfull[b]), (uint32_t)((lu / 2) & 1));
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int kb = (int)(u % nkb);
+      const int64_t r = u / nkb;
+      const int64_t tb = r % ntb;
+      const int f = (int)(r / ntb);
+      const float inv = 1.0f / (P.S.sU[f] * P.sV[f]);  // exact: powers of two
+      const int64_t t = tb * kTcM + lg * 32 + lane;
+      const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)b * ncols;
+      for (int col = 0; col < NB; col += 16) {
+        uint32_t v[16], w[16];
+        tmem_ld16(base + (uint32_t)col, v);
+        if (parts == 3) {
+          tmem_ld16(base + (uint32_t)(NB + col), w);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            v[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[j]), __uint_as_float(w[j])));
+        }
+        if (t < P.T) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            P.M[((int64_t)f * P.K + kb * NB + col + j) * P.T + t] = __uint_as_float(v[j]) * inv;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(&tempty[b]));
+    }
+  }
+  const bool cta_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (tid == 0) {
+    // every MMA completed (the issuer's last commit), then, after a failed
+    // wait, the fills that were issued but not consumed
+    const bool fin = mbar_wait_bounded(smem_addr(&done), 0u);
+    if (!cta_ok || !fin) {
+      atomicExch(P.err, 1);
+      for (int it = s_consumed; it < s_issued; ++it)
+        (void)mbar_wait_bounded(smem_addr(&full[it % NS]), (uint32_t)((it / NS) & 1));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(2 * ncols));
+  }
+}
+
 // TMEM columns of one CTA: NB FP32 accumulator columns (two accumulators for
 // the split x6 form), at least 32.
 static int tc_ncols(int NB, int parts) {
@@ -985,10 +1214,30 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
         cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set[dev] = true;
   }
-  {
+  if (parts < 3 && Cp / kTcKc < kTwsMinChunks) {
     ProfScope ps(kKTcGemm, st);
     dim3 grid((unsigned)(Tp / kTcM), (unsigned)(g.K / NB), (unsigned)g.F);
     k_tc_gemm<<<grid, kTcThreads, smem, st>>>(P);
+    note_launches(1);
+  } else {
+    // warp-specialised persistent form: one CTA per SM, as many ring stages
+    // as fit in 200 KB
+    ProfScope ps(kKTcGemm, st);
+    const size_t stage = (size_t)parts * ((size_t)kTcM * 128 + (size_t)NB * 128);
+    int ns = (int)((200 * 1024) / stage);
+    ns = ns < 2 ? 2 : (ns > kTwsMaxNS ? kTwsMaxNS : ns);
+    const size_t smem_ws = (size_t)ns * stage + 1024;
+    static bool ws_attr[16] = {false};
+    if (!ws_attr[dev]) {
+      WINO_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         210 * 1024));
+      ws_attr[dev] = true;
+    }
+    int sms = 0;
+    WINO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t units = (int64_t)g.F * (Tp / kTcM) * (g.K / NB);
+    const unsigned grid = (unsigned)std::min<int64_t>(units, sms);
+    k_tc_gemm_ws<<<grid, kTwsThreads, smem_ws, st>>>(P, ns, g.F);
     note_launches(1);
   }
   {
