@@ -424,7 +424,11 @@ int wino_mlp_grid_features(const wino_size* sizes, int n_sizes,
 int wino_mlp_loss_grad(void* mlp, const float* X, const float* y, int B,
                        float* grad, double* loss, void* cuda_stream);
 /* `epochs` passes over n samples (device) in whole batches of `batch`, in
- * order; one epoch is captured as a CUDA graph and replayed.              */
+ * order; one epoch is captured as a CUDA graph and replayed.  The batch
+ * gradient is summed over blocks of 64 samples in a fixed order (no
+ * atomics), so a run is deterministic: the same data, seed and schedule
+ * give the same weights.  Grows a per-model buffer of partial gradients
+ * (batch / 64 rows of WINO_MLP_PARAMS + 1 floats) on first use.            */
 int wino_mlp_train(void* mlp, const float* X, const float* y, int64_t n,
                    int batch, int epochs, float lr, void* cuda_stream);
 /* out[n] (device) = f(X[n][16]) at the working weights.                  */

@@ -10,9 +10,12 @@
 // BF16-rounded working copy pw (stored as floats) used by the forward and
 // backward passes; Adam updates the masters and re-rounds pw.
 // One training step = gradient kernel (blocks of 64 samples, per-block
-// reduction in shared memory, one atomic add per parameter per block) +
-// Adam kernel (one block; it also advances the step counter, which lives on
-// the device so an epoch can be captured once in a CUDA graph and replayed).
+// reduction in shared memory into that block's row of partial gradients;
+// block 0 also advances the step counter, which lives on the device so an
+// epoch can be captured once in a CUDA graph and replayed) + Adam kernel
+// (one thread per parameter, which first adds the blocks' partials in block
+// order).  No atomics: a training run is deterministic, the same weights
+// from the same data, seed and schedule on every run.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -44,20 +47,24 @@ __global__ void k_mlp_round(const float* __restrict__ p, float* __restrict__ pw)
     pw[i] = __bfloat162float(__float2bfloat16_rn(p[i]));
 }
 
-// MSE gradient of a batch at the working weights.  grad (kNParam) and
-// loss_sum must be zero on entry; grad receives sum over the batch of
-// d/dp (out - y)^2 / B, loss_sum the sum of squared residuals.
+// MSE gradient of a batch at the working weights, per block: row b of
+// part (kPartStride floats) receives the sum over block b's samples of
+// d/dp (out - y)^2 / B and, in its last word, their squared residuals.
+// With t non-null, block 0 advances the step counter.
+constexpr int kPartStride = kNParam + 1;
 __global__ void __launch_bounds__(kGradBlock) k_mlp_grad(const float* __restrict__ pw,
                                                          const float* __restrict__ X,
                                                          const float* __restrict__ y, int B,
-                                                         float* __restrict__ grad,
-                                                         float* __restrict__ loss_sum) {
+                                                         float* __restrict__ part,
+                                                         int* __restrict__ t) {
   __shared__ float sp[kNParam];
   __shared__ float sdz[kGradBlock][kHid + 1];
   __shared__ float sh[kGradBlock][kHid + 1];
   __shared__ float sx[kGradBlock][kIn + 1];
   __shared__ float sdo[kGradBlock];
+  __shared__ float sr2[kGradBlock / 32];
   const int tid = threadIdx.x;
+  if (t && blockIdx.x == 0 && tid == 0) *t += 1;
   for (int i = tid; i < kNParam; i += kGradBlock) sp[i] = pw[i];
   __syncthreads();
   const int s = blockIdx.x * kGradBlock + tid;
@@ -94,10 +101,16 @@ __global__ void __launch_bounds__(kGradBlock) k_mlp_grad(const float* __restrict
     }
     for (int i = 0; i < kIn; ++i) sx[tid][i] = 0.0f;
   }
-  // squared residuals: warp shuffle, one atomic per warp
+  // squared residuals: warp shuffle, then the warps in order
   for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
-  if ((tid & 31) == 0) atomicAdd(loss_sum, r2);
+  if ((tid & 31) == 0) sr2[tid >> 5] = r2;
   __syncthreads();
+  float* row = part + (int64_t)blockIdx.x * kPartStride;
+  if (tid == 0) {
+    float l = 0.0f;
+    for (int w = 0; w < kGradBlock / 32; ++w) l += sr2[w];
+    row[kNParam] = l;
+  }
   // per-parameter sums over the block's samples
   for (int q = tid; q < kNParam; q += kGradBlock) {
     float acc = 0.0f;
@@ -113,20 +126,35 @@ __global__ void __launch_bounds__(kGradBlock) k_mlp_grad(const float* __restrict
     } else {
       for (int t = 0; t < kGradBlock; ++t) acc += sdo[t];
     }
-    atomicAdd(grad + q, acc);
+    row[q] = acc;
   }
 }
 
-// Adam (one block): p <- p - lr mhat / (sqrt(vhat) + eps); t (device) += 1;
-// pw <- bf16(p); grad is cleared for the next step.
-__global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ pw, float* __restrict__ grad,
-                           float* __restrict__ m, float* __restrict__ v, int* __restrict__ t,
-                           float lr, float* __restrict__ loss_sum) {
-  const int step = *t + 1;
+// Sum of the blocks' partial gradients (and squared residuals) in block
+// order: grad[i] = sum_b part[b][i], i < kNParam + 1.
+__device__ __forceinline__ float sum_parts(const float* __restrict__ part, int nblocks, int i) {
+  float g = 0.0f;
+  for (int b = 0; b < nblocks; ++b) g += part[(int64_t)b * kPartStride + i];
+  return g;
+}
+__global__ void k_mlp_reduce(const float* __restrict__ part, int nblocks,
+                             float* __restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kPartStride) grad[i] = sum_parts(part, nblocks, i);
+}
+
+// Adam, one thread per parameter: g = the blocks' partials added in block
+// order; p <- p - lr mhat / (sqrt(vhat) + eps) at the step the gradient
+// kernel counted; pw <- bf16(p).
+__global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ pw,
+                           const float* __restrict__ part, int nblocks, float* __restrict__ m,
+                           float* __restrict__ v, const int* __restrict__ t, float lr) {
+  const int step = *t;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-  for (int i = threadIdx.x; i < kNParam; i += blockDim.x) {
-    const float g = grad[i];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kNParam) {
+    const float g = sum_parts(part, nblocks, i);
     const float mi = b1 * m[i] + (1.0f - b1) * g;
     const float vi = b2 * v[i] + (1.0f - b2) * g * g;
     m[i] = mi;
@@ -134,12 +162,6 @@ __global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ pw, float*
     const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     p[i] = pi;
     pw[i] = __bfloat162float(__float2bfloat16_rn(pi));
-    grad[i] = 0.0f;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    *t = step;
-    *loss_sum = 0.0f;
   }
 }
 
@@ -260,7 +282,30 @@ struct Mlp {
   float *p = nullptr, *pw = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *loss = nullptr;
   int* t = nullptr;
   void* buf = nullptr;
+  float* part = nullptr;  // per-block partial gradients (grown as needed)
+  int part_blocks = 0;
 };
+
+// The handle's partial-gradient rows for `nblocks` gradient blocks.
+static int mlp_part(Mlp* M, int nblocks, float** part) {
+  if (nblocks > M->part_blocks) {
+    if (M->part) {
+      WINO_CUDA_TRY(cudaDeviceSynchronize());
+      WINO_CUDA_TRY(cudaFree(M->part));
+      M->part = nullptr;
+      M->part_blocks = 0;
+    }
+    if (cudaMalloc(&M->part, (size_t)nblocks * kPartStride * sizeof(float)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      M->part = nullptr;
+      set_error("could not allocate the surrogate's gradient partials");
+      return WINO_ENOMEM;
+    }
+    M->part_blocks = nblocks;
+  }
+  *part = M->part;
+  return WINO_OK;
+}
 
 static uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -351,21 +396,23 @@ int wino_mlp_loss_grad(void* mlp, const float* X, const float* y, int B, float* 
     return WINO_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  WINO_CUDA_TRY(cudaMemsetAsync(M->grad, 0, kNParam * sizeof(float), st));
-  WINO_CUDA_TRY(cudaMemsetAsync(M->loss, 0, sizeof(float), st));
+  const int nb = (B + kGradBlock - 1) / kGradBlock;
+  float* part = nullptr;
+  int rc = mlp_part(M, nb, &part);
+  if (rc != WINO_OK) return rc;
   {
     ProfScope ps(kKMlp, st);
-    k_mlp_grad<<<(B + kGradBlock - 1) / kGradBlock, kGradBlock, 0, st>>>(M->pw, X, y, B, M->grad,
-                                                                          M->loss);
-    note_launches(1);
+    k_mlp_grad<<<nb, kGradBlock, 0, st>>>(M->pw, X, y, B, part, nullptr);
+    k_mlp_reduce<<<(kPartStride + 255) / 256, 256, 0, st>>>(part, nb, M->grad);
+    note_launches(2);
   }
   WINO_CUDA_TRY(cudaGetLastError());
   float ls = 0.0f;
   WINO_CUDA_TRY(cudaMemcpyAsync(grad_out, M->grad, kNParam * sizeof(float),
                                 cudaMemcpyDeviceToHost, st));
-  WINO_CUDA_TRY(cudaMemcpyAsync(&ls, M->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+  WINO_CUDA_TRY(cudaMemcpyAsync(&ls, M->grad + kNParam, sizeof(float), cudaMemcpyDeviceToHost,
+                                st));
   WINO_CUDA_TRY(cudaStreamSynchronize(st));
-  WINO_CUDA_TRY(cudaMemsetAsync(M->grad, 0, kNParam * sizeof(float), st));
   *loss_out = (double)ls / B;
   return WINO_OK;
 }
@@ -382,6 +429,12 @@ int wino_mlp_train(void* mlp, const float* X, const float* y, int64_t n, int bat
     set_error("fewer samples than one batch");
     return WINO_EINVAL;
   }
+  const int nb = (batch + kGradBlock - 1) / kGradBlock;
+  float* part = nullptr;
+  {
+    int rc = mlp_part(M, nb, &part);
+    if (rc != WINO_OK) return rc;
+  }
   cudaStream_t st = nullptr;
   WINO_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   cudaEvent_t ev = nullptr;
@@ -394,9 +447,10 @@ int wino_mlp_train(void* mlp, const float* X, const float* y, int64_t n, int bat
   cudaGraphExec_t exec = nullptr;
   WINO_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   for (int64_t s = 0; s < steps; ++s) {
-    k_mlp_grad<<<(batch + kGradBlock - 1) / kGradBlock, kGradBlock, 0, st>>>(
-        M->pw, X + s * batch * kIn, y + s * batch, batch, M->grad, M->loss);
-    k_mlp_adam<<<1, 1024, 0, st>>>(M->p, M->pw, M->grad, M->m, M->v, M->t, lr, M->loss);
+    k_mlp_grad<<<nb, kGradBlock, 0, st>>>(M->pw, X + s * batch * kIn, y + s * batch, batch,
+                                          part, M->t);
+    k_mlp_adam<<<(kNParam + 255) / 256, 256, 0, st>>>(M->p, M->pw, part, nb, M->m, M->v, M->t,
+                                                      lr);
   }
   cudaError_t e = cudaStreamEndCapture(st, &graph);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -532,6 +586,7 @@ int wino_topk_rows(const float* vals, int rows, int cols, int k, int* idx, void*
 void wino_mlp_destroy(void* mlp) {
   Mlp* M = (Mlp*)mlp;
   if (!M) return;
+  if (M->part) cudaFree(M->part);
   cudaFree(M->buf);
   (void)cudaGetLastError();
   delete M;

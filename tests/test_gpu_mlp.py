@@ -59,6 +59,30 @@ def test_mlp_adam_step_vs_oracle(wino):
         model.close()
 
 
+def test_training_is_deterministic(wino):
+    """The batch gradient is summed per block and the blocks' partials are
+    added in block order (no atomics), so two runs of the same training --
+    same initial weights, data and schedule -- end at the same weights, bit
+    for bit (several blocks per batch, several steps and epochs)."""
+    X, y, Xt, yt = _batch(4096 * 5, 12)
+    out = []
+    for _ in range(2):
+        model = wino.Surrogate(seed=13)
+        try:
+            model.set_output_bias(float(y.mean()))
+            model.train(Xt, yt, batch=4096, epochs=3, lr=3e-3)
+            out.append(model.params())
+        finally:
+            model.close()
+    fresh = wino.Surrogate(seed=13)
+    try:
+        p0 = fresh.params()
+    finally:
+        fresh.close()
+    assert np.array_equal(out[0], out[1])
+    assert not np.array_equal(out[0], p0)  # training moved the weights
+
+
 def test_topk_rows_vs_numpy(wino):
     import torch
     rng = np.random.default_rng(9)
