@@ -78,6 +78,30 @@ int scratch_get(int slot, size_t bytes, void** ptr) {
   return WINO_OK;
 }
 
+int side_stream(cudaStream_t* aux, cudaEvent_t* fork, cudaEvent_t* join) {
+  static cudaStream_t streams[kMaxDev];
+  static cudaEvent_t forks[kMaxDev], joins[kMaxDev];
+  static bool made[kMaxDev] = {false};
+  static std::mutex mu;
+  int dev = 0;
+  WINO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) {
+    set_error("device index out of range");
+    return WINO_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!made[dev]) {
+    WINO_CUDA_TRY(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    WINO_CUDA_TRY(cudaEventCreateWithFlags(&forks[dev], cudaEventDisableTiming));
+    WINO_CUDA_TRY(cudaEventCreateWithFlags(&joins[dev], cudaEventDisableTiming));
+    made[dev] = true;
+  }
+  *aux = streams[dev];
+  *fork = forks[dev];
+  *join = joins[dev];
+  return WINO_OK;
+}
+
 int wait_error_flag(int** ptr) {
   int* (&flags)[kMaxDev] = g_wait_flag;
   int dev = 0;

@@ -134,6 +134,12 @@ class ProfScope {
   void* a_;
 };
 
+// The current device's side stream of the layer paths and its two events
+// (created on first use): a layer call forks work that does not depend on
+// the input (the filter transforms) onto it with `fork`, recorded on the
+// caller's stream, and joins it back with `join` before the contraction.
+int side_stream(cudaStream_t* aux, cudaEvent_t* fork, cudaEvent_t* join);
+
 // Scratch owned by the library (grow-only, per purpose and device).
 enum ScratchSlot { kScratchLayer = 0, kScratchSweep = 1, kScratchStats = 2, kScratchTC = 3,
                    kScratchMLP = 4, kNumScratch = 5 };

@@ -1116,17 +1116,26 @@ static bool launch_split_transforms(const float* x, const float* w, const LayerG
       return false;
     attr_set[dev] = true;
   }
+  // the filter transform does not depend on x: it runs on the side stream,
+  // beside the input transform, and the caller's stream waits for it
+  // before the contraction
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (side_stream(&aux, &fork, &join) != WINO_OK) return false;
+  if (cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(aux, fork, 0) != cudaSuccess)
+    return false;
   {
-    ProfScope ps(kKFilter, st);
+    ProfScope ps(kKFilter, aux);
     k_filter_transform_blk<MM><<<dim3((unsigned)((g.K + kFtK - 1) / kFtK), (unsigned)fy), 256, 0,
-                                 st>>>(w, Vb, g.C, g.K, M, sg);
+                                 aux>>>(w, Vb, g.C, g.K, M, sg);
   }
+  if (cudaEventRecord(join, aux) != cudaSuccess) return false;
   {
     ProfScope ps(kKInput, st);
     k_input_transform_blk<MM><<<dim3((unsigned)sg.ntb, (unsigned)sg.nch), sg.CC * sg.TB, csm,
                                 st>>>(x, Ub, g, M, sg);
   }
-  return true;
+  return cudaStreamWaitEvent(st, join, 0) == cudaSuccess;
 }
 
 template <SPLIT_TPARAMS>

@@ -1143,9 +1143,20 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
       S.sU[f] = (gain > 0.0) ? (float)ldexp(1.0, 1 - e) : 1.0f;
     }
   }
-  WINO_CUDA_TRY(cudaMemsetAsync(vmax, 0, (size_t)g.F * 4, st));
+  // the filter side (max |V|, V rounded and split) does not depend on x: it
+  // runs on the side stream, beside the quantising input transform, and the
+  // caller's stream waits for it before the contraction
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   {
-    ProfScope ps(kKTcTransform, st);
+    int rc = side_stream(&aux, &fork, &join);
+    if (rc != WINO_OK) return rc;
+  }
+  WINO_CUDA_TRY(cudaEventRecord(fork, st));
+  WINO_CUDA_TRY(cudaStreamWaitEvent(aux, fork, 0));
+  WINO_CUDA_TRY(cudaMemsetAsync(vmax, 0, (size_t)g.F * 4, aux));
+  {
+    ProfScope psf(kKTcTransform, aux);
     // per-frequency maxima of V (each block reduces up to 8 kernels per
     // thread), then V recomputed, scaled and split
     const int64_t nck = (int64_t)g.C * g.K;
@@ -1154,18 +1165,23 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
                                                            (8 * kFvThreads), 1 << 16));
     const unsigned bq = (unsigned)(((int64_t)g.K * Cp + 255) / 256);
     if (M.m == 2) {
-      k_filter_vmax<2><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<2><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+      k_filter_vmax<2><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
+      k_filter_quant<2><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
                                             NB);
     } else if (M.m == 4) {
-      k_filter_vmax<4><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<4><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+      k_filter_vmax<4><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
+      k_filter_quant<4><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
                                             NB);
     } else {
-      k_filter_vmax<6><<<bf, kFvThreads, 0, st>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<6><<<bq, 256, 0, st>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+      k_filter_vmax<6><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
+      k_filter_quant<6><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
                                             NB);
     }
+    note_launches(2);
+  }
+  WINO_CUDA_TRY(cudaEventRecord(join, aux));
+  {
+    ProfScope ps(kKTcTransform, st);
     const dim3 gq((unsigned)(Tp / 64), (unsigned)(Cp / (M.m == 6 ? 4 : 8)));
     if (M.m == 2)
       k_quant_input_mn<2><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
@@ -1176,8 +1192,9 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     else
       k_quant_input_mn<6><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
                                                         mode);
-    note_launches(3);
+    note_launches(1);
   }
+  WINO_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
   TcGemmArgs P;
   for (int pp = 0; pp < 3; ++pp) {
     P.U[pp] = Up[pp];
