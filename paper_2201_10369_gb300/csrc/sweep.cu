@@ -182,6 +182,14 @@ int sweep_combine(const double* part, int n_chunks, int64_t stride, int64_t n,
   return WINO_OK;
 }
 
+// The warps a size's launch aims for when its sizes run beside each other
+// on the internal streams: an eighth of sweep_target_warps() (four warps
+// per SM).  Splitting an instance's chunks over more warps rebuilds its FP64
+// matrices in each of them; on the full grid the split targets 1/2, 1/4,
+// 1/8, 1/16, 1/32, 1/64 of sweep_target_warps() and no split measured
+// 8.21, 8.01, 7.79, 7.88, 8.10, 9.0 and 9.3 ms (1/1: 8.49 ms).
+int sweep_split_warps() { return sweep_target_warps() / 8; }
+
 int sweep_target_warps() {
   static int sms = 0;
   if (sms == 0) {
@@ -301,8 +309,8 @@ int error_sweep(const double* c_grid, int n_c, const SweepSize* sizes, int n_siz
     ml[s] = valid_masks(sizes[s], subsets, n_subsets);
     const int items = ml[s].n * nblk;
     if (order == 0 && !sweep_wide(sizes[s].dim, sizes[s].m, sizes[s].r) && items > 0 &&
-        items < sweep_target_warps())
-      split[s] = std::min(n_chunks, (sweep_target_warps() + items - 1) / items);
+        items < sweep_split_warps())
+      split[s] = std::min(n_chunks, (sweep_split_warps() + items - 1) / items);
     if (split[s] > 1) n_part = std::max(n_part, (size_t)n_chunks * n_subsets * n_c);
   }
   // scratch layout: records | partials | ysum | c_grid | err | chunk partials

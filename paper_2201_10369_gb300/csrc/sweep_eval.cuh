@@ -325,6 +325,9 @@ int sweep_combine(const double* part, int n_chunks, int64_t stride, int64_t n,
 // How many warps a chunk-split sweep launch aims for: enough items that a
 // launch of few instances still fills every SM several times over.
 int sweep_target_warps();
+// The same for one size of the per-size sweep, whose sizes share the GPU
+// (sweep.cu).
+int sweep_split_warps();
 
 // Sizes the sweep is compiled for, as (index, dim, m, r) cases.
 #define WINO_SWEEP_SIZES(X) \

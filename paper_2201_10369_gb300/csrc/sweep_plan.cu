@@ -423,10 +423,11 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
   }
   p->size_first.assign(n_sizes, 0);
   p->size_count.assign(n_sizes, 0);
-  // a size with too few groups of 32 instances to fill the GPU on its own
-  // (per-size mode runs each size as one launch) spreads each group's trial
-  // chunks over several items; their partial sums are combined in fixed
-  // order afterwards, so the errors are the same bits either way
+  // a size with too few groups of 32 instances to fill its share of the GPU
+  // (per-size mode runs each size as one launch, beside the others)
+  // spreads each group's trial chunks over several items; their partial
+  // sums are combined in fixed order afterwards, so the errors are the same
+  // bits either way
   const int n_chunks = trial_chunks(trials);
   p->inst_first.assign(n_sizes, 0);
   p->inst_count.assign(n_sizes, 0);
@@ -437,8 +438,8 @@ int wino_sweep_plan_create(const wino_size* sizes, int n_sizes, const wino_insta
     const double flops = sweep_trial_flops(p->sizes[s].dim, p->sizes[s].m, p->sizes[s].r);
     const int64_t items = ((int64_t)by_size[s].size() + 31) / 32;
     int split = 1;
-    if (items > 0 && items < sweep_target_warps())
-      split = (int)std::min<int64_t>(n_chunks, (sweep_target_warps() + items - 1) / items);
+    if (items > 0 && items < sweep_split_warps())
+      split = (int)std::min<int64_t>(n_chunks, (sweep_split_warps() + items - 1) / items);
     const int ch_per = (n_chunks + split - 1) / split;
     const int groups = (n_chunks + ch_per - 1) / ch_per;
     p->size_split[s] = groups > 1;
