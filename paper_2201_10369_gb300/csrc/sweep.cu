@@ -236,7 +236,8 @@ static MaskList valid_masks(const SweepSize& s, const unsigned char* subsets, in
 // use): the sizes' evaluation launches are spread over them so that one
 // size's last, partly filled wave overlaps the next size's work; the
 // caller's stream forks to them after the trial records and joins them
-// before the results are copied.
+// before the results are copied.  (Full grid: 2, 4 and 6 streams measured
+// 8.5, 8.4 and 7.85 ms against 7.8 ms for three.)
 constexpr int kSweepStreams = 3;
 static int sweep_streams(cudaStream_t** aux, cudaEvent_t** ev) {
   static cudaStream_t streams[16][kSweepStreams];
