@@ -1152,49 +1152,52 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     int rc = side_stream(&aux, &fork, &join);
     if (rc != WINO_OK) return rc;
   }
-  WINO_CUDA_TRY(cudaEventRecord(fork, st));
-  WINO_CUDA_TRY(cudaStreamWaitEvent(aux, fork, 0));
-  WINO_CUDA_TRY(cudaMemsetAsync(vmax, 0, (size_t)g.F * 4, aux));
   {
-    ProfScope psf(kKTcTransform, aux);
-    // per-frequency maxima of V (each block reduces up to 8 kernels per
-    // thread), then V recomputed, scaled and split
-    const int64_t nck = (int64_t)g.C * g.K;
-    const unsigned bf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(
-                                                           (nck + 8 * kFvThreads - 1) /
-                                                           (8 * kFvThreads), 1 << 16));
-    const unsigned bq = (unsigned)(((int64_t)g.K * Cp + 255) / 256);
-    if (M.m == 2) {
-      k_filter_vmax<2><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<2><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
-                                            NB);
-    } else if (M.m == 4) {
-      k_filter_vmax<4><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<4><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
-                                            NB);
-    } else {
-      k_filter_vmax<6><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
-      k_filter_quant<6><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
-                                            NB);
-    }
-    note_launches(2);
-  }
-  WINO_CUDA_TRY(cudaEventRecord(join, aux));
-  {
+    // profiled as one phase on the caller's stream, fork to join (the two
+    // sides overlap, so per-kernel events would count the overlap twice)
     ProfScope ps(kKTcTransform, st);
-    const dim3 gq((unsigned)(Tp / 64), (unsigned)(Cp / (M.m == 6 ? 4 : 8)));
-    if (M.m == 2)
-      k_quant_input_mn<2><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                        mode);
-    else if (M.m == 4)
-      k_quant_input_mn<4><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                        mode);
-    else
-      k_quant_input_mn<6><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                        mode);
-    note_launches(1);
+    WINO_CUDA_TRY(cudaEventRecord(fork, st));
+    WINO_CUDA_TRY(cudaStreamWaitEvent(aux, fork, 0));
+    WINO_CUDA_TRY(cudaMemsetAsync(vmax, 0, (size_t)g.F * 4, aux));
+    {
+      // per-frequency maxima of V (each block reduces up to 8 kernels per
+      // thread), then V recomputed, scaled and split
+      const int64_t nck = (int64_t)g.C * g.K;
+      const unsigned bf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(
+                                                             (nck + 8 * kFvThreads - 1) /
+                                                             (8 * kFvThreads), 1 << 16));
+      const unsigned bq = (unsigned)(((int64_t)g.K * Cp + 255) / 256);
+      if (M.m == 2) {
+        k_filter_vmax<2><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
+        k_filter_quant<2><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+                                              NB);
+      } else if (M.m == 4) {
+        k_filter_vmax<4><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
+        k_filter_quant<4><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+                                              NB);
+      } else {
+        k_filter_vmax<6><<<bf, kFvThreads, 0, aux>>>(w, g.C, g.K, M, vmax);
+        k_filter_quant<6><<<bq, 256, 0, aux>>>(w, g.C, g.K, Cp, M, vmax, sV, Vp[0], Vp[1], Vp[2], mode,
+                                              NB);
+      }
+      note_launches(2);
+    }
+    WINO_CUDA_TRY(cudaEventRecord(join, aux));
+    {
+      const dim3 gq((unsigned)(Tp / 64), (unsigned)(Cp / (M.m == 6 ? 4 : 8)));
+      if (M.m == 2)
+        k_quant_input_mn<2><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                          mode);
+      else if (M.m == 4)
+        k_quant_input_mn<4><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                          mode);
+      else
+        k_quant_input_mn<6><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
+                                                          mode);
+      note_launches(1);
+    }
+    WINO_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
   }
-  WINO_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
   TcGemmArgs P;
   for (int pp = 0; pp < 3; ++pp) {
     P.U[pp] = Up[pp];

@@ -247,3 +247,28 @@ def test_bounded_wait_gives_up_and_reports(wino):
     hdr = (pathlib.Path(__file__).resolve().parents[1] / "include" / "wino.h").read_text()
     polls = 1 << int(re.search(r"#define WINO_WAIT_POLLS \(1 << (\d+)\)", hdr).group(1))
     assert ns / 256 * polls < 5e9, (ns / 256, polls)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "split_bf16x6"])
+def test_layer_on_a_caller_stream(wino, dtype):
+    """A layer call enqueues part of its work (the filter transforms) on the
+    library's side stream and joins it back to the caller's stream: a caller
+    who waits for their own stream only sees the finished output, the same
+    bits as a call on the default stream.  The caller's stream starts behind
+    a long kernel, so the side stream's work would run ahead of it unless
+    the fork orders it."""
+    import torch
+    C, H, N = 128, 56, 8
+    x, w = inputs.vgg_layer_device(C, H, N=N, seed=3)
+    y0 = torch.empty((N, C, H, H), device="cuda")
+    wino.wino_conv2d(x, w, y0, POINTS[4], 4, 3, 1, dtype)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    y1 = torch.full_like(y0, float("nan"))
+    w1 = torch.zeros_like(w)
+    with torch.cuda.stream(s):
+        torch.cuda._sleep(20_000_000)  # the caller's stream is busy ...
+        w1.copy_(w)                    # ... and only then holds the weights
+        wino.wino_conv2d(x, w1, y1, POINTS[4], 4, 3, 1, dtype, stream=s)
+    s.synchronize()
+    assert torch.equal(y1, y0)
