@@ -14,8 +14,14 @@
  *  - Device pointers are plain CUDA device addresses (for example a torch
  *    tensor's data_ptr()), contiguous, row-major, owned by the caller.
  *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
- *    stream).  All device work of a call is enqueued on that stream and the
- *    call returns without synchronising, unless stated otherwise.
+ *    stream).  The device work of a call is ordered on that stream: it starts
+ *    after the work already enqueued there, and work enqueued there later
+ *    starts after it.  Parts of it may run on the library's internal streams
+ *    (the layers' filter transforms, the sweep's sizes), forked from and
+ *    joined back to that stream by events, so the ordering holds for them
+ *    too.  The call returns without synchronising, unless stated otherwise.
+ *    Calls that run at the same time from several host threads share those
+ *    internal streams and the library's scratch.
  *  - The library keeps internal scratch (allocated on first use and grown
  *    when needed, or caller-provided through wino_set_workspace) and releases
  *    it in wino_shutdown().  It never frees caller memory.
