@@ -1253,10 +1253,17 @@ static int launch_split_cl(const float* x, const float* w, float* y, const Layer
 // 5.2 waves of 152 SMs' resident clusters; 256 at stage 5 are 1.7).  32 x
 // 64 blocks (one warp per frequency, 6 or 8 CTAs per cluster, two per SM)
 // measured 10-25% slower than the best shape on every VGG16 stage; CL_M4_2
-// with four stages 5% slower; F(6x6) over 8 CTAs of two warps (16 tiles,
-// six CTAs per SM) 2% slower than CL_M6_2; 16 x 64 blocks in 16-channel
-// chunks over 6 CTAs (half the chunk steps, and one k block at K = 64) were
-// never the autotuner's pick on a VGG16 stage.
+// with four stages 5% slower, with two stages (96 registers, seven CTAs per
+// SM) 3-7% slower; F(6x6) over 8 CTAs of two warps (16 tiles, six CTAs per
+// SM) 2% slower than CL_M6_2; 16 x 64 blocks in 16-channel chunks over 6
+// CTAs (half the chunk steps, and one k block at K = 64) were never the
+// autotuner's pick on a VGG16 stage.  A persistent form (one cluster per
+// resident cluster slot walking the blocks, its stage ring running on from
+// one block's chunks into the next block's, the epilogue's accumulators in
+// a region of their own behind a split cluster barrier) was bit-identical
+// and 30-80% slower on every stage: that region costs the stages or the
+// CTAs per SM the main loop needs (two stages at four CTAs per SM, or three
+// at three, against three at five here).
 #define CL_M4_0 4, 3, 2, 4, 4, 8, 8, 8, 3, 2
 #define CL_M4_1 4, 3, 2, 4, 4, 8, 8, 8, 2, 3
 #define CL_M4_2 4, 6, 2, 4, 4, 8, 8, 8, 3, 4
