@@ -34,6 +34,7 @@
 #include "async_copy.cuh"
 #include "common.cuh"
 #include "packed.cuh"
+#include "patch.cuh"
 
 namespace wino {
 
@@ -456,8 +457,10 @@ static SplitGeom split_geom(const LayerGeom& g, int TB, int KB, int CC) {
 }
 
 // Input transform into Ub: one CTA per (tile block, chunk), one thread per
-// (channel, tile) of it (tiles fastest: neighbouring tiles share input rows
-// in L1).  The chunk's F x UPL floats are staged in shared memory and leave
+// (channel, tile) of it (tiles fastest: with padding 1 and W even a lane
+// loads its patch's interior columns as vectors and takes the halo columns
+// from the neighbouring lanes, patch.cuh; otherwise neighbouring tiles
+// share input rows in L1).  The chunk's F x UPL floats are staged in shared memory and leave
 // as one contiguous run of 16-byte stores (the chunk's rows are UPL floats
 // apart, not a multiple of the 128-byte line, so per-row stores would split
 // lines).  (Unpadded planes for the cluster shapes, UPL = CC TB, stored
@@ -478,7 +481,13 @@ __global__ void __launch_bounds__(256) k_input_transform_blk(const float* __rest
   const int c = ch * sg.CC + cc;
   float d[A][A];
   const bool live = t < g.T && c < g.C;
-  if (live) {
+  if (patch_rowvec_ok(x, g) && (blockDim.x & 31) == 0) {
+    // a lane's neighbours hold tiles t -+ 1 of channel c unless it is at
+    // an end of the warp or of the block's tile range
+    const int lane = threadIdx.x & 31;
+    load_patch_rowvec<MM>(x, g, t, c, live, lane == 0 || tl == 0,
+                          lane == 31 || tl == sg.TB - 1, d);
+  } else if (live) {
     const int tpi = g.th * g.tw;
     const int n = (int)(t / tpi);
     const int rem = (int)(t - (int64_t)n * tpi);

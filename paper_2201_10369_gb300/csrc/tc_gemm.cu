@@ -326,8 +326,10 @@ __device__ __forceinline__ void ldg8(const float* p, float (&v)[8]) {
 // contiguous run); column 4 tj - 1 is column 7 of lane q - 1 and column
 // 4 tj + 8 column 0 of lane q + 1 whenever those columns are inside the row
 // (the neighbours hold the adjacent tiles of the same tile row), else zero
-// padding, and the warp's first and last lanes load them.  Called by every
-// lane of the warp, lane q with t = t_w + 2q.
+// padding, and the warp's first and last lanes load them.  All six rows'
+// loads are issued before the first shuffle, which waits on them, so that
+// they are in flight together.  Called by every lane of the warp, lane q
+// with t = t_w + 2q.
 __device__ __forceinline__ void load_pair_f4_v8(const float* __restrict__ x, const LayerGeom& g,
                                                 int64_t t, int c, int lane,
                                                 unsigned long long (&d)[6][6]) {
@@ -343,29 +345,40 @@ __device__ __forceinline__ void load_pair_f4_v8(const float* __restrict__ x, con
   const int h0 = ti * 4 - 1, c0 = tj * 4;
   const float* xc = x + ((int64_t)n * g.C + c) * g.H * g.W;
   const bool has_l = live && c0 > 0, has_r = live && c0 + 8 < g.W;
+  float v[6][8], el[6], er[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     const int hh = h0 + i;
-    const bool in = live && (unsigned)hh < (unsigned)g.H;
-    float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    const float* row = xc + (int64_t)hh * g.W + c0;
-    if (in) ldg8(row, v);
-    float e0 = __shfl_up_sync(0xffffffffu, v[7], 1);
-    float e9 = __shfl_down_sync(0xffffffffu, v[0], 1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[i][k] = 0.0f;
+    el[i] = 0.0f;
+    er[i] = 0.0f;
+    if (live && (unsigned)hh < (unsigned)g.H) {
+      const float* row = xc + (int64_t)hh * g.W + c0;
+      ldg8(row, v[i]);
+      if (lane == 0 && has_l) el[i] = __ldg(row - 1);
+      if (lane == 31 && has_r) er[i] = __ldg(row + 8);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const bool in = live && (unsigned)(h0 + i) < (unsigned)g.H;
+    float e0 = __shfl_up_sync(0xffffffffu, v[i][7], 1);
+    float e9 = __shfl_down_sync(0xffffffffu, v[i][0], 1);
     if (!(in && has_l))
       e0 = 0.0f;
     else if (lane == 0)
-      e0 = __ldg(row - 1);
+      e0 = el[i];
     if (!(in && has_r))
       e9 = 0.0f;
     else if (lane == 31)
-      e9 = __ldg(row + 8);
-    d[i][0] = pack2(e0, v[3]);
-    d[i][1] = pack2(v[0], v[4]);
-    d[i][2] = pack2(v[1], v[5]);
-    d[i][3] = pack2(v[2], v[6]);
-    d[i][4] = pack2(v[3], v[7]);
-    d[i][5] = pack2(v[4], e9);
+      e9 = er[i];
+    d[i][0] = pack2(e0, v[i][3]);
+    d[i][1] = pack2(v[i][0], v[i][4]);
+    d[i][2] = pack2(v[i][1], v[i][5]);
+    d[i][3] = pack2(v[i][2], v[i][6]);
+    d[i][4] = pack2(v[i][3], v[i][7]);
+    d[i][5] = pack2(v[i][4], e9);
   }
 }
 

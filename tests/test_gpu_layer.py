@@ -154,6 +154,28 @@ def test_fused_layer_bitwise_vs_oracle(wino, orc, m, shape, variant, monkeypatch
     assert np.array_equal(out["y"], orc.wino_layer(x, w, 2, pad, POINTS[m], m, 3))
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("m", [2, 4, 6])
+@pytest.mark.parametrize("shape", [(2, 11, 64, 13, 16, 1), (1, 5, 64, 7, 22, 1),
+                                   (3, 8, 64, 9, 36, 1)])
+def test_row_vector_patches_bitwise_vs_oracle(wino, orc, m, shape, variant, monkeypatch):
+    """Padding 1 and an even width: the input transforms load each patch
+    row's interior columns as vectors and take the halo columns from the
+    neighbouring lanes.  Widths a multiple of 4 and 2 mod 4, tile rows and
+    columns cut by the image edge, tile blocks that start inside a tile row
+    and channel counts off the chunking, in every tile shape: the same bits
+    as the oracle."""
+    if not _has_variant(m, variant):
+        pytest.skip(f"F({m}x{m},3x3) has {SPLIT_SHAPES[m]} split tile shapes")
+    monkeypatch.setenv("WINO_LAYER_VARIANT", variant)
+    N, C, K, H, W, pad = shape
+    x, w = inputs.layer_uniform(N, C, K, H, W, seed=300 + m)
+    out = {}
+    n = _fused_launches(wino, lambda: out.setdefault("y", _run2d(wino, x, w, POINTS[m], m, pad)))
+    assert n == 1, "fused kernel not taken"
+    assert np.array_equal(out["y"], orc.wino_layer(x, w, 2, pad, POINTS[m], m, 3))
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("m", [4, 6])

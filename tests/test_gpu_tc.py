@@ -91,7 +91,7 @@ def tc_parity_bound(orc, x, w, pts, m, dtype):
 @pytest.mark.parametrize("dtype", ["bf16", "fp16", "split_bf16x3", "split_bf16x6"])
 @pytest.mark.parametrize("m", [4, 6, 2])
 @pytest.mark.parametrize("shape", [(2, 64, 64, 10, 10), (1, 80, 128, 9, 13), (1, 64, 256, 6, 6),
-                                   (1, 300, 128, 7, 9)])
+                                   (1, 300, 128, 7, 9), (1, 64, 64, 11, 24)])
 def test_tc_layer_vs_oracle_emulation(wino, orc, dtype, m, shape):
     import torch
     N, C, K, H, W = shape
