@@ -1057,13 +1057,13 @@ def profile_case(name):
         base, shapes = name[:-4], inputs.VGG16_LAYERS
     elif name[-3:-1] == "_l":  # one VGG16 stage at the bench's N=32
         base, shapes, nimg = name[:-3], [inputs.VGG16_LAYERS[int(name[-1])]], 32
-    if base in ("f4x4", "f6x6", "f4x4_bf16", "f4x4_split", "f4x4_x6"):
+    if base in ("f4x4", "f6x6", "f4x4_bf16", "f4x4_split", "f4x4_x6", "f6x6_bf16", "f6x6_x6"):
         # one layer (64 ch, 224x224, N=8) unless a suffix says otherwise
         xs = [inputs.vgg_layer_device(C, H, N=nimg, seed=i) for i, (C, H) in enumerate(shapes)]
         ys = [torch.empty_like(x) for x, _ in xs]
         m, pts = (4, PTS4) if base.startswith("f4x4") else (6, PTS6)
-        dt = {"f4x4_bf16": "bf16", "f4x4_split": "split_bf16x3",
-              "f4x4_x6": "split_bf16x6"}.get(base, "f32")
+        dt = {"bf16": "bf16", "split": "split_bf16x3",
+              "x6": "split_bf16x6"}.get(base[5:], "f32")
         for _ in range(4):
             for (x, w), y in zip(xs, ys):
                 wino.wino_conv2d(x, w, y, pts, m, 3, 1, dt)
@@ -1105,7 +1105,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     help="run one small workload a few times for an ncu capture: "
-                         "f4x4 | f6x6 | f4x4_bf16 | f4x4_split | f4x4_x6 (VGG 64ch 224x224, N=8; "
+                         "f4x4 | f6x6 | f4x4_bf16 | f4x4_split | f4x4_x6 | f6x6_bf16 | f6x6_x6 (VGG 64ch 224x224, N=8; "
                          "suffix _vgg: the five VGG16 stages, N=8; suffix _l0.._l4: that "
                          "VGG16 stage at N=32) | sweep (2D F(4x4), all masks, 4096 c) | "
                          "sweep_<dim>d<m> (that sweep size, e.g. sweep_1d4) | "

@@ -444,11 +444,14 @@ __device__ __forceinline__ void load_patch_pair(const float* __restrict__ x, con
     for (int j = 0; j < A; ++j) d[i][j] = pack2(p0[i][j], p1[i][j]);
 }
 
-template <int MM>
+// MODE 1-4 fixes the form at compile time (its parts, stores and pointer
+// updates only); MODE 0 takes it from `mode_rt`.
+template <int MM, int MODE>
 __global__ void __launch_bounds__(kQuantThreads) k_quant_input_mn(
     const float* __restrict__ x, const LayerGeom g, const LayerMats Mx, const TcScales S, int Cp,
     int64_t Tp, uint16_t* __restrict__ U0, uint16_t* __restrict__ U1, uint16_t* __restrict__ U2,
-    int mode) {
+    int mode_rt) {
+  const int mode = MODE != 0 ? MODE : mode_rt;
   constexpr int A = MM + 2, F = A * A;
   constexpr int TPL = A <= 6 ? 2 : 1;    // tiles per lane
   constexpr int WT = 64 / (32 * TPL);    // warps per 64 tiles
@@ -528,6 +531,22 @@ __global__ void __launch_bounds__(kQuantThreads) k_quant_input_mn(
     });
   }
   (void)F;
+}
+
+// k_quant_input_mn with the form (1 BF16, 2 FP16, 3 split-BF16x3, 4
+// split-BF16x6) as a template argument.
+template <int MM>
+static void launch_quant_input(dim3 gq, cudaStream_t st, const float* x, const LayerGeom& g,
+                               const LayerMats& M, const TcScales& S, int Cp, int64_t Tp,
+                               uint16_t* U0, uint16_t* U1, uint16_t* U2, int mode) {
+  if (mode == 1)
+    k_quant_input_mn<MM, 1><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, U0, U1, U2, mode);
+  else if (mode == 2)
+    k_quant_input_mn<MM, 2><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, U0, U1, U2, mode);
+  else if (mode == 3)
+    k_quant_input_mn<MM, 3><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, U0, U1, U2, mode);
+  else
+    k_quant_input_mn<MM, 4><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, U0, U1, U2, mode);
 }
 
 // Output transform A^T M A with compile-time sizes, M [F][K][T]: one thread
@@ -1199,14 +1218,12 @@ int layer_forward_tc(const float* x, const float* w, float* y, const LayerGeom& 
     {
       const dim3 gq((unsigned)(Tp / 64), (unsigned)(Cp / (M.m == 6 ? 4 : 8)));
       if (M.m == 2)
-        k_quant_input_mn<2><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                          mode);
+        k_quant_input_mn<2, 0><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1],
+                                                             Up[2], mode);
       else if (M.m == 4)
-        k_quant_input_mn<4><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                          mode);
+        launch_quant_input<4>(gq, st, x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2], mode);
       else
-        k_quant_input_mn<6><<<gq, kQuantThreads, 0, st>>>(x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2],
-                                                          mode);
+        launch_quant_input<6>(gq, st, x, g, M, S, Cp, Tp, Up[0], Up[1], Up[2], mode);
       note_launches(1);
     }
     WINO_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
