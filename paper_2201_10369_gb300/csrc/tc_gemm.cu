@@ -227,10 +227,11 @@ __global__ void __launch_bounds__(256) k_filter_quant(const float* __restrict__ 
 // channels c >= C are zero.  A warp takes one channel of 64 consecutive
 // tiles (F(2x2), F(4x4): two adjacent tiles per lane) or 32 (F(6x6): one per
 // lane), so that its patch loads run along the input rows (F(4x4): a lane's
-// two patches are one 16-byte-aligned run of ten columns per row, loaded as
-// two 16-byte vectors and two scalars) and its results for one frequency
-// and part are one contiguous run of the image: 128 bytes (a whole line,
-// two tiles' 16-bit values in each 32-bit store) or 64 bytes.  Nothing is
+// two patches are one run of ten columns per row, loaded as one 32-byte
+// vector with the two edge columns from the neighbouring lanes, or as two
+// 16-byte vectors and two scalars) and its results for one frequency and
+// part are one contiguous run of the image: 128 bytes (a whole line, two
+// tiles' 16-bit values in each 32-bit store) or 64 bytes.  Nothing is
 // staged in shared memory.  Launch: grid (Tp / 64, Cp / 8) blocks of 256
 // threads for F(2x2) and F(4x4), (Tp / 64, Cp / 4) for F(6x6).
 constexpr int kQuantThreads = 256;
